@@ -1,0 +1,156 @@
+/*
+ * pw.h -- C ABI of the GB300 Chebyshev-filtered plane-wave Hamiltonian library.
+ *
+ * The problem is the Kohn-Sham generalised eigenproblem H psi_i = lambda_i S psi_i
+ * of arxiv 2604.11139 Sec. 3.1: N plane waves (the sphere |k+G|^2/2 <= E_cut),
+ * M bands, H = T + V_loc + sum_ij |p_i> D_ij <p_j| (Sec. 4.2, nonlocal operator),
+ * S = I + sum_ij |p_i> Q_ij <p_j| (PAW overlap, Sec. 3.1).  The library applies H
+ * matrix-free (Sec. 3.2), runs the degree-m Chebyshev filter of Alg. 7 / Alg. 12
+ * and the Rayleigh-Ritz step of Alg. 5, all in hand-written CUDA kernels for one
+ * GB300 (sm_103a).
+ *
+ * Conventions shared by every entry point
+ *  - Wave-function blocks are column-major N x M complex matrices (interleaved
+ *    re/im), band j at offset j*ld elements, ld >= npw (strided bands, Sec. 2.1).
+ *    Rows follow the context's canonical plane-wave order (pw_ctx_gvectors).
+ *    Element type: complex128 for PW_FP64 entry points, complex64 where a
+ *    PW_MIXED precision is requested.  Blocks are DEVICE pointers owned by the
+ *    caller unless stated otherwise.
+ *  - Every call is asynchronous on the context's stream unless it returns host
+ *    values (eigenvalues, bounds), in which case it synchronises that stream.
+ *  - Workspaces are owned by the context and only grow; after the first call
+ *    with a given shape no further device allocation happens.
+ *  - Return value: PW_OK (0) or a negative pw_status.  No exception, abort or
+ *    exit crosses the ABI.  pw_last_error() gives a one-line description of the
+ *    last failure on the calling thread.  After PW_ECUDA the context must be
+ *    destroyed.
+ */
+#ifndef PW_H
+#define PW_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(__GNUC__)
+#define PW_API __attribute__((visibility("default")))
+#else
+#define PW_API
+#endif
+
+typedef struct pw_ctx pw_ctx;
+
+enum pw_status {
+  PW_OK = 0,
+  PW_EINVAL = -1,       /* bad argument: shapes, ld < npw, sphere not fitting the box */
+  PW_ENOMEM = -2,       /* device allocation failed */
+  PW_ECUDA = -3,        /* a CUDA call failed; the context is poisoned */
+  PW_ENOTSPD = -4,      /* Cholesky of S_Psi, of Q or of Q^-1 + P^dagger P failed */
+  PW_ETIMEDOUT = -5,    /* a bounded device-side wait expired */
+  PW_ENOTCONV = -6,     /* subspace eigensolver did not converge */
+  PW_EUNSUPPORTED = -7  /* FFT length with a prime factor outside {2,3,5}, etc. */
+};
+
+enum pw_precision {
+  PW_FP64 = 0,  /* complex128 blocks, FP64 FFT and FP64 projector GEMMs */
+  PW_MIXED = 1  /* complex64 blocks and FFTs, BF16-split tensor-core projector
+                   GEMMs with FP32 accumulation (filter only) */
+};
+
+/* Problem statement (Sec. 3.1 and 4.2).  All pointers are HOST pointers and are
+ * only read during pw_ctx_create. */
+typedef struct {
+  double lattice[9];   /* rows a1, a2, a3 in bohr */
+  double kpt[3];       /* k-point in reduced coordinates */
+  double ecut;         /* plane-wave cut-off (Ha): sphere |k+G|^2/2 <= ecut */
+  int box[3];          /* FFT box n1, n2, n3; each factorises into 2, 3, 5 */
+  const double* vloc;  /* n1*n2*n3 real V_loc(r_j), C order (index (j1*n2+j2)*n3+j3) */
+  int natom;
+  const double* tau;   /* natom*3 cartesian atom positions (bohr) */
+  int nchan;           /* projector channels per atom; 4 projectors (s, px, py, pz) each */
+  const double* sigma; /* nchan Gaussian widths (bohr) of the projector form factors */
+  const double* D;     /* nproj*nproj real symmetric, column-major, nproj = natom*4*nchan */
+  const double* Q;     /* nproj*nproj real symmetric positive definite, or NULL (S = I) */
+} pw_problem_desc;
+
+/* Builds the plane-wave sphere, the FFT plans, the projector matrix P (Sec. 4.2:
+ * P = <G|p_i^R>, Gaussian s/p form factors, structure phase exp(-i(k+G).R),
+ * unit column norm), the permuted V_loc grid and, when Q != NULL, the Woodbury
+ * matrices of S^-1 (Sec. 3.3 Sinv).  stream: a cudaStream_t, or NULL for the
+ * legacy default stream.  On success *out owns all device memory it uses. */
+PW_API int pw_ctx_create(const pw_problem_desc* desc, void* stream, pw_ctx** out);
+PW_API int pw_ctx_destroy(pw_ctx* ctx);
+PW_API int pw_ctx_set_stream(pw_ctx* ctx, void* stream);
+
+/* Sizes: number of plane waves N and projectors N_projs. */
+PW_API int pw_ctx_info(const pw_ctx* ctx, int* npw, int* nproj);
+
+/* Canonical plane-wave order: Miller indices (h,k,l) sorted ascending by h, then
+ * k, then l (host int32 array 3*npw, row-major), and the kinetic energies
+ * |k+G|^2/2 (host, npw doubles).  Either pointer may be NULL. */
+PW_API int pw_ctx_gvectors(const pw_ctx* ctx, int32_t* miller, double* kinetic);
+
+/* Copies the generated projector matrix P (npw x nproj complex128, column-major,
+ * ld = npw) to the device buffer P_out. */
+PW_API int pw_ctx_projectors(const pw_ctx* ctx, void* P_out);
+
+/* HX / HX_SX of Sec. 3.3: hpsi = H psi and, if spsi != NULL, spsi = S psi for
+ * nband bands.  psi, hpsi, spsi: device blocks of the element type of
+ * `precision`, leading dimensions ldpsi and ldout.  psi must not alias the
+ * outputs. */
+PW_API int pw_hamiltonian_apply(pw_ctx* ctx, const void* psi, int64_t ldpsi, int nband,
+                                void* hpsi, void* spsi, int64_t ldout, int precision);
+
+/* Spectrum bounds of Alg. 12 (FP64): Rayleigh quotients
+ * lambda_i = (H psi_i)^dagger psi_i / ((S psi_i)^dagger psi_i) of the complex128
+ * block psi -> *rq_min, *rq_max (host); and an upper bound of the spectrum of
+ * S^-1 H from `lanczos_steps` Lanczos steps on H from the complex128 start
+ * vector v0 (npw, device): *upper = theta_max + |beta_k| (host).  With nband = 0
+ * only the Lanczos bound is computed; with lanczos_steps = 0 only the quotients. */
+PW_API int pw_spectrum_bounds(pw_ctx* ctx, const void* psi, int64_t ld, int nband,
+                              int lanczos_steps, const void* v0,
+                              double* rq_min, double* rq_max, double* upper);
+
+/* Chebyshev filter of degree m (Alg. 7 / Alg. 12, three-term recurrence):
+ * c = (b+a)/2, e = (b-a)/2, Y_0 = psi, Y_1 = (A-c)Y_0/e,
+ * Y_{k+1} = (2/e)(A-c)Y_k - Y_{k-1}, A = S^-1 H (Woodbury, Sec. 3.3) or H.
+ * psi is overwritten with Y_m.  PW_FP64: complex128 block; PW_MIXED:
+ * complex64 block, FP32 FFTs and BF16-split tensor-core projector GEMMs. */
+PW_API int pw_chebyshev_filter(pw_ctx* ctx, void* psi, int64_t ldpsi, int nband,
+                               int degree, double a, double b, int precision);
+
+/* Rayleigh-Ritz on the complex128 block psi (Alg. 5 preceded by two S-Ortho
+ * passes, Alg. 9), all FP64: psi <- S-orthonormalised Ritz vectors, eig (host,
+ * nband, ascending) <- Ritz values, resid (host, nband, may be NULL) <-
+ * ||H psi_i - lambda_i S psi_i||.  hpsi (may be NULL, ld = ldpsi) receives H psi.
+ * Returns PW_ENOTSPD if the block is numerically rank deficient. */
+PW_API int pw_rayleigh_ritz(pw_ctx* ctx, void* psi, int64_t ldpsi, int nband,
+                            void* hpsi, double* eig, double* resid);
+
+/* One full ChebFi solve (Alg. 12): Lanczos upper bound from v0 (device, complex128),
+ * cycle-1 cut = max Rayleigh quotient of psi, then `cycles` times
+ * [filter (precision) -> Rayleigh-Ritz (FP64)], the cut of each later cycle
+ * being the largest Ritz value.  psi: complex128 device block, overwritten with
+ * the Ritz vectors.  eig, resid: host arrays of nband (resid may be NULL).
+ * bounds (host, may be NULL) receives {upper, first cut}. */
+PW_API int pw_chebfi_solve(pw_ctx* ctx, void* psi, int64_t ldpsi, int nband, int degree,
+                           int cycles, int lanczos_steps, const void* v0, int precision,
+                           double* eig, double* resid, double* bounds);
+
+/* Density / gradient contraction (Alg. 3 density step):
+ * out(r_j) (+)= sum_i w_i Re[conj(a_i(r_j)) b_i(r_j)], a_i(r) = sum_G a_iG e^{iG.r_j}
+ * (unnormalised inverse DFT), b = a when b == NULL.  a, b: complex128 device
+ * blocks (ld); w: host weights (nband); out: device n1*n2*n3 doubles in C order;
+ * accumulate != 0 adds to out instead of overwriting it. */
+PW_API int pw_density_grad(pw_ctx* ctx, const void* a, const void* b, int64_t ld, int nband,
+                           const double* w, double* out, int accumulate);
+
+PW_API const char* pw_strerror(int status);
+PW_API const char* pw_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PW_H */

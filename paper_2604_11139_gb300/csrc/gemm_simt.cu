@@ -1,0 +1,180 @@
+// Complex GEMMs on the CUDA cores (FP64 DFMA / FP32 FFMA) for the projector
+// contractions C_proj = P^dagger Psi and Psi += P (D C_proj) (Sec. 4.2), the
+// Rayleigh-Ritz Grams and rotations (Alg. 5) and the small projector-space
+// products.  On GB300 FP64 has no fast tensor path, so the FP64 forms are
+// DFMA-bound; the kernel keeps a 64x64 complex tile per CTA with a 4x4 register
+// tile per thread and stages 16-deep K slices through shared memory.
+#include "pw_internal.cuh"
+
+namespace pw {
+
+template <typename T>
+__device__ __forceinline__ void epi_apply(const Epi<T>& e, int m, int n, cplx<T> v) {
+  using C = cplx<T>;
+  C* o = e.out + m + (int64_t)n * e.ldo;
+  switch (e.mode) {
+    case EPI_STORE: *o = cscale(v, e.alpha); break;
+    case EPI_ACCUM: *o = cadd(*o, cscale(v, e.alpha)); break;
+    case EPI_CHEB: {
+      const C w = *o;
+      const C yk = e.yk[m + (int64_t)n * e.ldy];
+      C r = cscale(csub(cadd(w, v), cscale(yk, e.shift)), e.alpha);
+      if (e.ykm1) r = csub(r, cscale(e.ykm1[m + (int64_t)n * e.ldy2], e.beta));
+      *o = r;
+    } break;
+    default: break;
+  }
+}
+
+constexpr int BM = 64, BN = 64, BK = 16;
+
+template <typename T, int TA, int TB>
+__global__ void __launch_bounds__(256) k_cgemm(int M, int N, int K, const cplx<T>* __restrict__ A, int64_t lda,
+                                               const cplx<T>* __restrict__ B, int64_t ldb, Epi<T> epi,
+                                               int kchunk, cplx<T>* __restrict__ ws) {
+  using C = cplx<T>;
+  __shared__ C As[BK][BM + 1];
+  __shared__ C Bs[BK][BN + 1];
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
+  const int kb = blockIdx.z * kchunk, ke = min(K, kb + kchunk);
+  C acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = czero<C>();
+  for (int k0 = kb; k0 < ke; k0 += BK) {
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const int lin = tid + 256 * e;
+      int mm, kk;
+      if (TA == 0) { mm = lin % BM; kk = lin / BM; } else { kk = lin % BK; mm = lin / BK; }
+      const int gm = m0 + mm, gk = k0 + kk;
+      C v = czero<C>();
+      if (gm < M && gk < ke) v = (TA == 0) ? A[gm + gk * lda] : cconj(A[gk + gm * lda]);
+      As[kk][mm] = v;
+    }
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const int lin = tid + 256 * e;
+      int nn, kk;
+      if (TB == 0) { kk = lin % BK; nn = lin / BK; } else { nn = lin % BN; kk = lin / BN; }
+      const int gn = n0 + nn, gk = k0 + kk;
+      C v = czero<C>();
+      if (gn < N && gk < ke) v = (TB == 0) ? B[gk + gn * ldb] : cconj(B[gn + gk * ldb]);
+      Bs[kk][nn] = v;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < BK; ++kk) {
+      C a[4], b[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) a[i] = As[kk][ty + 16 * i];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx + 16 * j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          acc[i][j].x = fma(a[i].x, b[j].x, acc[i][j].x);
+          acc[i][j].x = fma(-a[i].y, b[j].y, acc[i][j].x);
+          acc[i][j].y = fma(a[i].x, b[j].y, acc[i][j].y);
+          acc[i][j].y = fma(a[i].y, b[j].x, acc[i][j].y);
+        }
+    }
+    __syncthreads();
+  }
+  if (gridDim.z > 1) {
+    C* w = ws + (int64_t)blockIdx.z * M * N;
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int m = m0 + ty + 16 * i, n = n0 + tx + 16 * j;
+        if (m < M && n < N) w[m + (int64_t)n * M] = acc[i][j];
+      }
+  } else {
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int m = m0 + ty + 16 * i, n = n0 + tx + 16 * j;
+        if (m < M && n < N) epi_apply<T>(epi, m, n, acc[i][j]);
+      }
+  }
+}
+
+template <typename T>
+__global__ void k_splitk_reduce(int M, int N, int nsplit, const cplx<T>* __restrict__ ws, Epi<T> epi) {
+  using C = cplx<T>;
+  const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (idx >= (int64_t)M * N) return;
+  C s = czero<C>();
+  for (int z = 0; z < nsplit; ++z) s = cadd(s, ws[z * (int64_t)M * N + idx]);
+  const int m = (int)(idx % M), n = (int)(idx / M);
+  epi_apply<T>(epi, m, n, s);
+}
+
+template <typename T>
+cudaError_t launch_cgemm(int ta, int tb, int M, int N, int K, const cplx<T>* A, int64_t lda,
+                         const cplx<T>* B, int64_t ldb, const Epi<T>& epi, int nsplit, cplx<T>* ws,
+                         cudaStream_t st) {
+  if (M <= 0 || N <= 0) return cudaSuccess;
+  if (K <= 0) nsplit = 1;
+  if (nsplit < 1) nsplit = 1;
+  int kchunk = (K + nsplit - 1) / nsplit;
+  kchunk = ((kchunk + BK - 1) / BK) * BK;
+  if (kchunk <= 0) kchunk = BK;
+  nsplit = (K + kchunk - 1) / kchunk;
+  if (nsplit < 1) nsplit = 1;
+  dim3 grid((M + BM - 1) / BM, (N + BN - 1) / BN, nsplit);
+  if (ta == 0 && tb == 0) k_cgemm<T, 0, 0><<<grid, 256, 0, st>>>(M, N, K, A, lda, B, ldb, epi, kchunk, ws);
+  else if (ta == 1 && tb == 0) k_cgemm<T, 1, 0><<<grid, 256, 0, st>>>(M, N, K, A, lda, B, ldb, epi, kchunk, ws);
+  else if (ta == 0 && tb == 1) k_cgemm<T, 0, 1><<<grid, 256, 0, st>>>(M, N, K, A, lda, B, ldb, epi, kchunk, ws);
+  else k_cgemm<T, 1, 1><<<grid, 256, 0, st>>>(M, N, K, A, lda, B, ldb, epi, kchunk, ws);
+  if (nsplit > 1) {
+    const int64_t tot = (int64_t)M * N;
+    k_splitk_reduce<T><<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(M, N, nsplit, ws, epi);
+  }
+  return cudaGetLastError();
+}
+
+// Z = D C with D real (nproj x nproj, column-major) applied block by block
+template <typename T>
+__global__ void k_dblock(int nproj, int nband, const T* __restrict__ D, const int* __restrict__ blk0,
+                         const int* __restrict__ blklen, const cplx<T>* __restrict__ Cm, int64_t ldc,
+                         cplx<T>* __restrict__ Z, int64_t ldz) {
+  using C = cplx<T>;
+  const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (idx >= (int64_t)nproj * nband) return;
+  const int p = (int)(idx % nproj), j = (int)(idx / nproj);
+  const int q0 = blk0[p], nq = blklen[p];
+  C s = czero<C>();
+  for (int q = q0; q < q0 + nq; ++q) {
+    const T d = D[p + (int64_t)q * nproj];
+    const C c = Cm[q + (int64_t)j * ldc];
+    s.x = fma(d, c.x, s.x);
+    s.y = fma(d, c.y, s.y);
+  }
+  Z[p + (int64_t)j * ldz] = s;
+}
+
+template <typename T>
+cudaError_t launch_dblock(int nproj, int nband, const T* D, const int* blk0, const int* blklen,
+                          const cplx<T>* Cm, int64_t ldc, cplx<T>* Z, int64_t ldz, cudaStream_t st) {
+  const int64_t tot = (int64_t)nproj * nband;
+  if (tot <= 0) return cudaSuccess;
+  k_dblock<T><<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(nproj, nband, D, blk0, blklen, Cm, ldc, Z, ldz);
+  return cudaGetLastError();
+}
+
+template cudaError_t launch_cgemm<double>(int, int, int, int, int, const double2*, int64_t, const double2*,
+                                          int64_t, const Epi<double>&, int, double2*, cudaStream_t);
+template cudaError_t launch_cgemm<float>(int, int, int, int, int, const float2*, int64_t, const float2*,
+                                         int64_t, const Epi<float>&, int, float2*, cudaStream_t);
+template cudaError_t launch_dblock<double>(int, int, const double*, const int*, const int*, const double2*,
+                                           int64_t, double2*, int64_t, cudaStream_t);
+template cudaError_t launch_dblock<float>(int, int, const float*, const int*, const int*, const float2*,
+                                          int64_t, float2*, int64_t, cudaStream_t);
+
+}  // namespace pw

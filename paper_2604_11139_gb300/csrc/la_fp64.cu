@@ -1,0 +1,565 @@
+// FP64 dense linear algebra of the subspace step, all on the GPU (Alg. 5, Alg. 9):
+// Hermitian symmetrisation, blocked Cholesky (potrf), triangular inverse
+// (the trsm of S-Ortho done as an explicit inverse and a GEMM), a parallel
+// cyclic Jacobi eigensolver for the reduced Hermitian matrix (the hegvd step,
+// after Cholesky reduction), eigenpair sorting, column reductions (Rayleigh
+// quotients, residual norms) and the Lanczos helpers of the spectrum bound.
+#include <math.h>
+
+#include "pw_internal.cuh"
+#include "la.cuh"
+
+namespace pw {
+
+// ---- symmetrisation ---------------------------------------------------------------
+__global__ void k_herm_sym(double2* A, int64_t lda, int n) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  if (i >= n || j >= n || i < j) return;
+  if (i == j) { A[i + i * lda].y = 0.0; return; }
+  const double2 a = A[i + j * lda], b = A[j + i * lda];
+  const double2 m = make_double2(0.5 * (a.x + b.x), 0.5 * (a.y - b.y));
+  A[i + j * lda] = m;
+  A[j + i * lda] = cconj(m);
+}
+
+cudaError_t la_herm_sym(double2* A, int64_t lda, int n, cudaStream_t st) {
+  dim3 b(16, 16), g((n + 15) / 16, (n + 15) / 16);
+  k_herm_sym<<<g, b, 0, st>>>(A, lda, n);
+  return cudaGetLastError();
+}
+
+// ---- blocked Cholesky A = L L^dagger (lower, in place; strict upper part zeroed) ---
+constexpr int NB = 32;
+
+__global__ void k_chol_diag(double2* A, int64_t lda, int k0, int kb, int* flag) {
+  __shared__ double2 S[NB][NB + 1];
+  const int tx = threadIdx.x, ty = threadIdx.y;  // 32 x 32
+  if (tx < kb && ty < kb) S[ty][tx] = A[(k0 + ty) + (int64_t)(k0 + tx) * lda];  // S[row][col]
+  __syncthreads();
+  for (int j = 0; j < kb; ++j) {
+    if (tx == 0 && ty == 0) {
+      double d = S[j][j].x;
+      if (!(d > 0.0) || !isfinite(d)) { atomicExch(flag, 1); d = 1.0; }
+      S[j][j] = make_double2(sqrt(d), 0.0);
+    }
+    __syncthreads();
+    const double dj = S[j][j].x;
+    if (tx == 0 && ty > j && ty < kb) S[ty][j] = cscale(S[ty][j], 1.0 / dj);
+    __syncthreads();
+    // trailing: S[i][k] -= S[i][j] conj(S[k][j]) for j < k <= i
+    if (ty > j && ty < kb && tx > j && tx <= ty) S[ty][tx] = csub(S[ty][tx], cmul(S[ty][j], cconj(S[tx][j])));
+    __syncthreads();
+  }
+  if (tx < kb && ty < kb) {
+    const double2 v = (tx <= ty) ? S[ty][tx] : make_double2(0.0, 0.0);
+    A[(k0 + ty) + (int64_t)(k0 + tx) * lda] = v;
+  }
+}
+
+// rows i >= k0+kb: L21[i,:] = A21[i,:] L11^{-dagger}
+__global__ void k_chol_panel(double2* A, int64_t lda, int n, int k0, int kb) {
+  __shared__ double2 Ls[NB][NB + 1];
+  const int t = threadIdx.x;
+  for (int e = t; e < kb * kb; e += blockDim.x) {
+    const int r = e % kb, c = e / kb;
+    Ls[r][c] = A[(k0 + r) + (int64_t)(k0 + c) * lda];
+  }
+  __syncthreads();
+  const int i = k0 + kb + blockIdx.x * blockDim.x + t;
+  if (i >= n) return;
+  double2 x[NB];
+  for (int j = 0; j < kb; ++j) {
+    double2 s = A[i + (int64_t)(k0 + j) * lda];
+    for (int tt = 0; tt < j; ++tt) s = csub(s, cmul(x[tt], cconj(Ls[j][tt])));
+    x[j] = cscale(s, 1.0 / Ls[j][j].x);
+  }
+  for (int j = 0; j < kb; ++j) A[i + (int64_t)(k0 + j) * lda] = x[j];
+}
+
+// trailing update of the lower triangle: A[i][j] -= sum_t L[i][t] conj(L[j][t])
+__global__ void k_chol_update(double2* A, int64_t lda, int n, int k0, int kb) {
+  const int bi = blockIdx.x, bj = blockIdx.y;
+  if (bj > bi) return;
+  __shared__ double2 Li[32][NB + 1], Lj[32][NB + 1];
+  const int s0 = k0 + kb;
+  const int i0 = s0 + bi * 32, j0 = s0 + bj * 32;
+  const int t = threadIdx.x;  // 256
+  for (int e = t; e < 32 * kb; e += 256) {
+    const int r = e % 32, c = e / 32;
+    Li[r][c] = (i0 + r < n) ? A[(i0 + r) + (int64_t)(k0 + c) * lda] : make_double2(0, 0);
+    Lj[r][c] = (j0 + r < n) ? A[(j0 + r) + (int64_t)(k0 + c) * lda] : make_double2(0, 0);
+  }
+  __syncthreads();
+  for (int e = t; e < 32 * 32; e += 256) {
+    const int r = e % 32, c = e / 32;
+    const int i = i0 + r, j = j0 + c;
+    if (i >= n || j >= n || j > i) continue;
+    double2 s = make_double2(0, 0);
+    for (int tt = 0; tt < kb; ++tt) {
+      const double2 a = Li[r][tt], b = Lj[c][tt];
+      s.x += a.x * b.x + a.y * b.y;
+      s.y += a.y * b.x - a.x * b.y;
+    }
+    A[i + (int64_t)j * lda] = csub(A[i + (int64_t)j * lda], s);
+  }
+}
+
+__global__ void k_zero_upper(double2* A, int64_t lda, int n) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  if (i < n && j < n && j > i) A[i + (int64_t)j * lda] = make_double2(0, 0);
+}
+
+cudaError_t la_zero_upper(double2* A, int64_t lda, int n, cudaStream_t st) {
+  dim3 b(16, 16), g((n + 15) / 16, (n + 15) / 16);
+  k_zero_upper<<<g, b, 0, st>>>(A, lda, n);
+  return cudaGetLastError();
+}
+
+cudaError_t la_cholesky(double2* A, int64_t lda, int n, int* flag, cudaStream_t st) {
+  for (int k0 = 0; k0 < n; k0 += NB) {
+    const int kb = min(NB, n - k0);
+    k_chol_diag<<<1, dim3(32, 32), 0, st>>>(A, lda, k0, kb, flag);
+    const int rest = n - k0 - kb;
+    if (rest > 0) {
+      k_chol_panel<<<(rest + 127) / 128, 128, 0, st>>>(A, lda, n, k0, kb);
+      const int nt = (rest + 31) / 32;
+      k_chol_update<<<dim3(nt, nt), 256, 0, st>>>(A, lda, n, k0, kb);
+    }
+  }
+  // zero the strict upper triangle
+  dim3 zb(16, 16), zg((n + 15) / 16, (n + 15) / 16);
+  k_zero_upper<<<zg, zb, 0, st>>>(A, lda, n);
+  return cudaGetLastError();
+}
+
+// ---- triangular inverse X = L^{-1} (lower) -------------------------------------------
+__global__ void k_transpose(const double2* A, int64_t lda, int n, double2* At) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  if (i < n && j < n) At[j + (int64_t)i * n] = A[i + (int64_t)j * lda];
+}
+
+// one warp per column j of X; Lt holds L row-major (Lt[t + i n] = L[i][t])
+__global__ void k_trinv(const double2* __restrict__ Lt, int n, double2* __restrict__ X, int64_t ldx) {
+  extern __shared__ double2 xs[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int j = blockIdx.x * (blockDim.x >> 5) + warp;
+  if (j >= n) return;
+  double2* x = xs + (int64_t)warp * n;
+  for (int i = lane; i < j; i += 32) X[i + (int64_t)j * ldx] = make_double2(0, 0);
+  if (lane == 0) {
+    const double d = Lt[j + (int64_t)j * n].x;
+    x[j] = make_double2(1.0 / d, 0.0);
+    X[j + (int64_t)j * ldx] = x[j];
+  }
+  __syncwarp();
+  for (int i = j + 1; i < n; ++i) {
+    const double2* row = Lt + (int64_t)i * n;
+    double sr = 0, si = 0;
+    for (int t = j + lane; t < i; t += 32) {
+      const double2 a = row[t], b = x[t];
+      sr += a.x * b.x - a.y * b.y;
+      si += a.x * b.y + a.y * b.x;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      sr += __shfl_down_sync(0xffffffffu, sr, o);
+      si += __shfl_down_sync(0xffffffffu, si, o);
+    }
+    if (lane == 0) {
+      const double d = row[i].x;
+      x[i] = make_double2(-sr / d, -si / d);
+      X[i + (int64_t)j * ldx] = x[i];
+    }
+    __syncwarp();
+  }
+}
+
+cudaError_t la_trinv_lower(const double2* L, int64_t lda, int n, double2* X, int64_t ldx, double2* tmp,
+                           cudaStream_t st) {
+  dim3 b(16, 16), g((n + 15) / 16, (n + 15) / 16);
+  k_transpose<<<g, b, 0, st>>>(L, lda, n, tmp);
+  const int wpb = 4;
+  const size_t sm = sizeof(double2) * (size_t)n * wpb;
+  cudaError_t e = cudaFuncSetAttribute(k_trinv, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e) return e;
+  k_trinv<<<(n + wpb - 1) / wpb, 32 * wpb, sm, st>>>(tmp, n, X, ldx);
+  return cudaGetLastError();
+}
+
+// ---- parallel cyclic Jacobi for Hermitian A (n x n, lda = n) ---------------------------
+struct Rot { double c, s; double2 ph; };  // J = [[c, s], [-s ph, c ph]]
+
+__device__ __forceinline__ void rr_pair(int t, int i, int np, int& p, int& q) {
+  auto pos = [&](int s) { return s == 0 ? 0 : ((s - 1 + t) % (np - 1)) + 1; };
+  p = pos(i);
+  q = pos(np - 1 - i);
+}
+
+__device__ __forceinline__ Rot jac_rot(const double2* A, int n, int p, int q) {
+  Rot r{1.0, 0.0, make_double2(1.0, 0.0)};
+  if (p >= n || q >= n) return r;
+  const double a = A[p + (int64_t)p * n].x, d = A[q + (int64_t)q * n].x;
+  const double2 b = A[p + (int64_t)q * n];
+  const double ab = hypot(b.x, b.y);
+  if (!(ab > 1e-300)) return r;
+  const double tau = (d - a) / (2.0 * ab);
+  const double t = (tau >= 0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
+  r.c = 1.0 / sqrt(1.0 + t * t);
+  r.s = t * r.c;
+  r.ph = make_double2(b.x / ab, -b.y / ab);
+  return r;
+}
+
+__global__ void k_jacobi_round(const double2* __restrict__ Ao, double2* __restrict__ An,
+                               const double2* __restrict__ Vo, double2* __restrict__ Vn, int n, int np, int t) {
+  const int npair = np / 2;
+  const int64_t nblk = (int64_t)npair * npair;
+  const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (idx < nblk) {
+    const int I = (int)(idx % npair), Jx = (int)(idx / npair);
+    int pI, qI, pJ, qJ;
+    rr_pair(t, I, np, pI, qI);
+    rr_pair(t, Jx, np, pJ, qJ);
+    const Rot ri = jac_rot(Ao, n, pI, qI), rj = jac_rot(Ao, n, pJ, qJ);
+    const bool vpI = pI < n, vqI = qI < n, vpJ = pJ < n, vqJ = qJ < n;
+    const double2 z = make_double2(0, 0);
+    const double2 b00 = (vpI && vpJ) ? Ao[pI + (int64_t)pJ * n] : z;
+    const double2 b01 = (vpI && vqJ) ? Ao[pI + (int64_t)qJ * n] : z;
+    const double2 b10 = (vqI && vpJ) ? Ao[qI + (int64_t)pJ * n] : z;
+    const double2 b11 = (vqI && vqJ) ? Ao[qI + (int64_t)qJ * n] : z;
+    // T = blk * J_J ;  J_J = [[c, s], [-s ph, c ph]]
+    const double2 mJ10 = cscale(rj.ph, -rj.s), mJ11 = cscale(rj.ph, rj.c);
+    const double2 t00 = cadd(cscale(b00, rj.c), cmul(b01, mJ10));
+    const double2 t01 = cadd(cscale(b00, rj.s), cmul(b01, mJ11));
+    const double2 t10 = cadd(cscale(b10, rj.c), cmul(b11, mJ10));
+    const double2 t11 = cadd(cscale(b10, rj.s), cmul(b11, mJ11));
+    // N = J_I^H T ; J_I^H = [[c, -s conj(ph)], [s, c conj(ph)]]
+    const double2 h01 = cscale(cconj(ri.ph), -ri.s), h11 = cscale(cconj(ri.ph), ri.c);
+    const double2 n00 = cadd(cscale(t00, ri.c), cmul(h01, t10));
+    const double2 n01 = cadd(cscale(t01, ri.c), cmul(h01, t11));
+    const double2 n10 = cadd(cscale(t00, ri.s), cmul(h11, t10));
+    const double2 n11 = cadd(cscale(t01, ri.s), cmul(h11, t11));
+    if (vpI && vpJ) An[pI + (int64_t)pJ * n] = n00;
+    if (vpI && vqJ) An[pI + (int64_t)qJ * n] = n01;
+    if (vqI && vpJ) An[qI + (int64_t)pJ * n] = n10;
+    if (vqI && vqJ) An[qI + (int64_t)qJ * n] = n11;
+  } else if (idx < nblk + (int64_t)n * npair) {
+    const int64_t k = idx - nblk;
+    const int r = (int)(k % n), Jx = (int)(k / n);
+    int pJ, qJ;
+    rr_pair(t, Jx, np, pJ, qJ);
+    const Rot rj = jac_rot(Ao, n, pJ, qJ);
+    const bool vp = pJ < n, vq = qJ < n;
+    const double2 z = make_double2(0, 0);
+    const double2 vpv = vp ? Vo[r + (int64_t)pJ * n] : z;
+    const double2 vqv = vq ? Vo[r + (int64_t)qJ * n] : z;
+    const double2 mJ10 = cscale(rj.ph, -rj.s), mJ11 = cscale(rj.ph, rj.c);
+    if (vp) Vn[r + (int64_t)pJ * n] = cadd(cscale(vpv, rj.c), cmul(vqv, mJ10));
+    if (vq) Vn[r + (int64_t)qJ * n] = cadd(cscale(vpv, rj.s), cmul(vqv, mJ11));
+  }
+}
+
+__global__ void k_eye(double2* V, int n) {
+  const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (idx >= (int64_t)n * n) return;
+  const int i = (int)(idx % n), j = (int)(idx / n);
+  V[idx] = make_double2(i == j ? 1.0 : 0.0, 0.0);
+}
+
+// out[0] = sum_{i != j} |A_ij|^2, out[1] = sum_i A_ii^2
+__global__ void k_offnorm(const double2* A, int n, double* out) {
+  __shared__ double so[256], sd[256];
+  double o = 0, d = 0;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < (int64_t)n * n;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(idx % n), j = (int)(idx / n);
+    const double2 a = A[idx];
+    if (i == j) d += a.x * a.x; else o += a.x * a.x + a.y * a.y;
+  }
+  so[threadIdx.x] = o; sd[threadIdx.x] = d;
+  __syncthreads();
+  for (int s = 128; s > 0; s >>= 1) {
+    if (threadIdx.x < s) { so[threadIdx.x] += so[threadIdx.x + s]; sd[threadIdx.x] += sd[threadIdx.x + s]; }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) { atomicAdd(out, so[0]); atomicAdd(out + 1, sd[0]); }
+}
+
+// ascending sort of the diagonal with its eigenvectors (rank by counting; ties by index)
+__global__ void k_sort_eig(const double2* A, const double2* V, int n, double* eig, double2* U) {
+  const int i = blockIdx.x;
+  if (i >= n) return;
+  const double li = A[i + (int64_t)i * n].x;
+  __shared__ int rank;
+  if (threadIdx.x == 0) rank = 0;
+  __syncthreads();
+  int r = 0;
+  for (int j = threadIdx.x; j < n; j += blockDim.x) {
+    const double lj = A[j + (int64_t)j * n].x;
+    if (lj < li || (lj == li && j < i)) ++r;
+  }
+  atomicAdd(&rank, r);
+  __syncthreads();
+  const int rk = rank;
+  if (threadIdx.x == 0) eig[rk] = li;
+  for (int k = threadIdx.x; k < n; k += blockDim.x) U[k + (int64_t)rk * n] = V[k + (int64_t)i * n];
+}
+
+int la_jacobi_eigh(double2* A, int n, double2* U, double* eig, double2* ws, double* norms_dev,
+                   cudaStream_t st, int max_sweeps, double tol, int* sweeps_out) {
+  // ws: 3 n*n complex (A copy, V, V copy)
+  double2* A2 = ws;
+  double2* V = ws + (int64_t)n * n;
+  double2* V2 = ws + 2 * (int64_t)n * n;
+  const int64_t nn = (int64_t)n * n;
+  k_eye<<<(unsigned)((nn + 255) / 256), 256, 0, st>>>(V, n);
+  cudaMemcpyAsync(A2, A, sizeof(double2) * nn, cudaMemcpyDeviceToDevice, st);
+  cudaMemcpyAsync(V2, V, sizeof(double2) * nn, cudaMemcpyDeviceToDevice, st);
+  const int np = (n % 2) ? n + 1 : n;
+  const int npair = np / 2;
+  const int64_t work = (int64_t)npair * npair + (int64_t)n * npair;
+  const unsigned nblk = (unsigned)((work + 255) / 256);
+  double2 *Acur = A, *Anext = A2, *Vcur = V, *Vnext = V2;
+  int sweep = 0;
+  bool conv = (n <= 1);
+  double h[2];
+  while (!conv && sweep < max_sweeps) {
+    for (int t = 0; t < np - 1; ++t) {
+      k_jacobi_round<<<nblk, 256, 0, st>>>(Acur, Anext, Vcur, Vnext, n, np, t);
+      double2* x = Acur; Acur = Anext; Anext = x;
+      x = Vcur; Vcur = Vnext; Vnext = x;
+    }
+    ++sweep;
+    cudaMemsetAsync(norms_dev, 0, 2 * sizeof(double), st);
+    k_offnorm<<<64, 256, 0, st>>>(Acur, n, norms_dev);
+    cudaError_t e = cudaMemcpyAsync(h, norms_dev, 2 * sizeof(double), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_status(e, "jacobi");
+    if (h[0] <= tol * tol * (h[0] + h[1])) conv = true;
+  }
+  if (sweeps_out) *sweeps_out = sweep;
+  k_sort_eig<<<n, 128, 0, st>>>(Acur, Vcur, n, eig, U);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_status(e, "jacobi sort");
+  return conv ? PW_OK : set_error(PW_ENOTCONV, "Jacobi eigensolver: %d sweeps without convergence", sweep);
+}
+
+// ---- column reductions ------------------------------------------------------------
+// out[j] = sum_g conj(A[g, j]) B[g, j]
+template <typename T>
+__global__ void k_coldot(const cplx<T>* A, int64_t lda, const cplx<T>* B, int64_t ldb, int npw, double2* out) {
+  const int j = blockIdx.x;
+  const cplx<T>* a = A + (int64_t)j * lda;
+  const cplx<T>* b = B + (int64_t)j * ldb;
+  double sr = 0, si = 0;
+  for (int g = threadIdx.x; g < npw; g += blockDim.x) {
+    const double ax = a[g].x, ay = a[g].y, bx = b[g].x, by = b[g].y;
+    sr += ax * bx + ay * by;
+    si += ax * by - ay * bx;
+  }
+  __shared__ double s1[256], s2[256];
+  s1[threadIdx.x] = sr; s2[threadIdx.x] = si;
+  __syncthreads();
+  for (int s = 128; s > 0; s >>= 1) {
+    if (threadIdx.x < s) { s1[threadIdx.x] += s1[threadIdx.x + s]; s2[threadIdx.x] += s2[threadIdx.x + s]; }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[j] = make_double2(s1[0], s2[0]);
+}
+
+cudaError_t la_coldot(const double2* A, int64_t lda, const double2* B, int64_t ldb, int npw, int m,
+                      double2* out, cudaStream_t st) {
+  if (m <= 0) return cudaSuccess;
+  k_coldot<double><<<m, 256, 0, st>>>(A, lda, B, ldb, npw, out);
+  return cudaGetLastError();
+}
+
+// r_j = || HY_j - eig_j SY_j ||
+__global__ void k_resid(const double2* HY, int64_t ldh, const double2* SY, int64_t lds, int npw, const double* eig,
+                        double* r) {
+  const int j = blockIdx.x;
+  const double l = eig[j];
+  double s = 0;
+  for (int g = threadIdx.x; g < npw; g += blockDim.x) {
+    const double2 h = HY[g + (int64_t)j * ldh], sv = SY[g + (int64_t)j * lds];
+    const double x = h.x - l * sv.x, y = h.y - l * sv.y;
+    s += x * x + y * y;
+  }
+  __shared__ double sh[256];
+  sh[threadIdx.x] = s;
+  __syncthreads();
+  for (int k = 128; k > 0; k >>= 1) {
+    if (threadIdx.x < k) sh[threadIdx.x] += sh[threadIdx.x + k];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) r[j] = sqrt(sh[0]);
+}
+
+cudaError_t la_resid(const double2* HY, int64_t ldh, const double2* SY, int64_t lds, int npw, int m,
+                     const double* eig, double* r, cudaStream_t st) {
+  if (m <= 0) return cudaSuccess;
+  k_resid<<<m, 256, 0, st>>>(HY, ldh, SY, lds, npw, eig, r);
+  return cudaGetLastError();
+}
+
+// rq[j] = Re(num_j) / Re(den_j); mm[0] = min, mm[1] = max
+__global__ void k_rq_minmax(const double2* num, const double2* den, int m, double* rq, double* mm) {
+  __shared__ double smin[256], smax[256];
+  double lo = INFINITY, hi = -INFINITY;
+  for (int j = threadIdx.x; j < m; j += blockDim.x) {
+    const double v = num[j].x / den[j].x;
+    rq[j] = v;
+    lo = fmin(lo, v); hi = fmax(hi, v);
+  }
+  smin[threadIdx.x] = lo; smax[threadIdx.x] = hi;
+  __syncthreads();
+  for (int s = 128; s > 0; s >>= 1) {
+    if (threadIdx.x < s) {
+      smin[threadIdx.x] = fmin(smin[threadIdx.x], smin[threadIdx.x + s]);
+      smax[threadIdx.x] = fmax(smax[threadIdx.x], smax[threadIdx.x + s]);
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) { mm[0] = smin[0]; mm[1] = smax[0]; }
+}
+
+cudaError_t la_rq_minmax(const double2* num, const double2* den, int m, double* rq, double* mm, cudaStream_t st) {
+  k_rq_minmax<<<1, 256, 0, st>>>(num, den, m, rq, mm);
+  return cudaGetLastError();
+}
+
+// ---- Lanczos helpers (one vector) ---------------------------------------------------
+// ab: device array, alpha at ab[2k], beta at ab[2k+1]
+__global__ void k_lz_dot(const double2* v, const double2* w, int n, double* alpha_out) {
+  __shared__ double sh[1024];
+  double s = 0;
+  for (int g = threadIdx.x; g < n; g += blockDim.x) s += v[g].x * w[g].x + v[g].y * w[g].y;
+  sh[threadIdx.x] = s;
+  __syncthreads();
+  for (int k = blockDim.x / 2; k > 0; k >>= 1) {
+    if (threadIdx.x < k) sh[threadIdx.x] += sh[threadIdx.x + k];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *alpha_out = sh[0];
+}
+
+// w <- w - alpha v - beta vprev ; beta_out = ||w|| ; vprev <- v ; v <- w / beta_out
+__global__ void k_lz_update(double2* w, double2* v, double2* vprev, int n, const double* alpha,
+                            const double* beta_prev, double* beta_out) {
+  __shared__ double sh[1024];
+  const double a = *alpha, b = beta_prev ? *beta_prev : 0.0;
+  double s = 0;
+  for (int g = threadIdx.x; g < n; g += blockDim.x) {
+    double2 x = w[g];
+    const double2 vv = v[g], vp = vprev[g];
+    x.x -= a * vv.x + b * vp.x;
+    x.y -= a * vv.y + b * vp.y;
+    w[g] = x;
+    s += x.x * x.x + x.y * x.y;
+  }
+  sh[threadIdx.x] = s;
+  __syncthreads();
+  for (int k = blockDim.x / 2; k > 0; k >>= 1) {
+    if (threadIdx.x < k) sh[threadIdx.x] += sh[threadIdx.x + k];
+    __syncthreads();
+  }
+  const double nb = sqrt(sh[0]);
+  const double inv = nb > 0 ? 1.0 / nb : 0.0;
+  for (int g = threadIdx.x; g < n; g += blockDim.x) {
+    vprev[g] = v[g];
+    v[g] = cscale(w[g], inv);
+  }
+  if (threadIdx.x == 0) *beta_out = nb;
+}
+
+__global__ void k_lz_normalize(const double2* v0, double2* v, double2* vprev, int n) {
+  __shared__ double sh[1024];
+  double s = 0;
+  for (int g = threadIdx.x; g < n; g += blockDim.x) s += v0[g].x * v0[g].x + v0[g].y * v0[g].y;
+  sh[threadIdx.x] = s;
+  __syncthreads();
+  for (int k = blockDim.x / 2; k > 0; k >>= 1) {
+    if (threadIdx.x < k) sh[threadIdx.x] += sh[threadIdx.x + k];
+    __syncthreads();
+  }
+  const double inv = 1.0 / sqrt(sh[0]);
+  for (int g = threadIdx.x; g < n; g += blockDim.x) {
+    v[g] = cscale(v0[g], inv);
+    vprev[g] = make_double2(0, 0);
+  }
+}
+
+// largest eigenvalue of the k x k symmetric tridiagonal (alpha, beta) by Sturm bisection;
+// out[0] = theta_max + |beta_k|, out[1] = theta_max
+__global__ void k_lz_bound(const double* ab, int k, double* out) {
+  if (threadIdx.x != 0) return;
+  double lo = INFINITY, hi = -INFINITY;
+  for (int i = 0; i < k; ++i) {
+    const double a = ab[2 * i];
+    const double r = (i > 0 ? fabs(ab[2 * i - 1]) : 0.0) + (i < k - 1 ? fabs(ab[2 * i + 1]) : 0.0);
+    lo = fmin(lo, a - r);
+    hi = fmax(hi, a + r);
+  }
+  // count of eigenvalues < x
+  for (int it = 0; it < 200; ++it) {
+    const double x = 0.5 * (lo + hi);
+    if (x == lo || x == hi) break;
+    int cnt = 0;
+    double d = 1.0;
+    for (int i = 0; i < k; ++i) {
+      const double b2 = (i > 0) ? ab[2 * i - 1] * ab[2 * i - 1] : 0.0;
+      d = (ab[2 * i] - x) - (i > 0 ? b2 / d : 0.0);
+      if (d == 0.0) d = -1e-300;
+      if (d < 0) ++cnt;
+    }
+    if (cnt == k) hi = x; else lo = x;
+  }
+  out[1] = hi;
+  out[0] = hi + fabs(ab[2 * k - 1]);
+}
+
+cudaError_t la_lanczos(const double2* v0, int n, int steps, double2* v, double2* vprev, double2* w, double* ab,
+                       double* bound, ApplyFn apply, void* ctx, cudaStream_t st) {
+  k_lz_normalize<<<1, 1024, 0, st>>>(v0, v, vprev, n);
+  for (int k = 0; k < steps; ++k) {
+    int s = apply(ctx, v, w);
+    if (s != PW_OK) return cudaErrorUnknown;
+    k_lz_dot<<<1, 1024, 0, st>>>(v, w, n, ab + 2 * k);
+    k_lz_update<<<1, 1024, 0, st>>>(w, v, vprev, n, ab + 2 * k, k > 0 ? ab + 2 * k - 1 : nullptr, ab + 2 * k + 1);
+  }
+  k_lz_bound<<<1, 32, 0, st>>>(ab, steps, bound);
+  return cudaGetLastError();
+}
+
+// ---- conversions ----------------------------------------------------------------
+__global__ void k_c128_to_c64(const double2* a, int64_t lda, float2* b, int64_t ldb, int n, int m) {
+  const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (idx >= (int64_t)n * m) return;
+  const int g = (int)(idx % n), j = (int)(idx / n);
+  const double2 v = a[g + j * lda];
+  b[g + j * ldb] = make_float2((float)v.x, (float)v.y);
+}
+__global__ void k_c64_to_c128(const float2* a, int64_t lda, double2* b, int64_t ldb, int n, int m) {
+  const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (idx >= (int64_t)n * m) return;
+  const int g = (int)(idx % n), j = (int)(idx / n);
+  const float2 v = a[g + j * lda];
+  b[g + j * ldb] = make_double2(v.x, v.y);
+}
+cudaError_t la_to_c64(const double2* a, int64_t lda, float2* b, int64_t ldb, int n, int m, cudaStream_t st) {
+  const int64_t t = (int64_t)n * m;
+  if (t <= 0) return cudaSuccess;
+  k_c128_to_c64<<<(unsigned)((t + 255) / 256), 256, 0, st>>>(a, lda, b, ldb, n, m);
+  return cudaGetLastError();
+}
+cudaError_t la_to_c128(const float2* a, int64_t lda, double2* b, int64_t ldb, int n, int m, cudaStream_t st) {
+  const int64_t t = (int64_t)n * m;
+  if (t <= 0) return cudaSuccess;
+  k_c64_to_c128<<<(unsigned)((t + 255) / 256), 256, 0, st>>>(a, lda, b, ldb, n, m);
+  return cudaGetLastError();
+}
+
+}  // namespace pw

@@ -1,0 +1,863 @@
+// C ABI of the Chebyshev-filtered plane-wave H-apply: context set-up (plane-wave
+// sphere, FFT plans, projectors, Woodbury matrices) and the entry points of pw.h.
+// Host code here only builds index tables, sizes workspaces and sequences
+// kernel launches; every arithmetic step of the path runs in the kernels of
+// fft_local.cu, gemm_simt.cu, la_fp64.cu and setup_kernels.cu.
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <new>
+#include <type_traits>
+
+#include "la.cuh"
+#include "pw_internal.cuh"
+#include "setup.cuh"
+
+namespace pw {
+
+static thread_local char g_err[512] = "";
+
+int set_error(int status, const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof(g_err), fmt, ap);
+  va_end(ap);
+  return status;
+}
+
+int cuda_status(cudaError_t e, const char* where) {
+  if (e == cudaSuccess) return PW_OK;
+  const int s = (e == cudaErrorMemoryAllocation) ? PW_ENOMEM : PW_ECUDA;
+  return set_error(s, "%s: %s", where, cudaGetErrorString(e));
+}
+
+void* ws_get(pw_ctx* c, int slot, size_t bytes, int* status) {
+  if (bytes == 0) bytes = 16;
+  pw_ctx::Buf& b = c->ws[slot];
+  if (b.bytes >= bytes) return b.p;
+  if (b.p) {
+    cudaStreamSynchronize(c->stream);
+    cudaFree(b.p);
+    b.p = nullptr;
+    b.bytes = 0;
+  }
+  cudaError_t e = cudaMalloc(&b.p, bytes);
+  if (e != cudaSuccess) {
+    b.p = nullptr;
+    *status = cuda_status(e, "workspace allocation");
+    return nullptr;
+  }
+  b.bytes = bytes;
+  return b.p;
+}
+
+}  // namespace pw
+
+using namespace pw;
+
+#define PW_TRY(expr)                    \
+  do {                                  \
+    int _s = (expr);                    \
+    if (_s != PW_OK) return _s;         \
+  } while (0)
+#define CU_TRY(expr, where)                                          \
+  do {                                                               \
+    cudaError_t _e = (expr);                                         \
+    if (_e != cudaSuccess) { ctx->poisoned = true; return cuda_status(_e, where); } \
+  } while (0)
+#define WS(ptr, T, slot, count)                                               \
+  T* ptr;                                                                     \
+  do {                                                                        \
+    int _st = PW_OK;                                                          \
+    ptr = (T*)ws_get(ctx, slot, sizeof(T) * (size_t)(count), &_st);           \
+    if (!ptr) return _st;                                                     \
+  } while (0)
+
+namespace {
+
+constexpr double kPi = 3.14159265358979323846264338327950288;
+
+// ---------------------------------------------------------------------------
+// host-side planning
+// ---------------------------------------------------------------------------
+bool factorize(int n, FftDim& d) {
+  d.n = n;
+  d.nst = 0;
+  int m = n;
+  const int order[5] = {8, 4, 5, 3, 2};
+  for (int r : order) {
+    while (m % r == 0 && m > 1) {
+      if (r == 8 && m % 8 != 0) break;
+      if (d.nst >= kMaxStages) return false;
+      d.radix[d.nst++] = r;
+      m /= r;
+    }
+  }
+  if (m != 1 || n < 1) return false;
+  int L = n;
+  for (int s = 0; s < d.nst; ++s) {
+    d.L[s] = L;
+    L /= d.radix[s];
+  }
+  return true;
+}
+
+// position j of a DIF output holds frequency rho(j)
+std::vector<int> digit_reversal(const FftDim& d) {
+  std::vector<int> r(d.n);
+  for (int j = 0; j < d.n; ++j) {
+    int t = j, f = 0, mult = 1, q = d.n;
+    for (int s = 0; s < d.nst; ++s) {
+      q /= d.radix[s];
+      const int m = t / q;
+      t %= q;
+      f += m * mult;
+      mult *= d.radix[s];
+    }
+    r[j] = f;
+  }
+  return r;
+}
+
+void block_structure(const double* A, int n, std::vector<int>& b0, std::vector<int>& bl) {
+  b0.assign(n, 0);
+  bl.assign(n, 0);
+  int s = 0;
+  while (s < n) {
+    int e = s + 1, reach = s;
+    for (int i = s; i < e; ++i) {
+      for (int j = 0; j < n; ++j)
+        if (A[i + (size_t)j * n] != 0.0 || A[j + (size_t)i * n] != 0.0) reach = std::max(reach, j);
+      if (reach + 1 > e) e = reach + 1;
+    }
+    for (int i = s; i < e; ++i) { b0[i] = s; bl[i] = e - s; }
+    s = e;
+  }
+}
+
+void inv3(const double* a, double* out) {  // out = inverse of row-major 3x3
+  const double det = a[0] * (a[4] * a[8] - a[5] * a[7]) - a[1] * (a[3] * a[8] - a[5] * a[6]) +
+                     a[2] * (a[3] * a[7] - a[4] * a[6]);
+  out[0] = (a[4] * a[8] - a[5] * a[7]) / det;
+  out[1] = (a[2] * a[7] - a[1] * a[8]) / det;
+  out[2] = (a[1] * a[5] - a[2] * a[4]) / det;
+  out[3] = (a[5] * a[6] - a[3] * a[8]) / det;
+  out[4] = (a[0] * a[8] - a[2] * a[6]) / det;
+  out[5] = (a[2] * a[3] - a[0] * a[5]) / det;
+  out[6] = (a[3] * a[7] - a[4] * a[6]) / det;
+  out[7] = (a[1] * a[6] - a[0] * a[7]) / det;
+  out[8] = (a[0] * a[4] - a[1] * a[3]) / det;
+}
+
+template <typename X>
+int upload(pw_ctx* ctx, X** dst, const X* src, size_t n) {
+  void* p = nullptr;
+  cudaError_t e = cudaMalloc(&p, sizeof(X) * std::max<size_t>(n, 1));
+  if (e != cudaSuccess) return cuda_status(e, "context allocation");
+  ctx->owned.push_back(p);
+  *dst = (X*)p;
+  if (src && n) {
+    e = cudaMemcpy(p, src, sizeof(X) * n, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_status(e, "context upload");
+  }
+  return PW_OK;
+}
+
+int nsplit_for(int m, int n, int k) {
+  const int tiles = ((m + 63) / 64) * ((n + 63) / 64);
+  int s = (2 * 152 + tiles - 1) / tiles;
+  s = std::min(s, std::max(1, k / 512));
+  return std::max(1, std::min(s, 64));
+}
+
+template <typename T> struct Prec;
+template <> struct Prec<double> {
+  static const double2* P(const pw_ctx* c) { return c->P64; }
+  static const double* D(const pw_ctx* c) { return c->D64; }
+  static const double* kin(const pw_ctx* c) { return c->kin64; }
+  static const double* vp(const pw_ctx* c) { return c->vperm64; }
+  static const double2* tw(const pw_ctx* c) { return c->tw64; }
+  static const double2* K(const pw_ctx* c) { return c->K64; }
+  static const double2* E(const pw_ctx* c) { return c->E64; }
+};
+template <> struct Prec<float> {
+  static const float2* P(const pw_ctx* c) { return c->P32; }
+  static const float* D(const pw_ctx* c) { return c->D32; }
+  static const float* kin(const pw_ctx* c) { return c->kin32; }
+  static const float* vp(const pw_ctx* c) { return c->vperm32; }
+  static const float2* tw(const pw_ctx* c) { return c->tw32; }
+  static const float2* K(const pw_ctx* c) { return c->K32; }
+  static const float2* E(const pw_ctx* c) { return c->E32; }
+};
+
+template <typename T>
+Epi<T> epi(int mode, cplx<T>* out, int64_t ldo, T alpha = 1) {
+  Epi<T> e;
+  e.mode = mode; e.out = out; e.ldo = ldo; e.alpha = alpha; e.beta = 0; e.shift = 0;
+  e.yk = nullptr; e.ykm1 = nullptr; e.ldy = 0; e.ldy2 = 0;
+  return e;
+}
+
+int band_batch(const pw_ctx* ctx, int nband) {
+  // keep a batch's half-box planes around 256 MB
+  const size_t per = (size_t)ctx->sp.nplane * ctx->n[1] * ctx->n[2] * 16;
+  int bb = (int)std::max<size_t>(1, ((size_t)256 << 20) / std::max<size_t>(per, 1));
+  return std::max(1, std::min(bb, nband));
+}
+
+// ---------------------------------------------------------------------------
+// H-apply (HX / HX_SX of Sec. 3.3)
+// ---------------------------------------------------------------------------
+template <typename T>
+int apply_impl(pw_ctx* ctx, const cplx<T>* psi, int64_t ldpsi, int nband, cplx<T>* hpsi, cplx<T>* spsi,
+               int64_t ldout) {
+  using C = cplx<T>;
+  const int npw = ctx->npw, np = ctx->nproj;
+  const cudaStream_t st = ctx->stream;
+  const int bb = band_batch(ctx, nband);
+  const int64_t hb_bs = (int64_t)ctx->sp.nplane * ctx->n[1] * ctx->n[2];
+  WS(hb, C, WS_HB, hb_bs * bb);
+  WS(Cm, C, WS_C, (size_t)np * nband);
+  WS(Z, C, WS_Z, (size_t)np * nband);
+  const int ns = nsplit_for(np, nband, npw);
+  WS(sp, C, WS_SPLIT, (size_t)ns * np * nband);
+  CU_TRY(launch_local_apply<T>(ctx->plan, Prec<T>::tw(ctx), ctx->sp, Prec<T>::vp(ctx), Prec<T>::kin(ctx), psi,
+                               ldpsi, nband, hpsi, ldout, hb, bb, st), "local apply");
+  if (np > 0) {
+    CU_TRY(launch_cgemm<T>(1, 0, np, nband, npw, Prec<T>::P(ctx), npw, psi, ldpsi, epi<T>(EPI_STORE, Cm, np), ns,
+                           sp, st), "projection gemm");
+    CU_TRY(launch_dblock<T>(np, nband, Prec<T>::D(ctx), ctx->blk0, ctx->blklen, Cm, np, Z, np, st), "D block");
+    CU_TRY(launch_cgemm<T>(0, 0, npw, nband, np, Prec<T>::P(ctx), npw, Z, np, epi<T>(EPI_ACCUM, hpsi, ldout), 1,
+                           sp, st), "back-projection gemm");
+  }
+  if (spsi) {
+    CU_TRY(cudaMemcpy2DAsync(spsi, sizeof(C) * ldout, psi, sizeof(C) * ldpsi, sizeof(C) * npw, nband,
+                             cudaMemcpyDeviceToDevice, st), "copy S psi");
+    if constexpr (std::is_same<T, double>::value) {
+      if (ctx->has_q && np > 0) {
+        CU_TRY(launch_dblock<double>(np, nband, ctx->Q64, ctx->qblk0, ctx->qblklen, Cm, np, Z, np, st), "Q block");
+        CU_TRY(launch_cgemm<T>(0, 0, npw, nband, np, Prec<T>::P(ctx), npw, Z, np, epi<T>(EPI_ACCUM, spsi, ldout), 1,
+                               sp, st), "overlap gemm");
+      }
+    } else {
+      if (ctx->has_q && np > 0) return set_error(PW_EUNSUPPORTED, "S apply is FP64 only");
+    }
+  }
+  return PW_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Chebyshev filter (Alg. 7 / Alg. 12)
+// ---------------------------------------------------------------------------
+template <typename T>
+int filter_impl(pw_ctx* ctx, cplx<T>* psi, int64_t ldpsi, int nband, int degree, double a, double b) {
+  using C = cplx<T>;
+  if (degree <= 0 || nband <= 0) return PW_OK;
+  if (!(b > a)) return set_error(PW_EINVAL, "filter interval needs upper > lower (a=%g, b=%g)", a, b);
+  const int npw = ctx->npw, np = ctx->nproj;
+  const cudaStream_t st = ctx->stream;
+  const int bb = band_batch(ctx, nband);
+  const int64_t hb_bs = (int64_t)ctx->sp.nplane * ctx->n[1] * ctx->n[2];
+  WS(hb, C, WS_HB, hb_bs * bb);
+  WS(Cm, C, WS_C, (size_t)np * nband);
+  WS(Z, C, WS_Z, (size_t)np * nband);
+  WS(Cw, C, WS_CW, (size_t)np * nband);
+  const int ns = nsplit_for(np, nband, npw);
+  WS(spl, C, WS_SPLIT, (size_t)ns * np * nband);
+  WS(Y1, C, WS_Y1, (size_t)npw * nband);
+  WS(Y2, C, WS_Y2, (size_t)npw * nband);
+  C* buf[3] = {psi, Y1, Y2};
+  const int64_t ld[3] = {ldpsi, npw, npw};
+  const double cc = 0.5 * (b + a), e = 0.5 * (b - a);
+  for (int k = 0; k < degree; ++k) {
+    C* cur = buf[k % 3];
+    C* prev = buf[(k + 2) % 3];
+    C* dst = buf[(k + 1) % 3];
+    const int64_t ldc = ld[k % 3], ldp = ld[(k + 2) % 3], ldd = ld[(k + 1) % 3];
+    const T alpha = (T)(k == 0 ? 1.0 / e : 2.0 / e);
+    // W = (T + V) Y_k
+    CU_TRY(launch_local_apply<T>(ctx->plan, Prec<T>::tw(ctx), ctx->sp, Prec<T>::vp(ctx), Prec<T>::kin(ctx), cur,
+                                 ldc, nband, dst, ldd, hb, bb, st), "filter local");
+    Epi<T> ce = epi<T>(EPI_CHEB, dst, ldd, alpha);
+    ce.beta = (T)1;
+    ce.shift = (T)cc;
+    ce.yk = cur;
+    ce.ldy = ldc;
+    ce.ykm1 = (k == 0) ? nullptr : prev;
+    ce.ldy2 = ldp;
+    if (np > 0) {
+      // C = P^dagger Y_k
+      CU_TRY(launch_cgemm<T>(1, 0, np, nband, npw, Prec<T>::P(ctx), npw, cur, ldc, epi<T>(EPI_STORE, Cm, np), ns,
+                             spl, st), "filter projection");
+      if (!ctx->has_q) {
+        CU_TRY(launch_dblock<T>(np, nband, Prec<T>::D(ctx), ctx->blk0, ctx->blklen, Cm, np, Z, np, st), "filter D");
+      } else {
+        // S^-1 H Y = W + P [E C - K P^dagger W],  E = (I - K P^dagger P) D  (Woodbury, Sec. 3.3)
+        CU_TRY(launch_cgemm<T>(1, 0, np, nband, npw, Prec<T>::P(ctx), npw, dst, ldd, epi<T>(EPI_STORE, Cw, np), ns,
+                               spl, st), "filter projection of W");
+        CU_TRY(launch_cgemm<T>(0, 0, np, nband, np, Prec<T>::E(ctx), np, Cm, np, epi<T>(EPI_STORE, Z, np), 1, spl,
+                               st), "filter E C");
+        CU_TRY(launch_cgemm<T>(0, 0, np, nband, np, Prec<T>::K(ctx), np, Cw, np, epi<T>(EPI_ACCUM, Z, np, (T)-1), 1,
+                               spl, st), "filter K Cw");
+      }
+      CU_TRY(launch_cgemm<T>(0, 0, npw, nband, np, Prec<T>::P(ctx), npw, Z, np, ce, 1, spl, st), "filter recurrence");
+    } else {
+      CU_TRY(launch_cgemm<T>(0, 0, npw, nband, 0, Prec<T>::P(ctx), npw, Z, 1, ce, 1, spl, st), "filter recurrence");
+    }
+  }
+  if (degree % 3 != 0) {
+    CU_TRY(cudaMemcpy2DAsync(psi, sizeof(C) * ldpsi, buf[degree % 3], sizeof(C) * npw, sizeof(C) * npw, nband,
+                             cudaMemcpyDeviceToDevice, st), "filter copy-out");
+  }
+  return PW_OK;
+}
+
+// ---------------------------------------------------------------------------
+// S-Ortho (Alg. 9) and Rayleigh-Ritz (Alg. 5), FP64
+// ---------------------------------------------------------------------------
+// G = Y^H SY (herm.), L = chol(G), Linv = L^-1.  flag set on failure.
+int gram_chol(pw_ctx* ctx, const double2* Y, int64_t ldy, const double2* SY, int64_t lds, int m, double2* G,
+              double2* Linv, double2* tmp, int* flag) {
+  const cudaStream_t st = ctx->stream;
+  const int ns = nsplit_for(m, m, ctx->npw);
+  WS(spl, double2, WS_SPLIT, (size_t)ns * m * m);
+  CU_TRY(launch_cgemm<double>(1, 0, m, m, ctx->npw, Y, ldy, SY, lds, epi<double>(EPI_STORE, G, m), ns, spl, st),
+         "gram");
+  CU_TRY(la_herm_sym(G, m, m, st), "gram sym");
+  CU_TRY(la_cholesky(G, m, m, flag, st), "cholesky");
+  CU_TRY(la_trinv_lower(G, m, m, Linv, m, tmp, st), "triangular inverse");
+  return PW_OK;
+}
+
+int check_flag(pw_ctx* ctx, int* flag_dev, const char* what) {
+  int h = 0;
+  CU_TRY(cudaMemcpyAsync(&h, flag_dev, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream), "flag copy");
+  CU_TRY(cudaStreamSynchronize(ctx->stream), "flag sync");
+  if (h) return set_error(PW_ENOTSPD, "%s: matrix is not positive definite", what);
+  return PW_OK;
+}
+
+int rr_impl(pw_ctx* ctx, double2* Y, int64_t ldy, int m, double2* hpsi_out, double* eig_h, double* resid_h) {
+  const int npw = ctx->npw;
+  const cudaStream_t st = ctx->stream;
+  WS(HY, double2, WS_HY, (size_t)npw * m);
+  WS(SYb, double2, WS_SY, (size_t)npw * m);
+  WS(ROT, double2, WS_ROT, (size_t)npw * m);
+  WS(G, double2, WS_GRAM, (size_t)m * m);
+  WS(G2, double2, WS_GRAM2, (size_t)m * m);
+  WS(Linv, double2, WS_LINV, (size_t)m * m);
+  WS(tmp, double2, WS_TMP, (size_t)m * m);
+  WS(U, double2, WS_U, (size_t)m * m);
+  WS(jac, double2, WS_JAC, (size_t)3 * m * m);
+  WS(eig, double, WS_EIG, (size_t)2 * m + 4);
+  WS(scal, int, WS_SCAL, 16);
+  double* norms = eig + 2 * m;
+  double* resid = eig + m;
+  CU_TRY(cudaMemsetAsync(scal, 0, 16 * sizeof(int), st), "flag reset");
+  // two passes of Cholesky-QR in the S metric
+  for (int rep = 0; rep < 2; ++rep) {
+    const double2* SY = Y;
+    int64_t lds = ldy;
+    if (ctx->has_q) {
+      PW_TRY(apply_impl<double>(ctx, Y, ldy, m, HY, SYb, npw));  // HY is scratch here
+      SY = SYb;
+      lds = npw;
+    }
+    PW_TRY(gram_chol(ctx, Y, ldy, SY, lds, m, G, Linv, tmp, scal));
+    // Y <- Y L^{-dagger}
+    CU_TRY(launch_cgemm<double>(0, 1, npw, m, m, Y, ldy, Linv, m, epi<double>(EPI_STORE, ROT, npw), 1, nullptr, st),
+           "s-ortho rotate");
+    CU_TRY(cudaMemcpy2DAsync(Y, sizeof(double2) * ldy, ROT, sizeof(double2) * npw, sizeof(double2) * npw, m,
+                             cudaMemcpyDeviceToDevice, st), "s-ortho copy");
+  }
+  PW_TRY(check_flag(ctx, scal, "S-Ortho Cholesky"));
+  // H Psi, S Psi
+  PW_TRY(apply_impl<double>(ctx, Y, ldy, m, HY, ctx->has_q ? SYb : nullptr, npw));
+  const double2* SY = ctx->has_q ? SYb : Y;
+  const int64_t lds = ctx->has_q ? npw : ldy;
+  const int ns = nsplit_for(m, m, npw);
+  WS(spl, double2, WS_SPLIT, (size_t)ns * m * m);
+  // H_Psi = Psi^dagger (H Psi) -> G2
+  CU_TRY(launch_cgemm<double>(1, 0, m, m, npw, Y, ldy, HY, npw, epi<double>(EPI_STORE, G2, m), ns, spl, st), "H gram");
+  CU_TRY(la_herm_sym(G2, m, m, st), "H gram sym");
+  // S_Psi -> G, Cholesky, Linv
+  PW_TRY(gram_chol(ctx, Y, ldy, SY, lds, m, G, Linv, tmp, scal));
+  // Cm = Linv H_Psi Linv^dagger
+  CU_TRY(launch_cgemm<double>(0, 1, m, m, m, G2, m, Linv, m, epi<double>(EPI_STORE, tmp, m), 1, nullptr, st), "reduce 1");
+  CU_TRY(launch_cgemm<double>(0, 0, m, m, m, Linv, m, tmp, m, epi<double>(EPI_STORE, G, m), 1, nullptr, st), "reduce 2");
+  CU_TRY(la_herm_sym(G, m, m, st), "reduced sym");
+  PW_TRY(check_flag(ctx, scal, "Rayleigh-Ritz Cholesky"));
+  int sweeps = 0;
+  PW_TRY(la_jacobi_eigh(G, m, U, eig, jac, norms, st, 40, 1e-15, &sweeps));
+  // X = Linv^dagger U  -> tmp
+  CU_TRY(launch_cgemm<double>(1, 0, m, m, m, Linv, m, U, m, epi<double>(EPI_STORE, tmp, m), 1, nullptr, st), "back-transform");
+  // rotate Y, HY, SY
+  CU_TRY(launch_cgemm<double>(0, 0, npw, m, m, Y, ldy, tmp, m, epi<double>(EPI_STORE, ROT, npw), 1, nullptr, st), "rotate Y");
+  CU_TRY(cudaMemcpy2DAsync(Y, sizeof(double2) * ldy, ROT, sizeof(double2) * npw, sizeof(double2) * npw, m,
+                           cudaMemcpyDeviceToDevice, st), "rotate copy");
+  CU_TRY(launch_cgemm<double>(0, 0, npw, m, m, HY, npw, tmp, m, epi<double>(EPI_STORE, ROT, npw), 1, nullptr, st), "rotate HY");
+  double2* HYr = ROT;
+  const double2* SYr = Y;
+  int64_t ldsr = ldy;
+  if (ctx->has_q) {
+    CU_TRY(launch_cgemm<double>(0, 0, npw, m, m, SYb, npw, tmp, m, epi<double>(EPI_STORE, HY, npw), 1, nullptr, st), "rotate SY");
+    SYr = HY;
+    ldsr = npw;
+  }
+  CU_TRY(la_resid(HYr, npw, SYr, ldsr, npw, m, eig, resid, st), "residuals");
+  if (hpsi_out)
+    CU_TRY(cudaMemcpy2DAsync(hpsi_out, sizeof(double2) * ldy, HYr, sizeof(double2) * npw, sizeof(double2) * npw, m,
+                             cudaMemcpyDeviceToDevice, st), "copy H psi");
+  if (eig_h) CU_TRY(cudaMemcpyAsync(eig_h, eig, sizeof(double) * m, cudaMemcpyDeviceToHost, st), "eig copy");
+  if (resid_h) CU_TRY(cudaMemcpyAsync(resid_h, resid, sizeof(double) * m, cudaMemcpyDeviceToHost, st), "resid copy");
+  CU_TRY(cudaStreamSynchronize(st), "rr sync");
+  return PW_OK;
+}
+
+struct LzCtx { pw_ctx* ctx; };
+int lz_apply(void* p, const double2* v, double2* w) {
+  pw_ctx* ctx = ((LzCtx*)p)->ctx;
+  return apply_impl<double>(ctx, v, ctx->npw, 1, w, nullptr, ctx->npw);
+}
+
+int bounds_impl(pw_ctx* ctx, const double2* psi, int64_t ld, int nband, int steps, const double2* v0,
+                double* rq_min, double* rq_max, double* upper) {
+  const int npw = ctx->npw;
+  const cudaStream_t st = ctx->stream;
+  WS(rq, double2, WS_RQ, (size_t)3 * nband + 8);
+  if (nband > 0) {
+    WS(HY, double2, WS_HY, (size_t)npw * nband);
+    WS(SYb, double2, WS_SY, (size_t)npw * nband);
+    PW_TRY(apply_impl<double>(ctx, psi, ld, nband, HY, ctx->has_q ? SYb : nullptr, npw));
+    const double2* SY = ctx->has_q ? SYb : psi;
+    const int64_t lds = ctx->has_q ? npw : ld;
+    CU_TRY(la_coldot(psi, ld, HY, npw, npw, nband, rq, st), "rq num");
+    CU_TRY(la_coldot(psi, ld, SY, lds, npw, nband, rq + nband, st), "rq den");
+    double* mm = (double*)(rq + 2 * nband);
+    double* rqv = (double*)(rq + 2 * nband + 1);
+    CU_TRY(la_rq_minmax(rq, rq + nband, nband, rqv, mm, st), "rq minmax");
+    double h[2];
+    CU_TRY(cudaMemcpyAsync(h, mm, 2 * sizeof(double), cudaMemcpyDeviceToHost, st), "rq copy");
+    CU_TRY(cudaStreamSynchronize(st), "rq sync");
+    if (rq_min) *rq_min = h[0];
+    if (rq_max) *rq_max = h[1];
+  }
+  if (steps > 0) {
+    if (!v0) return set_error(PW_EINVAL, "Lanczos start vector is NULL");
+    WS(lz, double2, WS_LZ, (size_t)3 * npw + 2 * steps + 8);
+    double* ab = (double*)(lz + 3 * npw);
+    double* bound = ab + 2 * steps;
+    LzCtx lc{ctx};
+    CU_TRY(la_lanczos(v0, npw, steps, lz, lz + npw, lz + 2 * npw, ab, bound, lz_apply, &lc, st), "lanczos");
+    double h[2];
+    CU_TRY(cudaMemcpyAsync(h, bound, 2 * sizeof(double), cudaMemcpyDeviceToHost, st), "bound copy");
+    CU_TRY(cudaStreamSynchronize(st), "bound sync");
+    if (upper) *upper = h[0];
+  }
+  return PW_OK;
+}
+
+int check_ctx(pw_ctx* ctx) {
+  if (!ctx) return set_error(PW_EINVAL, "NULL context");
+  if (ctx->poisoned) return set_error(PW_ECUDA, "context poisoned by an earlier CUDA error");
+  return PW_OK;
+}
+
+int check_block(pw_ctx* ctx, const void* p, int64_t ld, int nband) {
+  if (nband < 0) return set_error(PW_EINVAL, "nband < 0");
+  if (nband > 0 && !p) return set_error(PW_EINVAL, "NULL block");
+  if (ld < ctx->npw) return set_error(PW_EINVAL, "ld (%lld) < npw (%d)", (long long)ld, ctx->npw);
+  return PW_OK;
+}
+
+// ---------------------------------------------------------------------------
+// context creation
+// ---------------------------------------------------------------------------
+int create_impl(const pw_problem_desc* d, void* stream, pw_ctx** out) {
+  if (!d || !out) return set_error(PW_EINVAL, "NULL argument");
+  *out = nullptr;
+  if (!d->vloc) return set_error(PW_EINVAL, "vloc is NULL");
+  if (d->natom < 0 || d->nchan < 0 || d->nchan > kMaxChan) return set_error(PW_EINVAL, "bad natom/nchan");
+  if (d->natom > 0 && (!d->tau || !d->sigma || !d->D)) return set_error(PW_EINVAL, "tau/sigma/D missing");
+  if (!(d->ecut > 0)) return set_error(PW_EINVAL, "ecut must be positive");
+  pw_ctx* ctx = new (std::nothrow) pw_ctx();
+  if (!ctx) return set_error(PW_ENOMEM, "host allocation");
+  *out = ctx;  // destroyed by the caller-facing wrapper on failure
+  ctx->stream = (cudaStream_t)stream;
+  memcpy(ctx->lattice, d->lattice, sizeof(ctx->lattice));
+  memcpy(ctx->kpt, d->kpt, sizeof(ctx->kpt));
+  ctx->ecut = d->ecut;
+  for (int i = 0; i < 3; ++i) {
+    ctx->n[i] = d->box[i];
+    if (!factorize(d->box[i], ctx->plan.d[i]))
+      return set_error(PW_EUNSUPPORTED, "box length %d does not factor into 2, 3, 5", d->box[i]);
+    ctx->plan.n[i] = d->box[i];
+  }
+  // reciprocal vectors, rows b_i
+  double Ainv[9], B[9];
+  inv3(d->lattice, Ainv);
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) B[i * 3 + j] = 2.0 * kPi * Ainv[j * 3 + i];
+  double kc[3];
+  for (int c = 0; c < 3; ++c) kc[c] = d->kpt[0] * B[c] + d->kpt[1] * B[3 + c] + d->kpt[2] * B[6 + c];
+  const double gmax = sqrt(2.0 * d->ecut);
+  const double kn = sqrt(kc[0] * kc[0] + kc[1] * kc[1] + kc[2] * kc[2]);
+  int lim[3];
+  for (int i = 0; i < 3; ++i) {
+    const double an = sqrt(d->lattice[3 * i] * d->lattice[3 * i] + d->lattice[3 * i + 1] * d->lattice[3 * i + 1] +
+                           d->lattice[3 * i + 2] * d->lattice[3 * i + 2]);
+    lim[i] = (int)ceil((gmax + kn) * an / (2.0 * kPi)) + 1;
+  }
+  // sphere, already in ascending (h, k, l) order by construction of the loops
+  std::vector<int> pl_h, pl_row0, rk, rl0, rcnt, rg0;
+  int mn[3] = {1 << 30, 1 << 30, 1 << 30}, mx[3] = {-(1 << 30), -(1 << 30), -(1 << 30)};
+  for (int h = -lim[0]; h <= lim[0]; ++h) {
+    bool plane_open = false;
+    for (int k = -lim[1]; k <= lim[1]; ++k) {
+      int run_start = -1, last_l = 0;
+      for (int l = -lim[2]; l <= lim[2]; ++l) {
+        double q[3];
+        for (int c = 0; c < 3; ++c) q[c] = h * B[c] + k * B[3 + c] + l * B[6 + c] + kc[c];
+        const double t = 0.5 * (q[0] * q[0] + q[1] * q[1] + q[2] * q[2]);
+        if (t <= d->ecut) {
+          if (!plane_open) {
+            pl_h.push_back(h);
+            pl_row0.push_back((int)rk.size());
+            plane_open = true;
+          }
+          if (run_start < 0) {
+            run_start = l;
+            rk.push_back(k);
+            rl0.push_back(l);
+            rcnt.push_back(0);
+            rg0.push_back(ctx->npw);
+          } else if (l != last_l + 1) {
+            return set_error(PW_EINVAL, "sphere row is not a contiguous run");
+          }
+          last_l = l;
+          rcnt.back()++;
+          ctx->miller.push_back(h);
+          ctx->miller.push_back(k);
+          ctx->miller.push_back(l);
+          ctx->kin_h.push_back(t);
+          const int m3[3] = {h, k, l};
+          for (int c = 0; c < 3; ++c) { mn[c] = std::min(mn[c], m3[c]); mx[c] = std::max(mx[c], m3[c]); }
+          ctx->npw++;
+        }
+      }
+    }
+  }
+  pl_row0.push_back((int)rk.size());
+  if (ctx->npw == 0) return set_error(PW_EINVAL, "empty plane-wave sphere");
+  for (int c = 0; c < 3; ++c)
+    if (mx[c] - mn[c] >= d->box[c]) return set_error(PW_EINVAL, "plane-wave sphere does not fit in the FFT box");
+  ctx->sp.npw = ctx->npw;
+  ctx->sp.nplane = (int)pl_h.size();
+  ctx->sp.nrow = (int)rk.size();
+  ctx->sp.max_rows = 0;
+  for (int p = 0; p < ctx->sp.nplane; ++p) ctx->sp.max_rows = std::max(ctx->sp.max_rows, pl_row0[p + 1] - pl_row0[p]);
+  int* dv;
+  PW_TRY(upload(ctx, &dv, pl_h.data(), pl_h.size())); ctx->sp.plane_h = dv;
+  PW_TRY(upload(ctx, &dv, pl_row0.data(), pl_row0.size())); ctx->sp.plane_row0 = dv;
+  PW_TRY(upload(ctx, &dv, rk.data(), rk.size())); ctx->sp.row_k = dv;
+  PW_TRY(upload(ctx, &dv, rl0.data(), rl0.size())); ctx->sp.row_l0 = dv;
+  PW_TRY(upload(ctx, &dv, rcnt.data(), rcnt.size())); ctx->sp.row_cnt = dv;
+  PW_TRY(upload(ctx, &dv, rg0.data(), rg0.size())); ctx->sp.row_g0 = dv;
+  int* miller_dev;
+  PW_TRY(upload(ctx, &miller_dev, ctx->miller.data(), ctx->miller.size()));
+  PW_TRY(upload(ctx, &ctx->kin64, ctx->kin_h.data(), ctx->kin_h.size()));
+  std::vector<float> kin32(ctx->kin_h.begin(), ctx->kin_h.end());
+  PW_TRY(upload(ctx, &ctx->kin32, kin32.data(), kin32.size()));
+  // twiddles e^{-2 pi i j m / L}
+  std::vector<double2> tw;
+  for (int dd = 0; dd < 3; ++dd) {
+    FftDim& f = ctx->plan.d[dd];
+    for (int s = 0; s < f.nst; ++s) {
+      f.tw_off[s] = (int)tw.size();
+      const int L = f.L[s], r = f.radix[s], q = L / r;
+      for (int j = 0; j < q; ++j)
+        for (int m = 1; m < r; ++m) {
+          const long jm = ((long)j * m) % L;
+          const double ang = -2.0 * kPi * (double)jm / (double)L;
+          tw.push_back(make_double2(cos(ang), sin(ang)));
+        }
+    }
+  }
+  std::vector<float2> tw32(tw.size());
+  for (size_t i = 0; i < tw.size(); ++i) tw32[i] = make_float2((float)tw[i].x, (float)tw[i].y);
+  PW_TRY(upload(ctx, &ctx->tw64, tw.data(), tw.size()));
+  PW_TRY(upload(ctx, &ctx->tw32, tw32.data(), tw32.size()));
+  for (int dd = 0; dd < 3; ++dd) {
+    std::vector<int> r = digit_reversal(ctx->plan.d[dd]);
+    PW_TRY(upload(ctx, &ctx->rho_perm[dd], r.data(), r.size()));
+  }
+  const cudaStream_t st = ctx->stream;
+  // permuted potential, scaled by 1 / n1n2n3 (the forward DFT normalisation)
+  const size_t ntot = (size_t)d->box[0] * d->box[1] * d->box[2];
+  double* vraw;
+  PW_TRY(upload(ctx, &vraw, d->vloc, ntot));
+  PW_TRY(upload(ctx, &ctx->vperm64, (const double*)nullptr, ntot));
+  PW_TRY(upload(ctx, &ctx->vperm32, (const float*)nullptr, ntot));
+  CU_TRY(setup_vperm(vraw, ctx->n, ctx->rho_perm, 1.0 / (double)ntot, ctx->vperm64, ctx->vperm32, st), "vperm");
+  // projectors
+  ctx->natom = d->natom;
+  ctx->nchan = d->nchan;
+  ctx->nproj = d->natom * d->nchan * 4;
+  const int np = ctx->nproj;
+  PW_TRY(upload(ctx, &ctx->P64, (const double2*)nullptr, (size_t)ctx->npw * std::max(np, 1)));
+  PW_TRY(upload(ctx, &ctx->P32, (const float2*)nullptr, (size_t)ctx->npw * std::max(np, 1)));
+  if (np > 0) {
+    ProjParams pp;
+    memcpy(pp.B, B, sizeof(B));
+    memcpy(pp.kred, d->kpt, sizeof(pp.kred));
+    double* tau_dev;
+    PW_TRY(upload(ctx, &tau_dev, d->tau, (size_t)3 * d->natom));
+    pp.tau = tau_dev;
+    pp.nchan = d->nchan;
+    for (int c = 0; c < d->nchan; ++c) pp.sigma[c] = d->sigma[c];
+    CU_TRY(setup_projectors(ctx->npw, miller_dev, pp, d->natom, ctx->P64, st), "projectors");
+    CU_TRY(cast_z2c(ctx->P64, ctx->P32, (int64_t)ctx->npw * np, st), "P cast");
+  }
+  // D and its block structure
+  std::vector<double> Dh(std::max(np * np, 1), 0.0);
+  if (np > 0) memcpy(Dh.data(), d->D, sizeof(double) * np * np);
+  std::vector<int> b0, bl;
+  block_structure(Dh.data(), np, b0, bl);
+  PW_TRY(upload(ctx, &ctx->D64, Dh.data(), Dh.size()));
+  PW_TRY(upload(ctx, &ctx->D32, (const float*)nullptr, Dh.size()));
+  CU_TRY(cast_d2f(ctx->D64, ctx->D32, (int64_t)Dh.size(), st), "D cast");
+  PW_TRY(upload(ctx, &ctx->blk0, b0.data(), std::max<size_t>(b0.size(), 1)));
+  PW_TRY(upload(ctx, &ctx->blklen, bl.data(), std::max<size_t>(bl.size(), 1)));
+  // Woodbury matrices for S^-1 (Sec. 3.3): K = (Q^-1 + P^dagger P)^-1, E = (I - K P^dagger P) D
+  ctx->has_q = (d->Q != nullptr) && np > 0;
+  if (ctx->has_q) {
+    std::vector<int> qb0, qbl;
+    block_structure(d->Q, np, qb0, qbl);
+    PW_TRY(upload(ctx, &ctx->Q64, d->Q, (size_t)np * np));
+    PW_TRY(upload(ctx, &ctx->qblk0, qb0.data(), qb0.size()));
+    PW_TRY(upload(ctx, &ctx->qblklen, qbl.data(), qbl.size()));
+    const size_t nn = (size_t)np * np;
+    double2 *Bm, *Qz, *Li, *tmp, *Dz;
+    PW_TRY(upload(ctx, &ctx->K64, (const double2*)nullptr, nn));
+    PW_TRY(upload(ctx, &ctx->E64, (const double2*)nullptr, nn));
+    PW_TRY(upload(ctx, &ctx->K32, (const float2*)nullptr, nn));
+    PW_TRY(upload(ctx, &ctx->E32, (const float2*)nullptr, nn));
+    PW_TRY(upload(ctx, &Bm, (const double2*)nullptr, nn));
+    PW_TRY(upload(ctx, &Qz, (const double2*)nullptr, nn));
+    PW_TRY(upload(ctx, &Li, (const double2*)nullptr, nn));
+    PW_TRY(upload(ctx, &tmp, (const double2*)nullptr, nn));
+    PW_TRY(upload(ctx, &Dz, (const double2*)nullptr, nn));
+    int* flag;
+    PW_TRY(upload(ctx, &flag, (const int*)nullptr, 1));
+    CU_TRY(cudaMemsetAsync(flag, 0, sizeof(int), st), "flag");
+    const int ns = nsplit_for(np, np, ctx->npw);
+    double2* spl;
+    PW_TRY(upload(ctx, &spl, (const double2*)nullptr, (size_t)ns * nn));
+    // B = P^dagger P
+    CU_TRY(launch_cgemm<double>(1, 0, np, np, ctx->npw, ctx->P64, ctx->npw, ctx->P64, ctx->npw,
+                                epi<double>(EPI_STORE, Bm, np), ns, spl, st), "P^dagger P");
+    CU_TRY(la_herm_sym(Bm, np, np, st), "B sym");
+    // Q^-1 = L^-dagger L^-1
+    CU_TRY(cast_r2z(ctx->Q64, Qz, (int64_t)nn, st), "Q cast");
+    CU_TRY(la_cholesky(Qz, np, np, flag, st), "Q cholesky");
+    CU_TRY(la_trinv_lower(Qz, np, np, Li, np, tmp, st), "Q trinv");
+    // Mm = Bm + Li^dagger Li  (accumulated into Bm copy `tmp`)
+    CU_TRY(cudaMemcpyAsync(tmp, Bm, sizeof(double2) * nn, cudaMemcpyDeviceToDevice, st), "copy B");
+    CU_TRY(launch_cgemm<double>(1, 0, np, np, np, Li, np, Li, np, epi<double>(EPI_ACCUM, tmp, np), 1, nullptr, st),
+           "Q inverse");
+    CU_TRY(la_herm_sym(tmp, np, np, st), "M sym");
+    CU_TRY(la_cholesky(tmp, np, np, flag, st), "M cholesky");
+    CU_TRY(la_trinv_lower(tmp, np, np, Li, np, Qz, st), "M trinv");
+    CU_TRY(launch_cgemm<double>(1, 0, np, np, np, Li, np, Li, np, epi<double>(EPI_STORE, ctx->K64, np), 1, nullptr,
+                                st), "K");
+    // E = D - K (B D)
+    CU_TRY(cast_r2z(ctx->D64, Dz, (int64_t)nn, st), "D cast");
+    CU_TRY(launch_cgemm<double>(0, 0, np, np, np, Bm, np, Dz, np, epi<double>(EPI_STORE, tmp, np), 1, nullptr, st),
+           "B D");
+    CU_TRY(cudaMemcpyAsync(ctx->E64, Dz, sizeof(double2) * nn, cudaMemcpyDeviceToDevice, st), "copy D");
+    CU_TRY(launch_cgemm<double>(0, 0, np, np, np, ctx->K64, np, tmp, np, epi<double>(EPI_ACCUM, ctx->E64, np, -1.0),
+                                1, nullptr, st), "E");
+    CU_TRY(cast_z2c(ctx->K64, ctx->K32, (int64_t)nn, st), "K cast");
+    CU_TRY(cast_z2c(ctx->E64, ctx->E32, (int64_t)nn, st), "E cast");
+    PW_TRY(check_flag(ctx, flag, "Woodbury set-up (Q or Q^-1 + P^dagger P)"));
+  }
+  CU_TRY(cudaStreamSynchronize(st), "context set-up");
+  return PW_OK;
+}
+
+void destroy_impl(pw_ctx* ctx) {
+  if (!ctx) return;
+  cudaStreamSynchronize(ctx->stream);
+  for (void* p : ctx->owned) cudaFree(p);
+  for (auto& b : ctx->ws)
+    if (b.p) cudaFree(b.p);
+  delete ctx;
+}
+
+}  // namespace
+
+// ===========================================================================
+// exported C ABI
+// ===========================================================================
+extern "C" {
+
+PW_API int pw_ctx_create(const pw_problem_desc* desc, void* stream, pw_ctx** out) {
+  pw_ctx* ctx = nullptr;
+  int s = create_impl(desc, stream, &ctx);
+  if (s != PW_OK) {
+    destroy_impl(ctx);
+    if (out) *out = nullptr;
+    return s;
+  }
+  *out = ctx;
+  return PW_OK;
+}
+
+PW_API int pw_ctx_destroy(pw_ctx* ctx) {
+  destroy_impl(ctx);
+  return PW_OK;
+}
+
+PW_API int pw_ctx_set_stream(pw_ctx* ctx, void* stream) {
+  PW_TRY(check_ctx(ctx));
+  ctx->stream = (cudaStream_t)stream;
+  return PW_OK;
+}
+
+PW_API int pw_ctx_info(const pw_ctx* ctx, int* npw, int* nproj) {
+  if (!ctx) return set_error(PW_EINVAL, "NULL context");
+  if (npw) *npw = ctx->npw;
+  if (nproj) *nproj = ctx->nproj;
+  return PW_OK;
+}
+
+PW_API int pw_ctx_gvectors(const pw_ctx* ctx, int32_t* miller, double* kinetic) {
+  if (!ctx) return set_error(PW_EINVAL, "NULL context");
+  if (miller) memcpy(miller, ctx->miller.data(), sizeof(int32_t) * ctx->miller.size());
+  if (kinetic) memcpy(kinetic, ctx->kin_h.data(), sizeof(double) * ctx->kin_h.size());
+  return PW_OK;
+}
+
+PW_API int pw_ctx_projectors(const pw_ctx* ctx_c, void* P_out) {
+  pw_ctx* ctx = const_cast<pw_ctx*>(ctx_c);
+  PW_TRY(check_ctx(ctx));
+  if (!P_out) return set_error(PW_EINVAL, "NULL output");
+  CU_TRY(cudaMemcpyAsync(P_out, ctx->P64, sizeof(double2) * (size_t)ctx->npw * ctx->nproj, cudaMemcpyDeviceToDevice,
+                         ctx->stream), "projector copy");
+  return PW_OK;
+}
+
+PW_API int pw_hamiltonian_apply(pw_ctx* ctx, const void* psi, int64_t ldpsi, int nband, void* hpsi, void* spsi,
+                                int64_t ldout, int precision) {
+  PW_TRY(check_ctx(ctx));
+  PW_TRY(check_block(ctx, psi, ldpsi, nband));
+  PW_TRY(check_block(ctx, hpsi, ldout, nband));
+  if (nband == 0) return PW_OK;
+  if (psi == hpsi || (spsi && psi == spsi)) return set_error(PW_EINVAL, "psi aliases an output");
+  if (precision == PW_FP64)
+    return apply_impl<double>(ctx, (const double2*)psi, ldpsi, nband, (double2*)hpsi, (double2*)spsi, ldout);
+  if (precision == PW_MIXED) {
+    if (spsi && ctx->has_q) return set_error(PW_EUNSUPPORTED, "S psi in mixed precision");
+    return apply_impl<float>(ctx, (const float2*)psi, ldpsi, nband, (float2*)hpsi, (float2*)spsi, ldout);
+  }
+  return set_error(PW_EINVAL, "unknown precision %d", precision);
+}
+
+PW_API int pw_spectrum_bounds(pw_ctx* ctx, const void* psi, int64_t ld, int nband, int lanczos_steps, const void* v0,
+                              double* rq_min, double* rq_max, double* upper) {
+  PW_TRY(check_ctx(ctx));
+  PW_TRY(check_block(ctx, psi, ld, nband));
+  if (lanczos_steps < 0) return set_error(PW_EINVAL, "lanczos_steps < 0");
+  return bounds_impl(ctx, (const double2*)psi, ld, nband, lanczos_steps, (const double2*)v0, rq_min, rq_max, upper);
+}
+
+PW_API int pw_chebyshev_filter(pw_ctx* ctx, void* psi, int64_t ldpsi, int nband, int degree, double a, double b,
+                               int precision) {
+  PW_TRY(check_ctx(ctx));
+  PW_TRY(check_block(ctx, psi, ldpsi, nband));
+  if (degree < 0) return set_error(PW_EINVAL, "degree < 0");
+  if (precision == PW_FP64) return filter_impl<double>(ctx, (double2*)psi, ldpsi, nband, degree, a, b);
+  if (precision == PW_MIXED) return filter_impl<float>(ctx, (float2*)psi, ldpsi, nband, degree, a, b);
+  return set_error(PW_EINVAL, "unknown precision %d", precision);
+}
+
+PW_API int pw_rayleigh_ritz(pw_ctx* ctx, void* psi, int64_t ldpsi, int nband, void* hpsi, double* eig,
+                            double* resid) {
+  PW_TRY(check_ctx(ctx));
+  PW_TRY(check_block(ctx, psi, ldpsi, nband));
+  if (nband == 0) return PW_OK;
+  if (nband > ctx->npw) return set_error(PW_EINVAL, "more bands than plane waves");
+  return rr_impl(ctx, (double2*)psi, ldpsi, nband, (double2*)hpsi, eig, resid);
+}
+
+PW_API int pw_chebfi_solve(pw_ctx* ctx, void* psi_v, int64_t ldpsi, int nband, int degree, int cycles,
+                           int lanczos_steps, const void* v0, int precision, double* eig, double* resid,
+                           double* bounds) {
+  PW_TRY(check_ctx(ctx));
+  PW_TRY(check_block(ctx, psi_v, ldpsi, nband));
+  if (nband == 0) return PW_OK;
+  if (!eig) return set_error(PW_EINVAL, "eig is NULL");
+  if (precision != PW_FP64 && precision != PW_MIXED) return set_error(PW_EINVAL, "unknown precision");
+  double2* psi = (double2*)psi_v;
+  double rqmin = 0, a = 0, upper = 0;
+  PW_TRY(bounds_impl(ctx, psi, ldpsi, nband, lanczos_steps, (const double2*)v0, &rqmin, &a, &upper));
+  if (bounds) { bounds[0] = upper; bounds[1] = a; }
+  for (int c = 0; c < cycles; ++c) {
+    if (precision == PW_FP64) {
+      PW_TRY(filter_impl<double>(ctx, psi, ldpsi, nband, degree, a, upper));
+    } else {
+      WS(y32, float2, WS_Y32, (size_t)ctx->npw * nband);
+      CU_TRY(la_to_c64(psi, ldpsi, y32, ctx->npw, ctx->npw, nband, ctx->stream), "to c64");
+      PW_TRY(filter_impl<float>(ctx, y32, ctx->npw, nband, degree, a, upper));
+      CU_TRY(la_to_c128(y32, ctx->npw, psi, ldpsi, ctx->npw, nband, ctx->stream), "to c128");
+    }
+    PW_TRY(rr_impl(ctx, psi, ldpsi, nband, nullptr, eig, resid));
+    a = eig[nband - 1];
+  }
+  return PW_OK;
+}
+
+PW_API int pw_density_grad(pw_ctx* ctx, const void* a, const void* b, int64_t ld, int nband, const double* w,
+                           double* out, int accumulate) {
+  PW_TRY(check_ctx(ctx));
+  PW_TRY(check_block(ctx, a, ld, nband));
+  if (!out) return set_error(PW_EINVAL, "NULL output grid");
+  if (nband > 0 && !w) return set_error(PW_EINVAL, "NULL weights");
+  const cudaStream_t st = ctx->stream;
+  const size_t ntot = (size_t)ctx->n[0] * ctx->n[1] * ctx->n[2];
+  WS(den, double, WS_DEN, ntot + (size_t)nband + 8);
+  double* wd = den + ntot;
+  CU_TRY(cudaMemsetAsync(den, 0, sizeof(double) * ntot, st), "density reset");
+  if (nband > 0) {
+    CU_TRY(cudaMemcpyAsync(wd, w, sizeof(double) * nband, cudaMemcpyHostToDevice, st), "weights");
+    const int bb = std::max(1, band_batch(ctx, nband) / 2);
+    const int64_t hb_bs = (int64_t)ctx->sp.nplane * ctx->n[1] * ctx->n[2];
+    WS(hb, double2, WS_HB, hb_bs * bb * 2);
+    CU_TRY(launch_density<double>(ctx->plan, ctx->tw64, ctx->sp, (const double2*)a, (const double2*)b, ld, nband, wd,
+                                  den, hb, bb, st), "density");
+  }
+  CU_TRY(setup_unperm(den, ctx->n, ctx->rho_perm, out, accumulate, st), "density unpermute");
+  CU_TRY(cudaStreamSynchronize(st), "density sync");
+  return PW_OK;
+}
+
+PW_API const char* pw_strerror(int status) {
+  switch (status) {
+    case PW_OK: return "ok";
+    case PW_EINVAL: return "invalid argument";
+    case PW_ENOMEM: return "out of device memory";
+    case PW_ECUDA: return "CUDA error";
+    case PW_ENOTSPD: return "matrix not positive definite";
+    case PW_ETIMEDOUT: return "device wait timed out";
+    case PW_ENOTCONV: return "eigensolver did not converge";
+    case PW_EUNSUPPORTED: return "unsupported";
+    default: return "unknown status";
+  }
+}
+
+PW_API const char* pw_last_error(void) { return g_err; }
+
+}  // extern "C"

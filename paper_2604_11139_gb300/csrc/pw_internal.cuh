@@ -1,0 +1,180 @@
+// Internal declarations shared by the CUDA translation units of libpwcheb.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/pw.h"
+
+namespace pw {
+
+// ---------------------------------------------------------------------------
+// complex helpers (interleaved re/im, double2 / float2)
+// ---------------------------------------------------------------------------
+template <typename T> struct CT;
+template <> struct CT<double> { using type = double2; };
+template <> struct CT<float> { using type = float2; };
+template <typename T> using cplx = typename CT<T>::type;
+
+template <typename C> __host__ __device__ __forceinline__ C mk(decltype(C{}.x) re, decltype(C{}.x) im) {
+  C c; c.x = re; c.y = im; return c;
+}
+__host__ __device__ __forceinline__ double2 cadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__host__ __device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__host__ __device__ __forceinline__ double2 csub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
+__host__ __device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__host__ __device__ __forceinline__ double2 cmul(double2 a, double2 b) {
+  return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__host__ __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+  return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+// conj(a) * b
+__host__ __device__ __forceinline__ double2 cmulc(double2 a, double2 b) {
+  return make_double2(a.x * b.x + a.y * b.y, a.x * b.y - a.y * b.x);
+}
+__host__ __device__ __forceinline__ float2 cmulc(float2 a, float2 b) {
+  return make_float2(a.x * b.x + a.y * b.y, a.x * b.y - a.y * b.x);
+}
+__host__ __device__ __forceinline__ double2 cscale(double2 a, double s) { return make_double2(a.x * s, a.y * s); }
+__host__ __device__ __forceinline__ float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
+__host__ __device__ __forceinline__ double2 cconj(double2 a) { return make_double2(a.x, -a.y); }
+__host__ __device__ __forceinline__ float2 cconj(float2 a) { return make_float2(a.x, -a.y); }
+// multiply by s*i (s = +1 or -1)
+template <int S> __host__ __device__ __forceinline__ double2 cmuli(double2 a) {
+  return make_double2(-S * a.y, S * a.x);
+}
+template <int S> __host__ __device__ __forceinline__ float2 cmuli(float2 a) {
+  return make_float2(-S * a.y, S * a.x);
+}
+template <typename C> __host__ __device__ __forceinline__ C czero() { C c; c.x = 0; c.y = 0; return c; }
+
+// ---------------------------------------------------------------------------
+// FFT plan: one mixed-radix in-place plan per box dimension.  Inverse
+// transforms run decimation-in-frequency (natural -> digit-reversed order),
+// forward transforms decimation-in-time with the stages reversed
+// (digit-reversed -> natural), so no permutation pass is ever needed; the
+// potential grid is stored permuted instead.
+// ---------------------------------------------------------------------------
+constexpr int kMaxStages = 8;
+struct FftDim {
+  int n, nst;
+  int radix[kMaxStages];
+  int L[kMaxStages];      // block length at each stage (n, n/r1, ...)
+  int tw_off[kMaxStages]; // offset of the stage's twiddles in the table
+};
+struct FftPlan {
+  int n[3];
+  FftDim d[3];
+};
+
+// plane-wave sphere decomposition: planes (fixed h) -> rows (fixed h,k) -> runs of l
+struct SphereDev {
+  int npw, nplane, nrow, max_rows;
+  const int* plane_h;     // [nplane] Miller h
+  const int* plane_row0;  // [nplane+1]
+  const int* row_k;       // [nrow]
+  const int* row_l0;      // [nrow] first l of the run
+  const int* row_cnt;     // [nrow]
+  const int* row_g0;      // [nrow] sphere index of the run's first element
+};
+
+// epilogue applied by the local-potential exit pass and by the GEMMs
+enum EpiMode {
+  EPI_STORE = 0,   // out = alpha * v
+  EPI_ACCUM = 1,   // out = out + alpha * v
+  EPI_CHEB = 2,    // out = alpha * (out + v - shift * yk) - beta * ykm1   (out holds W)
+  EPI_KIN = 3      // out = kin * y + v  (local pass only)
+};
+
+template <typename T> struct Epi {
+  int mode;
+  cplx<T>* out;
+  int64_t ldo;
+  T alpha, beta, shift;
+  const cplx<T>* yk;
+  const cplx<T>* ykm1;
+  int64_t ldy, ldy2;
+};
+
+// ---------------------------------------------------------------------------
+// launchers (defined in the kernel translation units)
+// ---------------------------------------------------------------------------
+template <typename T>
+cudaError_t launch_local_apply(const FftPlan& plan, const cplx<T>* tw, const SphereDev& sp,
+                               const T* vperm, const T* kin, const cplx<T>* psi, int64_t ldpsi,
+                               int nband, cplx<T>* out, int64_t ldout, cplx<T>* hb, int band_batch,
+                               cudaStream_t st);
+
+template <typename T>
+cudaError_t launch_density(const FftPlan& plan, const cplx<T>* tw, const SphereDev& sp,
+                           const cplx<T>* a, const cplx<T>* b, int64_t ld, int nband, const T* w_dev,
+                           double* out_perm, cplx<T>* hb, int band_batch, cudaStream_t st);
+
+// op(A) is M x K, op(B) is K x N; ta/tb: 0 = as stored (column-major), 1 = conjugate transpose.
+// nsplit > 1 splits K and reduces through `ws` (nsplit*M*N complex) before the epilogue.
+template <typename T>
+cudaError_t launch_cgemm(int ta, int tb, int M, int N, int K, const cplx<T>* A, int64_t lda,
+                         const cplx<T>* B, int64_t ldb, const Epi<T>& epi, int nsplit, cplx<T>* ws,
+                         cudaStream_t st);
+
+// real block-diagonal (or dense) D times complex C: Z = D C (nproj x nband)
+template <typename T>
+cudaError_t launch_dblock(int nproj, int nband, const T* D, const int* blk0, const int* blklen,
+                          const cplx<T>* Cm, int64_t ldc, cplx<T>* Z, int64_t ldz, cudaStream_t st);
+
+}  // namespace pw
+
+// the context (opaque to C callers)
+struct pw_ctx {
+  cudaStream_t stream = nullptr;
+  int n[3] = {0, 0, 0};
+  int npw = 0, nproj = 0, natom = 0, nchan = 0;
+  bool has_q = false;
+  double lattice[9], kpt[3], ecut = 0;
+  std::vector<int> miller;     // 3*npw
+  std::vector<double> kin_h;   // npw
+  pw::FftPlan plan;
+  pw::SphereDev sp;
+  // device memory owned by the context
+  std::vector<void*> owned;
+  double2* tw64 = nullptr;
+  float2* tw32 = nullptr;
+  double* kin64 = nullptr;
+  float* kin32 = nullptr;
+  double* vperm64 = nullptr;
+  float* vperm32 = nullptr;
+  int* rho_perm[3] = {nullptr, nullptr, nullptr};  // digit-reversal maps per dimension
+  double2* P64 = nullptr;   // npw x nproj
+  float2* P32 = nullptr;
+  double* D64 = nullptr;    // nproj x nproj column-major
+  float* D32 = nullptr;
+  int* blk0 = nullptr;      // per projector: first index of its D block
+  int* blklen = nullptr;
+  double* Q64 = nullptr;
+  int* qblk0 = nullptr;     // per projector: first index of its Q block
+  int* qblklen = nullptr;
+  double2* K64 = nullptr;   // Woodbury K = (Q^-1 + P^dagger P)^-1
+  double2* E64 = nullptr;   // E = (I - K P^dagger P) D
+  float2* K32 = nullptr;
+  float2* E32 = nullptr;
+  // grow-only workspaces
+  struct Buf { void* p = nullptr; size_t bytes = 0; };
+  Buf ws[32];
+  bool poisoned = false;
+};
+
+namespace pw {
+enum WsSlot {
+  WS_HB = 0, WS_C, WS_Z, WS_SPLIT, WS_Y1, WS_Y2, WS_CW,      // H-apply and filter
+  WS_HY, WS_SY, WS_ROT, WS_Y32,                              // Rayleigh-Ritz / solve
+  WS_GRAM, WS_GRAM2, WS_LINV, WS_TMP, WS_U, WS_JAC, WS_EIG,  // subspace matrices
+  WS_LZ, WS_RQ, WS_DEN, WS_SCAL, WS_NUM
+};
+void* ws_get(pw_ctx* c, int slot, size_t bytes, int* status);
+int set_error(int status, const char* fmt, ...);
+int cuda_status(cudaError_t e, const char* where);
+}  // namespace pw

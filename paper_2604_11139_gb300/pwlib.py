@@ -1,0 +1,281 @@
+"""Thin ctypes binding of libpwcheb (include/pw.h).
+
+Argument marshalling only: every step runs in the CUDA library.  Wave-function
+blocks are torch CUDA tensors of shape (M, ld), complex128 (PW_FP64) or
+complex64 (PW_MIXED), C-contiguous rows, i.e. the column-major N x M block of
+the C ABI with band j at row j.  Importing this module never falls back to any
+other implementation: if the library cannot be built or loaded, it raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional
+
+import numpy as np
+
+from . import build as _build
+
+PW_FP64 = 0
+PW_MIXED = 1
+
+STATUS = {0: "PW_OK", -1: "PW_EINVAL", -2: "PW_ENOMEM", -3: "PW_ECUDA", -4: "PW_ENOTSPD",
+          -5: "PW_ETIMEDOUT", -6: "PW_ENOTCONV", -7: "PW_EUNSUPPORTED"}
+
+# every function declared in include/pw.h
+EXPORTS = ("pw_ctx_create", "pw_ctx_destroy", "pw_ctx_set_stream", "pw_ctx_info", "pw_ctx_gvectors",
+           "pw_ctx_projectors", "pw_hamiltonian_apply", "pw_spectrum_bounds", "pw_chebyshev_filter",
+           "pw_rayleigh_ritz", "pw_chebfi_solve", "pw_density_grad", "pw_strerror", "pw_last_error")
+
+
+class PWError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class _Desc(ctypes.Structure):
+    _fields_ = [("lattice", ctypes.c_double * 9), ("kpt", ctypes.c_double * 3), ("ecut", ctypes.c_double),
+                ("box", ctypes.c_int * 3), ("vloc", ctypes.POINTER(ctypes.c_double)), ("natom", ctypes.c_int),
+                ("tau", ctypes.POINTER(ctypes.c_double)), ("nchan", ctypes.c_int),
+                ("sigma", ctypes.POINTER(ctypes.c_double)), ("D", ctypes.POINTER(ctypes.c_double)),
+                ("Q", ctypes.POINTER(ctypes.c_double))]
+
+
+_LIB = None
+
+
+def load(path: Optional[str] = None):
+    """Loads (building first if needed) the in-tree library; raises if impossible."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    if path is None:
+        path = _build.lib_path()
+        if not os.path.exists(path) or os.environ.get("PW_REBUILD"):
+            path = _build.build()
+    lib = ctypes.CDLL(path)
+    vp, i64, ci, cd = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_double
+    pd = ctypes.POINTER(ctypes.c_double)
+    lib.pw_ctx_create.argtypes = [ctypes.POINTER(_Desc), vp, ctypes.POINTER(vp)]
+    lib.pw_ctx_destroy.argtypes = [vp]
+    lib.pw_ctx_set_stream.argtypes = [vp, vp]
+    lib.pw_ctx_info.argtypes = [vp, ctypes.POINTER(ci), ctypes.POINTER(ci)]
+    lib.pw_ctx_gvectors.argtypes = [vp, ctypes.POINTER(ctypes.c_int32), pd]
+    lib.pw_ctx_projectors.argtypes = [vp, vp]
+    lib.pw_hamiltonian_apply.argtypes = [vp, vp, i64, ci, vp, vp, i64, ci]
+    lib.pw_spectrum_bounds.argtypes = [vp, vp, i64, ci, ci, vp, pd, pd, pd]
+    lib.pw_chebyshev_filter.argtypes = [vp, vp, i64, ci, ci, cd, cd, ci]
+    lib.pw_rayleigh_ritz.argtypes = [vp, vp, i64, ci, vp, pd, pd]
+    lib.pw_chebfi_solve.argtypes = [vp, vp, i64, ci, ci, ci, ci, vp, ci, pd, pd, pd]
+    lib.pw_density_grad.argtypes = [vp, vp, vp, i64, ci, pd, vp, ci]
+    lib.pw_strerror.restype = ctypes.c_char_p
+    lib.pw_strerror.argtypes = [ci]
+    lib.pw_last_error.restype = ctypes.c_char_p
+    for name in EXPORTS:
+        f = getattr(lib, name)
+        if f.restype is None or f.restype is ctypes.c_int:
+            if name not in ("pw_strerror", "pw_last_error"):
+                f.restype = ctypes.c_int
+    _LIB = lib
+    return lib
+
+
+def _check(status: int):
+    if status != 0:
+        raise PWError(status, load().pw_last_error().decode(errors="replace"))
+
+
+def _dptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _block(t, dtype, name):
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name}: expected a CUDA tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name}: expected {dtype}, got {t.dtype}")
+    if t.dim() == 1:
+        t = t.unsqueeze(0)
+    if t.dim() != 2 or t.stride(1) != 1:
+        raise ValueError(f"{name}: expected a (bands, ld) tensor with unit stride along plane waves")
+    return t, t.shape[0], t.stride(0) if t.shape[0] > 1 else t.shape[1]
+
+
+def _dtype(precision):
+    import torch
+    return torch.complex128 if precision == PW_FP64 else torch.complex64
+
+
+class Context:
+    """One k-point problem (pw_ctx): sphere, FFT plans, projectors, Woodbury matrices."""
+
+    def __init__(self, lattice, kpt, ecut, box, vloc, tau, sigmas, D, Q=None, stream=None):
+        import torch
+        lib = load()
+        self._keep = []
+        lat = np.ascontiguousarray(np.asarray(lattice, dtype=np.float64).reshape(9))
+        d = _Desc()
+        d.lattice[:] = list(lat)
+        d.kpt[:] = list(np.asarray(kpt, dtype=np.float64).reshape(3))
+        d.ecut = float(ecut)
+        d.box[:] = [int(b) for b in box]
+        vloc = np.ascontiguousarray(np.asarray(vloc, dtype=np.float64))
+        if vloc.size != int(np.prod(box)):
+            raise ValueError("vloc size does not match the box")
+        tau = np.ascontiguousarray(np.asarray(tau, dtype=np.float64).reshape(-1, 3))
+        sig = np.ascontiguousarray(np.asarray(sigmas, dtype=np.float64).reshape(-1))
+        D = np.asfortranarray(np.asarray(D, dtype=np.float64))
+        self._keep += [vloc, tau, sig, D]
+        d.vloc = _dptr(vloc)
+        d.natom = tau.shape[0]
+        d.tau = _dptr(tau)
+        d.nchan = sig.shape[0]
+        d.sigma = _dptr(sig)
+        d.D = _dptr(D)
+        if Q is not None:
+            Qa = np.asfortranarray(np.asarray(Q, dtype=np.float64))
+            self._keep.append(Qa)
+            d.Q = _dptr(Qa)
+        else:
+            d.Q = ctypes.POINTER(ctypes.c_double)()
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self.stream = stream
+        h = ctypes.c_void_p()
+        _check(lib.pw_ctx_create(ctypes.byref(d), ctypes.c_void_p(stream.cuda_stream), ctypes.byref(h)))
+        self._h = h
+        npw, nproj = ctypes.c_int(), ctypes.c_int()
+        _check(lib.pw_ctx_info(h, ctypes.byref(npw), ctypes.byref(nproj)))
+        self.npw, self.nproj = npw.value, nproj.value
+        self.box = tuple(int(b) for b in box)
+        self.has_q = Q is not None
+
+    @classmethod
+    def from_problem(cls, prob, kpt=None, ecut=None, stream=None):
+        return cls(prob.lattice, prob.kpt if kpt is None else kpt, prob.ecut if ecut is None else ecut, prob.box,
+                   prob.vloc, prob.tau, prob.sigmas, prob.D, prob.Q, stream=stream)
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            load().pw_ctx_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def _sync_stream(self):
+        import torch
+        cur = torch.cuda.current_stream()
+        if cur.cuda_stream != self.stream.cuda_stream:
+            self.stream.wait_stream(cur)
+
+    # -- queries --------------------------------------------------------------------
+    def gvectors(self):
+        miller = np.zeros((self.npw, 3), dtype=np.int32)
+        kin = np.zeros(self.npw, dtype=np.float64)
+        _check(load().pw_ctx_gvectors(self._h, miller.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), _dptr(kin)))
+        return miller, kin
+
+    def projectors(self):
+        import torch
+        P = torch.empty((self.nproj, self.npw), dtype=torch.complex128, device="cuda")
+        _check(load().pw_ctx_projectors(self._h, ctypes.c_void_p(P.data_ptr())))
+        torch.cuda.synchronize()
+        return P  # row i = projector column i
+
+    # -- the path -------------------------------------------------------------------
+    def hamiltonian_apply(self, psi, hpsi, spsi=None, precision=PW_FP64):
+        dt = _dtype(precision)
+        psi, m, ld = _block(psi, dt, "psi")
+        hpsi, m2, ldo = _block(hpsi, dt, "hpsi")
+        sp = None
+        if spsi is not None:
+            spsi, m3, lds = _block(spsi, dt, "spsi")
+            if lds != ldo or m3 < m:
+                raise ValueError("spsi must match hpsi's layout")
+            sp = ctypes.c_void_p(spsi.data_ptr())
+        if m2 < m:
+            raise ValueError("hpsi has fewer bands than psi")
+        self._sync_stream()
+        _check(load().pw_hamiltonian_apply(self._h, ctypes.c_void_p(psi.data_ptr()), ld, m,
+                                           ctypes.c_void_p(hpsi.data_ptr()), sp, ldo, precision))
+
+    def spectrum_bounds(self, psi=None, lanczos_steps=10, v0=None):
+        import torch
+        m, ld, p = 0, self.npw, None
+        if psi is not None:
+            psi, m, ld = _block(psi, torch.complex128, "psi")
+            p = ctypes.c_void_p(psi.data_ptr())
+        vp = None
+        if lanczos_steps > 0:
+            v0, _, _ = _block(v0, torch.complex128, "v0")
+            vp = ctypes.c_void_p(v0.data_ptr())
+        lo, hi, up = ctypes.c_double(np.nan), ctypes.c_double(np.nan), ctypes.c_double(np.nan)
+        self._sync_stream()
+        _check(load().pw_spectrum_bounds(self._h, p, ld, m, lanczos_steps, vp, ctypes.byref(lo), ctypes.byref(hi),
+                                         ctypes.byref(up)))
+        return lo.value, hi.value, up.value
+
+    def chebyshev_filter(self, psi, degree, a, b, precision=PW_FP64):
+        psi, m, ld = _block(psi, _dtype(precision), "psi")
+        self._sync_stream()
+        _check(load().pw_chebyshev_filter(self._h, ctypes.c_void_p(psi.data_ptr()), ld, m, int(degree), float(a),
+                                          float(b), precision))
+
+    def rayleigh_ritz(self, psi, hpsi=None):
+        import torch
+        psi, m, ld = _block(psi, torch.complex128, "psi")
+        hp = None
+        if hpsi is not None:
+            hpsi, _, ldh = _block(hpsi, torch.complex128, "hpsi")
+            if ldh != ld:
+                raise ValueError("hpsi must have psi's leading dimension")
+            hp = ctypes.c_void_p(hpsi.data_ptr())
+        eig = np.zeros(m)
+        res = np.zeros(m)
+        self._sync_stream()
+        _check(load().pw_rayleigh_ritz(self._h, ctypes.c_void_p(psi.data_ptr()), ld, m, hp, _dptr(eig), _dptr(res)))
+        return eig, res
+
+    def chebfi_solve(self, psi, degree, cycles, v0, lanczos_steps=10, precision=PW_FP64):
+        import torch
+        psi, m, ld = _block(psi, torch.complex128, "psi")
+        v0, _, _ = _block(v0, torch.complex128, "v0")
+        eig = np.zeros(m)
+        res = np.zeros(m)
+        bnd = np.zeros(2)
+        self._sync_stream()
+        _check(load().pw_chebfi_solve(self._h, ctypes.c_void_p(psi.data_ptr()), ld, m, int(degree), int(cycles),
+                                      int(lanczos_steps), ctypes.c_void_p(v0.data_ptr()), precision, _dptr(eig),
+                                      _dptr(res), _dptr(bnd)))
+        return eig, res, bnd
+
+    def density_grad(self, a, w, b=None, out=None, accumulate=False):
+        import torch
+        a, m, ld = _block(a, torch.complex128, "a")
+        bp = None
+        if b is not None:
+            b, mb, ldb = _block(b, torch.complex128, "b")
+            if ldb != ld or mb < m:
+                raise ValueError("b must match a's layout")
+            bp = ctypes.c_void_p(b.data_ptr())
+        if out is None:
+            out = torch.zeros(self.box, dtype=torch.float64, device="cuda")
+        w = np.ascontiguousarray(np.asarray(w, dtype=np.float64).reshape(-1))
+        if w.shape[0] < m:
+            raise ValueError("need one weight per band")
+        self._sync_stream()
+        _check(load().pw_density_grad(self._h, ctypes.c_void_p(a.data_ptr()), bp, ld, m, _dptr(w),
+                                      ctypes.c_void_p(out.data_ptr()), 1 if accumulate else 0))
+        return out

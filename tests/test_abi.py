@@ -1,0 +1,41 @@
+"""CPU checks of the C-ABI library: it builds for sm_103a, loads, and exports every
+function include/pw.h declares (no compute calls: no GPU here)."""
+import ctypes
+import os
+import re
+
+from paper_2604_11139_gb300 import build as B
+from paper_2604_11139_gb300 import pwlib
+
+HDR = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include")
+
+
+def declared():
+    names = set()
+    for f in os.listdir(HDR):
+        if f.endswith(".h"):
+            txt = open(os.path.join(HDR, f)).read()
+            names |= set(re.findall(r"PW_API\s+[\w\s\*]+?\b(pw_\w+)\s*\(", txt))
+    return names
+
+
+def test_library_builds_and_exports_every_declared_symbol():
+    path = B.build()
+    assert os.path.exists(path)
+    lib = ctypes.CDLL(path)
+    names = declared()
+    assert {"pw_ctx_create", "pw_hamiltonian_apply", "pw_chebyshev_filter", "pw_rayleigh_ritz",
+            "pw_density_grad"} <= names
+    for n in sorted(names):
+        assert hasattr(lib, n), n
+    assert names == set(pwlib.EXPORTS)
+
+
+def test_status_strings_without_gpu():
+    lib = pwlib.load()
+    assert lib.pw_strerror(0) == b"ok"
+    assert lib.pw_strerror(-4) == b"matrix not positive definite"
+    # a NULL descriptor is rejected on the host before any CUDA call
+    h = ctypes.c_void_p()
+    assert lib.pw_ctx_create(None, None, ctypes.byref(h)) == -1
+    assert b"NULL" in lib.pw_last_error()
