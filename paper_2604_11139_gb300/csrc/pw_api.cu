@@ -517,7 +517,8 @@ int create_impl(const pw_problem_desc* d, void* stream, pw_ctx** out) {
   for (int h = -lim[0]; h <= lim[0]; ++h) {
     bool plane_open = false;
     for (int k = -lim[1]; k <= lim[1]; ++k) {
-      int run_start = -1, last_l = 0;
+      bool in_run = false;
+      int last_l = 0;
       for (int l = -lim[2]; l <= lim[2]; ++l) {
         double q[3];
         for (int c = 0; c < 3; ++c) q[c] = h * B[c] + k * B[3 + c] + l * B[6 + c] + kc[c];
@@ -528,8 +529,8 @@ int create_impl(const pw_problem_desc* d, void* stream, pw_ctx** out) {
             pl_row0.push_back((int)rk.size());
             plane_open = true;
           }
-          if (run_start < 0) {
-            run_start = l;
+          if (!in_run) {
+            in_run = true;
             rk.push_back(k);
             rl0.push_back(l);
             rcnt.push_back(0);
