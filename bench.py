@@ -1,0 +1,377 @@
+#!/usr/bin/env python
+"""Benchmark of the Chebyshev-filtered plane-wave H-apply on one (or N replica) GB300.
+
+Metric: band.H-applies/s in the Chebyshev filter (M bands x degree m per filter
+call / filter time), mixed precision (complex64 FFTs, FP32-accumulated projector
+GEMMs) against the plain FP64 GPU path on the same inputs, with the eigenvalue
+error of one filter + Rayleigh-Ritz cycle between the two.
+
+Workload: the 96^3-box, ~55k plane-wave, 64-atom / 512-projector, 256-band,
+degree-10 Gamma-point problem (seeded synthetic inputs from workloads.py).  One
+step = one ChebFi cycle on one batch: the degree-m filter (timed: `value`)
+followed by the FP64 S-Ortho + Rayleigh-Ritz step.  Inputs are resident in HBM
+when the timed region starts; L2 is flushed (256 MB write) between steps.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+For N > 1 (torchrun) every rank runs an independent replica (k-point style
+weak scaling); the filter time is the max over ranks and `value` sums all ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+from paper_2604_11139_gb300 import workloads as W  # noqa: E402
+
+METRIC = "band·H-applies/s in Chebyshev filter, mixed vs FP64 GPU, at ≤1e-6 Ha eig error"
+UNIT = "band-applies/s"
+WORKLOAD = "fp64_at_scale"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--fp64-steps", type=int, default=2)
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--workload", default=WORKLOAD)
+    return ap.parse_args()
+
+
+def workload_config(prob, npw, nproj):
+    return {"workload": f"{prob.name}: {prob.box[0]}x{prob.box[1]}x{prob.box[2]} box, {npw} plane waves, "
+                        f"{prob.natom} atoms / {nproj} projectors, {prob.nband} bands, degree {prob.degree}, Gamma",
+            "box": list(prob.box), "npw": npw, "nband": prob.nband, "nproj": nproj, "degree": prob.degree,
+            "seed": prob.seed, "l2": "flushed between steps (256 MB write); working set > L2"}
+
+
+# ------------------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, dev):
+        self.dev = dev
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                       "-lms", "200", "-i", str(self.dev)], stdout=subprocess.PIPE,
+                                      stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            out, _ = self.p.communicate(timeout=5)
+        except Exception:
+            self.p.kill()
+            out = ""
+        sm, mx, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for line in out.splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------------------- helpers
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            d = json.load(fh)
+        return d.get("hbm_gbs", 6786.2), d.get("bf16_tflops", 1890.7), d.get("sm_max_mhz", 2070.0), "measured"
+    except Exception:
+        return 6800.0, 1900.0, 2070.0, "fallback"
+
+
+def kernel_traffic(cls):
+    """DRAM bytes per launch from the committed ncu summary, if the kernel source is unchanged."""
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+    except Exception:
+        return None
+    ent = d.get(cls)
+    if not ent:
+        return None
+    src = os.path.join(ROOT, "paper_2604_11139_gb300", "csrc", ent["source"])
+    try:
+        h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    except Exception:
+        return None
+    if h != ent.get("source_sha"):
+        return None
+    return ent["bytes_per_launch_scaled"]
+
+
+def cpu_oracle_rate(prob, seconds, max_bands=256):
+    """Oracle matrix-free H-apply (the filter's per-band work) on the host cores."""
+    from oracle import pw_oracle as O
+    ham = O.Hamiltonian.from_problem(prob)
+    Y = W.psi0(prob.seed, ham.npw, min(prob.nband, max_bands))
+    done, t0, nb = 0, time.perf_counter(), 8
+    while time.perf_counter() - t0 < seconds and done + nb <= Y.shape[0]:
+        ham.apply_h(Y[done:done + nb])
+        done += nb
+    dt = time.perf_counter() - t0
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    return {"value": done / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{done} bands x 1 filter step (matrix-free FP64 H-apply, direct separable DFT) "
+                      f"of the {prob.name} workload, {dt:.1f} s"}
+
+
+def emit(obj):
+    print(json.dumps(obj), flush=True)
+
+
+# ------------------------------------------------------------------------- reference arm
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    from oracle import pw_oracle as O
+    prob = W.make_problem(args.workload)
+    ham = O.Hamiltonian.from_problem(prob)
+    Y = W.psi0(prob.seed, ham.npw, prob.nband)
+    nb = 2
+    for s in range(args.warmup):
+        ham.apply_h(Y[:nb])
+    t = []
+    for s in range(args.steps):
+        j = (s * nb) % (prob.nband - nb)
+        t0 = time.perf_counter()
+        ham.apply_h(Y[j:j + nb])
+        t.append(time.perf_counter() - t0)
+    tot = sum(t)
+    val = nb * args.steps / tot
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    sample = f"each step: {nb} bands x 1 filter step (oracle matrix-free FP64 H-apply) of {prob.name}"
+    emit({"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
+          "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
+          "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+          "config": workload_config(prob, ham.npw, ham.P.shape[1]),
+          "cpu_baseline": {"value": val, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+          "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}})
+    return 0
+
+
+# ------------------------------------------------------------------------- our arm
+def run_ours(args):
+    import torch
+    from paper_2604_11139_gb300 import pwlib
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.cuda.current_device()
+
+    prob = W.make_problem(args.workload)
+    M, m = prob.nband, prob.degree
+    ctx = pwlib.Context.from_problem(prob)
+    npw, nproj = ctx.npw, ctx.nproj
+    psi0 = W.psi0(prob.seed, npw, M)
+    v0 = torch.from_numpy(W.lanczos_v0(prob.seed, npw)[None]).cuda()
+    Y0 = torch.from_numpy(psi0).cuda()                       # complex128, resident
+    Y0_32 = Y0.to(torch.complex64)
+    rqmin, a, b = ctx.spectrum_bounds(Y0, 10, v0)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+    Y32 = torch.empty_like(Y0_32)
+    Y64 = torch.empty_like(Y0)
+    st = torch.cuda.current_stream()
+
+    def step(timed_events):
+        Y32.copy_(Y0_32)
+        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        e0.record(st)
+        ctx.chebyshev_filter(Y32, m, a, b, precision=pwlib.PW_MIXED)
+        e1.record(st)
+        Y64.copy_(Y32)
+        eig, res = ctx.rayleigh_ritz(Y64)
+        e2.record(st)
+        timed_events.append((e0, e1, e2))
+        return eig
+
+    for _ in range(args.warmup):
+        step([])
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    clocks = ClockSampler(dev)
+    clocks.start()
+    ctx.profile(True)
+    ctx.profile_read()
+    l0 = pwlib.kernel_launches()
+    evs = []
+    torch.cuda.synchronize()
+    w0 = time.perf_counter()
+    for _ in range(args.steps):
+        flush.zero_()
+        eig_mixed = step(evs)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - w0
+    launches = pwlib.kernel_launches() - l0
+    prof = ctx.profile_read()
+    ctx.profile(False)
+    clk = clocks.stop()
+    filt_ms = [e0.elapsed_time(e1) for e0, e1, e2 in evs]
+    step_ms = [e0.elapsed_time(e2) for e0, e1, e2 in evs]
+    t_filter = sum(filt_ms) / 1e3
+    if dist is not None:
+        t = torch.tensor([t_filter, sum(step_ms) / 1e3], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_filter, t_step = float(t[0]), float(t[1])
+    else:
+        t_step = sum(step_ms) / 1e3
+    value = world * M * m * args.steps / t_filter
+
+    # FP64 GPU path on the same inputs (denominator of the mixed-vs-FP64 ratio)
+    fp64 = None
+    eig_err = None
+    if args.fp64_steps > 0:
+        Y64.copy_(Y0)
+        ctx.chebyshev_filter(Y64, m, a, b, precision=pwlib.PW_FP64)   # warm-up
+        ts = []
+        for _ in range(args.fp64_steps):
+            flush.zero_()
+            Y64.copy_(Y0)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            ctx.chebyshev_filter(Y64, m, a, b, precision=pwlib.PW_FP64)
+            e1.record(st)
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1) / 1e3)
+        eig64, _ = ctx.rayleigh_ritz(Y64)
+        eig_err = float(np.abs(eig64 - eig_mixed).max())
+        fp64 = {"value": M * m / statistics.mean(ts), "unit": UNIT, "filter_ms": 1e3 * statistics.mean(ts),
+                "steps": len(ts)}
+
+    # end to end through the public C ABI with host buffers: H2D psi, one ChebFi cycle, D2H psi + eigenvalues
+    host_in = torch.from_numpy(psi0).pin_memory()
+    host_out = torch.empty_like(host_in).pin_memory()
+    Ye = torch.empty_like(Y0)
+    e2e_t = []
+    for s in range(args.e2e_steps + 1):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        Ye.copy_(host_in, non_blocking=True)
+        eig_e, res_e, bnd = ctx.chebfi_solve(Ye, m, 1, v0, lanczos_steps=10, precision=pwlib.PW_MIXED)
+        host_out.copy_(Ye, non_blocking=True)
+        torch.cuda.synchronize()
+        if s > 0:
+            e2e_t.append(time.perf_counter() - t0)
+    e2e_val = world * M * m / statistics.mean(e2e_t)
+    bytes_psi = psi0.nbytes
+
+    # roofline of the dominant kernel class of the filter
+    hbm, bf16, smmax, src = peaks()
+    filt_classes = ("plane_inv", "xline", "plane_fwd", "gemm_proj", "gemm_back", "small")
+    dom = max(filt_classes, key=lambda c: prof[c][0])
+    ms_c, n_c = prof[dom]
+    per_launch_s = ms_c / 1e3 / max(n_c, 1)
+    c8 = 8  # complex64 bytes
+    nplane_planes = None
+    box = prob.box
+    # half-box planes: 2r+1 x-planes with sphere content
+    mill, _ = ctx.gvectors()
+    nplane = len(np.unique(mill[:, 0]))
+    bb = max(1, min(M, (256 << 20) // (nplane * box[1] * box[2] * 16)))
+    batches = [min(bb, M - i) for i in range(0, M, bb)]
+    nb_avg = M / len(batches)
+    half = nplane * box[1] * box[2]
+    if dom == "plane_inv":
+        bound, achieved_units = "hbm", nb_avg * (npw + half) * c8
+    elif dom == "xline":
+        bound, achieved_units = "hbm", nb_avg * 2 * half * c8 + box[0] * box[1] * box[2] * 4
+    elif dom == "plane_fwd":
+        bound, achieved_units = "hbm", nb_avg * (half + 2 * npw) * c8
+    else:
+        bound, achieved_units = "alu", 8.0 * npw * nproj * M
+    if bound == "hbm":
+        ach = achieved_units / per_launch_s / 1e9
+        roof = {"bound": "hbm", "kernel": dom, "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
+                "peak_source": src, "traffic": kernel_traffic(dom),
+                "algorithmic_bytes_per_launch": achieved_units, "avg_launch_ms": per_launch_s * 1e3}
+    else:
+        fp32_peak = 152 * 128 * 2 * smmax * 1e6 / 1e12
+        ach = achieved_units / per_launch_s / 1e12
+        roof = {"bound": "alu", "kernel": dom, "achieved": ach, "peak": fp32_peak, "unit": "TFLOP/s",
+                "frac": ach / fp32_peak, "peak_source": "FP32 FFMA: 152 SMs x 128 lanes x 2 x max SM clock",
+                "traffic": kernel_traffic(dom), "algorithmic_flops_per_launch": achieved_units,
+                "avg_launch_ms": per_launch_s * 1e3}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu and world == 1:
+        cpu = cpu_oracle_rate(prob, args.cpu_seconds)
+
+    if rank == 0:
+        emit({"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+              "warmup": args.warmup, "ms_per_step": 1e3 * t_step / args.steps, "higher_is_better": True,
+              "scaling": "weak", "vs_baseline": None, "dtype": "c64", "data": "synthetic",
+              "config": workload_config(prob, npw, nproj),
+              "precision": "filter: complex64 FFTs + FP32 SIMT projector GEMMs; RR: FP64",
+              "filter_ms": 1e3 * t_filter / args.steps, "wall_s": wall,
+              "fp64": fp64, "eig_err_vs_fp64": eig_err,
+              "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": bytes_psi,
+                      "d2h_bytes_per_step": bytes_psi + 8 * M,
+                      "what": "H2D psi (pinned) + pw_chebfi_solve (Lanczos bound, 1 mixed filter + FP64 RR) "
+                              "+ D2H psi and eigenvalues"},
+              "roofline": roof, "cpu_baseline": cpu, "clocks": clk, "gpu_launches": int(launches),
+              "kernels_ms_per_step": {k: v[0] / args.steps for k, v in prof.items()},
+              "kernel_launches_per_step": {k: v[1] / args.steps for k, v in prof.items()}})
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+    ctx.close()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -147,6 +147,26 @@ PW_API int pw_chebfi_solve(pw_ctx* ctx, void* psi, int64_t ldpsi, int nband, int
 PW_API int pw_density_grad(pw_ctx* ctx, const void* a, const void* b, int64_t ld, int nband,
                            const double* w, double* out, int accumulate);
 
+/* Diagnostics.  Per-context timing of kernel classes with CUDA events recorded
+ * on the context's stream around each launch (no extra synchronisation while
+ * enabled).  pw_profile_read synchronises the stream, returns the accumulated
+ * milliseconds and launch counts per class (arrays of PW_PROF_NCLASS) and resets
+ * them.  pw_kernel_launches returns the number of kernels this library has
+ * launched in the process so far. */
+enum pw_prof_class {
+  PW_PROF_PLANE_INV = 0,  /* FFT pass 1: sphere -> inverse (z, y) planes */
+  PW_PROF_XLINE = 1,      /* FFT pass 2: x-lines, inverse x, V_loc, forward x */
+  PW_PROF_PLANE_FWD = 2,  /* FFT pass 3: forward (y, z), gather, kinetic */
+  PW_PROF_GEMM_PROJ = 3,  /* C_proj = P^dagger Y (and P^dagger W with S) */
+  PW_PROF_GEMM_BACK = 4,  /* Y_{k+1} = alpha (W + P Z - c Y_k) - beta Y_{k-1}, or H psi += P Z */
+  PW_PROF_SMALL = 5,      /* projector-space products D C, E C - K C_w */
+  PW_PROF_RR = 6,         /* S-Ortho + Rayleigh-Ritz (whole step) */
+  PW_PROF_NCLASS = 7
+};
+PW_API int pw_profile_enable(pw_ctx* ctx, int on);
+PW_API int pw_profile_read(pw_ctx* ctx, double* ms, int64_t* launches);
+PW_API uint64_t pw_kernel_launches(void);
+
 PW_API const char* pw_strerror(int status);
 PW_API const char* pw_last_error(void);
 

@@ -333,7 +333,7 @@ template <typename T>
 cudaError_t launch_local_apply(const FftPlan& plan, const cplx<T>* tw, const SphereDev& sp,
                                const T* vperm, const T* kin, const cplx<T>* psi, int64_t ldpsi,
                                int nband, cplx<T>* out, int64_t ldout, cplx<T>* hb, int band_batch,
-                               cudaStream_t st) {
+                               cudaStream_t st, ::pw_ctx* prof) {
   if (nband <= 0) return cudaSuccess;
   const int cz = pick_cz(plan.n[2]);
   const int lyz = 32;
@@ -347,10 +347,16 @@ cudaError_t launch_local_apply(const FftPlan& plan, const cplx<T>* tw, const Sph
   const int nyz = plan.n[1] * plan.n[2];
   for (int b0 = 0; b0 < nband; b0 += band_batch) {
     const int nb = min(band_batch, nband - b0);
-    k_plane_inv<T><<<dim3(sp.nplane, nb), kThreads, sm1, st>>>(psi + b0 * ldpsi, ldpsi, hb, hb_bs, sp, plan, tw, cz);
-    k_xline<T><<<dim3((nyz + lyz - 1) / lyz, nb), kThreads, sm2, st>>>(hb, hb_bs, vperm, sp, plan, tw, lyz);
+    prof_begin(prof, PW_PROF_PLANE_INV);
+    k_plane_inv<T><<<dim3(sp.nplane, nb), kThreads, sm1, st>>>(psi + b0 * ldpsi, ldpsi, hb, hb_bs, sp, plan, tw, cz); count_launch();
+    prof_end(prof, PW_PROF_PLANE_INV);
+    prof_begin(prof, PW_PROF_XLINE);
+    k_xline<T><<<dim3((nyz + lyz - 1) / lyz, nb), kThreads, sm2, st>>>(hb, hb_bs, vperm, sp, plan, tw, lyz); count_launch();
+    prof_end(prof, PW_PROF_XLINE);
+    prof_begin(prof, PW_PROF_PLANE_FWD);
     k_plane_fwd<T><<<dim3(sp.nplane, nb), kThreads, sm1, st>>>(hb, hb_bs, sp, plan, tw, cz, kin,
-                                                                psi + b0 * ldpsi, ldpsi, out + b0 * ldout, ldout);
+                                                                psi + b0 * ldpsi, ldpsi, out + b0 * ldout, ldout); count_launch();
+    prof_end(prof, PW_PROF_PLANE_FWD);
   }
   return cudaGetLastError();
 }
@@ -373,20 +379,20 @@ cudaError_t launch_density(const FftPlan& plan, const cplx<T>* tw, const SphereD
   cplx<T>* hbb = b ? hb + hb_bs * band_batch : nullptr;
   for (int b0 = 0; b0 < nband; b0 += band_batch) {
     const int nb = min(band_batch, nband - b0);
-    k_plane_inv<T><<<dim3(sp.nplane, nb), kThreads, sm1, st>>>(a + b0 * ld, ld, hb, hb_bs, sp, plan, tw, cz);
-    if (b) k_plane_inv<T><<<dim3(sp.nplane, nb), kThreads, sm1, st>>>(b + b0 * ld, ld, hbb, hb_bs, sp, plan, tw, cz);
+    k_plane_inv<T><<<dim3(sp.nplane, nb), kThreads, sm1, st>>>(a + b0 * ld, ld, hb, hb_bs, sp, plan, tw, cz); count_launch();
+    if (b) { k_plane_inv<T><<<dim3(sp.nplane, nb), kThreads, sm1, st>>>(b + b0 * ld, ld, hbb, hb_bs, sp, plan, tw, cz); count_launch(); }
     k_xline_density<T><<<(nyz + lyz - 1) / lyz, kThreads, sm2, st>>>(hb, hbb, hb_bs, nb, w_dev + b0, sp, plan,
-                                                                     tw, lyz, out_perm);
+                                                                     tw, lyz, out_perm); count_launch();
   }
   return cudaGetLastError();
 }
 
 template cudaError_t launch_local_apply<double>(const FftPlan&, const double2*, const SphereDev&, const double*,
                                                 const double*, const double2*, int64_t, int, double2*, int64_t,
-                                                double2*, int, cudaStream_t);
+                                                double2*, int, cudaStream_t, ::pw_ctx*);
 template cudaError_t launch_local_apply<float>(const FftPlan&, const float2*, const SphereDev&, const float*,
                                                const float*, const float2*, int64_t, int, float2*, int64_t,
-                                               float2*, int, cudaStream_t);
+                                               float2*, int, cudaStream_t, ::pw_ctx*);
 template cudaError_t launch_density<double>(const FftPlan&, const double2*, const SphereDev&, const double2*,
                                             const double2*, int64_t, int, const double*, double*, double2*, int,
                                             cudaStream_t);

@@ -132,9 +132,10 @@ cudaError_t launch_cgemm(int ta, int tb, int M, int N, int K, const cplx<T>* A, 
   else if (ta == 1 && tb == 0) k_cgemm<T, 1, 0><<<grid, 256, 0, st>>>(M, N, K, A, lda, B, ldb, epi, kchunk, ws);
   else if (ta == 0 && tb == 1) k_cgemm<T, 0, 1><<<grid, 256, 0, st>>>(M, N, K, A, lda, B, ldb, epi, kchunk, ws);
   else k_cgemm<T, 1, 1><<<grid, 256, 0, st>>>(M, N, K, A, lda, B, ldb, epi, kchunk, ws);
+  count_launch();
   if (nsplit > 1) {
     const int64_t tot = (int64_t)M * N;
-    k_splitk_reduce<T><<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(M, N, nsplit, ws, epi);
+    k_splitk_reduce<T><<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(M, N, nsplit, ws, epi); count_launch();
   }
   return cudaGetLastError();
 }
@@ -164,7 +165,7 @@ cudaError_t launch_dblock(int nproj, int nband, const T* D, const int* blk0, con
                           const cplx<T>* Cm, int64_t ldc, cplx<T>* Z, int64_t ldz, cudaStream_t st) {
   const int64_t tot = (int64_t)nproj * nband;
   if (tot <= 0) return cudaSuccess;
-  k_dblock<T><<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(nproj, nband, D, blk0, blklen, Cm, ldc, Z, ldz);
+  k_dblock<T><<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(nproj, nband, D, blk0, blklen, Cm, ldc, Z, ldz); count_launch();
   return cudaGetLastError();
 }
 

@@ -25,7 +25,7 @@ __global__ void k_herm_sym(double2* A, int64_t lda, int n) {
 
 cudaError_t la_herm_sym(double2* A, int64_t lda, int n, cudaStream_t st) {
   dim3 b(16, 16), g((n + 15) / 16, (n + 15) / 16);
-  k_herm_sym<<<g, b, 0, st>>>(A, lda, n);
+  k_herm_sym<<<g, b, 0, st>>>(A, lda, n); count_launch();
   return cudaGetLastError();
 }
 
@@ -113,24 +113,24 @@ __global__ void k_zero_upper(double2* A, int64_t lda, int n) {
 
 cudaError_t la_zero_upper(double2* A, int64_t lda, int n, cudaStream_t st) {
   dim3 b(16, 16), g((n + 15) / 16, (n + 15) / 16);
-  k_zero_upper<<<g, b, 0, st>>>(A, lda, n);
+  k_zero_upper<<<g, b, 0, st>>>(A, lda, n); count_launch();
   return cudaGetLastError();
 }
 
 cudaError_t la_cholesky(double2* A, int64_t lda, int n, int* flag, cudaStream_t st) {
   for (int k0 = 0; k0 < n; k0 += NB) {
     const int kb = min(NB, n - k0);
-    k_chol_diag<<<1, dim3(32, 32), 0, st>>>(A, lda, k0, kb, flag);
+    k_chol_diag<<<1, dim3(32, 32), 0, st>>>(A, lda, k0, kb, flag); count_launch();
     const int rest = n - k0 - kb;
     if (rest > 0) {
-      k_chol_panel<<<(rest + 127) / 128, 128, 0, st>>>(A, lda, n, k0, kb);
+      k_chol_panel<<<(rest + 127) / 128, 128, 0, st>>>(A, lda, n, k0, kb); count_launch();
       const int nt = (rest + 31) / 32;
-      k_chol_update<<<dim3(nt, nt), 256, 0, st>>>(A, lda, n, k0, kb);
+      k_chol_update<<<dim3(nt, nt), 256, 0, st>>>(A, lda, n, k0, kb); count_launch();
     }
   }
   // zero the strict upper triangle
   dim3 zb(16, 16), zg((n + 15) / 16, (n + 15) / 16);
-  k_zero_upper<<<zg, zb, 0, st>>>(A, lda, n);
+  k_zero_upper<<<zg, zb, 0, st>>>(A, lda, n); count_launch();
   return cudaGetLastError();
 }
 
@@ -180,12 +180,12 @@ __global__ void k_trinv(const double2* __restrict__ Lt, int n, double2* __restri
 cudaError_t la_trinv_lower(const double2* L, int64_t lda, int n, double2* X, int64_t ldx, double2* tmp,
                            cudaStream_t st) {
   dim3 b(16, 16), g((n + 15) / 16, (n + 15) / 16);
-  k_transpose<<<g, b, 0, st>>>(L, lda, n, tmp);
+  k_transpose<<<g, b, 0, st>>>(L, lda, n, tmp); count_launch();
   const int wpb = 4;
   const size_t sm = sizeof(double2) * (size_t)n * wpb;
   cudaError_t e = cudaFuncSetAttribute(k_trinv, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e) return e;
-  k_trinv<<<(n + wpb - 1) / wpb, 32 * wpb, sm, st>>>(tmp, n, X, ldx);
+  k_trinv<<<(n + wpb - 1) / wpb, 32 * wpb, sm, st>>>(tmp, n, X, ldx); count_launch();
   return cudaGetLastError();
 }
 
@@ -315,7 +315,7 @@ int la_jacobi_eigh(double2* A, int n, double2* U, double* eig, double2* ws, doub
   double2* V = ws + (int64_t)n * n;
   double2* V2 = ws + 2 * (int64_t)n * n;
   const int64_t nn = (int64_t)n * n;
-  k_eye<<<(unsigned)((nn + 255) / 256), 256, 0, st>>>(V, n);
+  k_eye<<<(unsigned)((nn + 255) / 256), 256, 0, st>>>(V, n); count_launch();
   cudaMemcpyAsync(A2, A, sizeof(double2) * nn, cudaMemcpyDeviceToDevice, st);
   cudaMemcpyAsync(V2, V, sizeof(double2) * nn, cudaMemcpyDeviceToDevice, st);
   const int np = (n % 2) ? n + 1 : n;
@@ -326,22 +326,27 @@ int la_jacobi_eigh(double2* A, int n, double2* U, double* eig, double2* ws, doub
   int sweep = 0;
   bool conv = (n <= 1);
   double h[2];
+  double prev_off = INFINITY;
   while (!conv && sweep < max_sweeps) {
     for (int t = 0; t < np - 1; ++t) {
-      k_jacobi_round<<<nblk, 256, 0, st>>>(Acur, Anext, Vcur, Vnext, n, np, t);
+      k_jacobi_round<<<nblk, 256, 0, st>>>(Acur, Anext, Vcur, Vnext, n, np, t); count_launch();
       double2* x = Acur; Acur = Anext; Anext = x;
       x = Vcur; Vcur = Vnext; Vnext = x;
     }
     ++sweep;
     cudaMemsetAsync(norms_dev, 0, 2 * sizeof(double), st);
-    k_offnorm<<<64, 256, 0, st>>>(Acur, n, norms_dev);
+    k_offnorm<<<64, 256, 0, st>>>(Acur, n, norms_dev); count_launch();
     cudaError_t e = cudaMemcpyAsync(h, norms_dev, 2 * sizeof(double), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return cuda_status(e, "jacobi");
-    if (h[0] <= tol * tol * (h[0] + h[1])) conv = true;
+    // converged below tol * ||A||_F, or stalled at the rounding floor (no halving in a sweep)
+    const double off = sqrt(h[0]), nrm = sqrt(h[0] + h[1]);
+    if (off <= tol * nrm) conv = true;
+    else if (off <= 1e-10 * nrm && off > 0.5 * prev_off) conv = true;
+    prev_off = off;
   }
   if (sweeps_out) *sweeps_out = sweep;
-  k_sort_eig<<<n, 128, 0, st>>>(Acur, Vcur, n, eig, U);
+  k_sort_eig<<<n, 128, 0, st>>>(Acur, Vcur, n, eig, U); count_launch();
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_status(e, "jacobi sort");
   return conv ? PW_OK : set_error(PW_ENOTCONV, "Jacobi eigensolver: %d sweeps without convergence", sweep);
@@ -373,7 +378,7 @@ __global__ void k_coldot(const cplx<T>* A, int64_t lda, const cplx<T>* B, int64_
 cudaError_t la_coldot(const double2* A, int64_t lda, const double2* B, int64_t ldb, int npw, int m,
                       double2* out, cudaStream_t st) {
   if (m <= 0) return cudaSuccess;
-  k_coldot<double><<<m, 256, 0, st>>>(A, lda, B, ldb, npw, out);
+  k_coldot<double><<<m, 256, 0, st>>>(A, lda, B, ldb, npw, out); count_launch();
   return cudaGetLastError();
 }
 
@@ -401,7 +406,7 @@ __global__ void k_resid(const double2* HY, int64_t ldh, const double2* SY, int64
 cudaError_t la_resid(const double2* HY, int64_t ldh, const double2* SY, int64_t lds, int npw, int m,
                      const double* eig, double* r, cudaStream_t st) {
   if (m <= 0) return cudaSuccess;
-  k_resid<<<m, 256, 0, st>>>(HY, ldh, SY, lds, npw, eig, r);
+  k_resid<<<m, 256, 0, st>>>(HY, ldh, SY, lds, npw, eig, r); count_launch();
   return cudaGetLastError();
 }
 
@@ -427,7 +432,7 @@ __global__ void k_rq_minmax(const double2* num, const double2* den, int m, doubl
 }
 
 cudaError_t la_rq_minmax(const double2* num, const double2* den, int m, double* rq, double* mm, cudaStream_t st) {
-  k_rq_minmax<<<1, 256, 0, st>>>(num, den, m, rq, mm);
+  k_rq_minmax<<<1, 256, 0, st>>>(num, den, m, rq, mm); count_launch();
   return cudaGetLastError();
 }
 
@@ -523,14 +528,14 @@ __global__ void k_lz_bound(const double* ab, int k, double* out) {
 
 cudaError_t la_lanczos(const double2* v0, int n, int steps, double2* v, double2* vprev, double2* w, double* ab,
                        double* bound, ApplyFn apply, void* ctx, cudaStream_t st) {
-  k_lz_normalize<<<1, 1024, 0, st>>>(v0, v, vprev, n);
+  k_lz_normalize<<<1, 1024, 0, st>>>(v0, v, vprev, n); count_launch();
   for (int k = 0; k < steps; ++k) {
     int s = apply(ctx, v, w);
     if (s != PW_OK) return cudaErrorUnknown;
-    k_lz_dot<<<1, 1024, 0, st>>>(v, w, n, ab + 2 * k);
-    k_lz_update<<<1, 1024, 0, st>>>(w, v, vprev, n, ab + 2 * k, k > 0 ? ab + 2 * k - 1 : nullptr, ab + 2 * k + 1);
+    k_lz_dot<<<1, 1024, 0, st>>>(v, w, n, ab + 2 * k); count_launch();
+    k_lz_update<<<1, 1024, 0, st>>>(w, v, vprev, n, ab + 2 * k, k > 0 ? ab + 2 * k - 1 : nullptr, ab + 2 * k + 1); count_launch();
   }
-  k_lz_bound<<<1, 32, 0, st>>>(ab, steps, bound);
+  k_lz_bound<<<1, 32, 0, st>>>(ab, steps, bound); count_launch();
   return cudaGetLastError();
 }
 
@@ -552,13 +557,13 @@ __global__ void k_c64_to_c128(const float2* a, int64_t lda, double2* b, int64_t 
 cudaError_t la_to_c64(const double2* a, int64_t lda, float2* b, int64_t ldb, int n, int m, cudaStream_t st) {
   const int64_t t = (int64_t)n * m;
   if (t <= 0) return cudaSuccess;
-  k_c128_to_c64<<<(unsigned)((t + 255) / 256), 256, 0, st>>>(a, lda, b, ldb, n, m);
+  k_c128_to_c64<<<(unsigned)((t + 255) / 256), 256, 0, st>>>(a, lda, b, ldb, n, m); count_launch();
   return cudaGetLastError();
 }
 cudaError_t la_to_c128(const float2* a, int64_t lda, double2* b, int64_t ldb, int n, int m, cudaStream_t st) {
   const int64_t t = (int64_t)n * m;
   if (t <= 0) return cudaSuccess;
-  k_c64_to_c128<<<(unsigned)((t + 255) / 256), 256, 0, st>>>(a, lda, b, ldb, n, m);
+  k_c64_to_c128<<<(unsigned)((t + 255) / 256), 256, 0, st>>>(a, lda, b, ldb, n, m); count_launch();
   return cudaGetLastError();
 }
 

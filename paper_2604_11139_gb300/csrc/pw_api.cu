@@ -9,6 +9,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <atomic>
 #include <new>
 #include <type_traits>
 
@@ -53,6 +54,47 @@ void* ws_get(pw_ctx* c, int slot, size_t bytes, int* status) {
   b.bytes = bytes;
   return b.p;
 }
+
+static std::atomic<uint64_t> g_launches{0};
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+static cudaEvent_t prof_event(pw_ctx* c) {
+  if (c->ev_used == c->ev_pool.size()) {
+    cudaEvent_t e;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    c->ev_pool.push_back(e);
+  }
+  return c->ev_pool[c->ev_used++];
+}
+
+void prof_begin(pw_ctx* c, int cls) {
+  if (!c || !c->prof_on || (c->prof_suspend > 0 && cls != PW_PROF_RR)) return;
+  cudaEvent_t e = prof_event(c);
+  if (e) cudaEventRecord(e, c->stream);
+  c->prof_open[cls] = e;
+}
+
+void prof_end(pw_ctx* c, int cls) {
+  if (!c || !c->prof_on || !c->prof_open[cls] || (c->prof_suspend > 0 && cls != PW_PROF_RR)) return;
+  cudaEvent_t e = prof_event(c);
+  if (!e) return;
+  cudaEventRecord(e, c->stream);
+  c->prof_recs.push_back({cls, c->prof_open[cls], e});
+  c->prof_open[cls] = nullptr;
+}
+
+struct ProfScope {
+  pw_ctx* c;
+  int cls;
+  ProfScope(pw_ctx* c_, int cls_) : c(c_), cls(cls_) {
+    prof_begin(c, cls);
+    if (cls == PW_PROF_RR && c) c->prof_suspend++;
+  }
+  ~ProfScope() {
+    if (cls == PW_PROF_RR && c) c->prof_suspend--;
+    prof_end(c, cls);
+  }
+};
 
 }  // namespace pw
 
@@ -225,11 +267,18 @@ int apply_impl(pw_ctx* ctx, const cplx<T>* psi, int64_t ldpsi, int nband, cplx<T
   const int ns = nsplit_for(np, nband, npw);
   WS(sp, C, WS_SPLIT, (size_t)ns * np * nband);
   CU_TRY(launch_local_apply<T>(ctx->plan, Prec<T>::tw(ctx), ctx->sp, Prec<T>::vp(ctx), Prec<T>::kin(ctx), psi,
-                               ldpsi, nband, hpsi, ldout, hb, bb, st), "local apply");
+                               ldpsi, nband, hpsi, ldout, hb, bb, st, ctx), "local apply");
   if (np > 0) {
-    CU_TRY(launch_cgemm<T>(1, 0, np, nband, npw, Prec<T>::P(ctx), npw, psi, ldpsi, epi<T>(EPI_STORE, Cm, np), ns,
-                           sp, st), "projection gemm");
-    CU_TRY(launch_dblock<T>(np, nband, Prec<T>::D(ctx), ctx->blk0, ctx->blklen, Cm, np, Z, np, st), "D block");
+    {
+      ProfScope ps(ctx, PW_PROF_GEMM_PROJ);
+      CU_TRY(launch_cgemm<T>(1, 0, np, nband, npw, Prec<T>::P(ctx), npw, psi, ldpsi, epi<T>(EPI_STORE, Cm, np), ns,
+                             sp, st), "projection gemm");
+    }
+    {
+      ProfScope ps(ctx, PW_PROF_SMALL);
+      CU_TRY(launch_dblock<T>(np, nband, Prec<T>::D(ctx), ctx->blk0, ctx->blklen, Cm, np, Z, np, st), "D block");
+    }
+    ProfScope ps(ctx, PW_PROF_GEMM_BACK);
     CU_TRY(launch_cgemm<T>(0, 0, npw, nband, np, Prec<T>::P(ctx), npw, Z, np, epi<T>(EPI_ACCUM, hpsi, ldout), 1,
                            sp, st), "back-projection gemm");
   }
@@ -280,7 +329,7 @@ int filter_impl(pw_ctx* ctx, cplx<T>* psi, int64_t ldpsi, int nband, int degree,
     const T alpha = (T)(k == 0 ? 1.0 / e : 2.0 / e);
     // W = (T + V) Y_k
     CU_TRY(launch_local_apply<T>(ctx->plan, Prec<T>::tw(ctx), ctx->sp, Prec<T>::vp(ctx), Prec<T>::kin(ctx), cur,
-                                 ldc, nband, dst, ldd, hb, bb, st), "filter local");
+                                 ldc, nband, dst, ldd, hb, bb, st, ctx), "filter local");
     Epi<T> ce = epi<T>(EPI_CHEB, dst, ldd, alpha);
     ce.beta = (T)1;
     ce.shift = (T)cc;
@@ -289,22 +338,31 @@ int filter_impl(pw_ctx* ctx, cplx<T>* psi, int64_t ldpsi, int nband, int degree,
     ce.ykm1 = (k == 0) ? nullptr : prev;
     ce.ldy2 = ldp;
     if (np > 0) {
-      // C = P^dagger Y_k
-      CU_TRY(launch_cgemm<T>(1, 0, np, nband, npw, Prec<T>::P(ctx), npw, cur, ldc, epi<T>(EPI_STORE, Cm, np), ns,
-                             spl, st), "filter projection");
-      if (!ctx->has_q) {
-        CU_TRY(launch_dblock<T>(np, nband, Prec<T>::D(ctx), ctx->blk0, ctx->blklen, Cm, np, Z, np, st), "filter D");
-      } else {
-        // S^-1 H Y = W + P [E C - K P^dagger W],  E = (I - K P^dagger P) D  (Woodbury, Sec. 3.3)
-        CU_TRY(launch_cgemm<T>(1, 0, np, nband, npw, Prec<T>::P(ctx), npw, dst, ldd, epi<T>(EPI_STORE, Cw, np), ns,
-                               spl, st), "filter projection of W");
-        CU_TRY(launch_cgemm<T>(0, 0, np, nband, np, Prec<T>::E(ctx), np, Cm, np, epi<T>(EPI_STORE, Z, np), 1, spl,
-                               st), "filter E C");
-        CU_TRY(launch_cgemm<T>(0, 0, np, nband, np, Prec<T>::K(ctx), np, Cw, np, epi<T>(EPI_ACCUM, Z, np, (T)-1), 1,
-                               spl, st), "filter K Cw");
+      {
+        ProfScope ps(ctx, PW_PROF_GEMM_PROJ);
+        // C = P^dagger Y_k
+        CU_TRY(launch_cgemm<T>(1, 0, np, nband, npw, Prec<T>::P(ctx), npw, cur, ldc, epi<T>(EPI_STORE, Cm, np), ns,
+                               spl, st), "filter projection");
+        if (ctx->has_q)
+          CU_TRY(launch_cgemm<T>(1, 0, np, nband, npw, Prec<T>::P(ctx), npw, dst, ldd, epi<T>(EPI_STORE, Cw, np), ns,
+                                 spl, st), "filter projection of W");
       }
+      {
+        ProfScope ps(ctx, PW_PROF_SMALL);
+        if (!ctx->has_q) {
+          CU_TRY(launch_dblock<T>(np, nband, Prec<T>::D(ctx), ctx->blk0, ctx->blklen, Cm, np, Z, np, st), "filter D");
+        } else {
+          // S^-1 H Y = W + P [E C - K P^dagger W],  E = (I - K P^dagger P) D  (Woodbury, Sec. 3.3)
+          CU_TRY(launch_cgemm<T>(0, 0, np, nband, np, Prec<T>::E(ctx), np, Cm, np, epi<T>(EPI_STORE, Z, np), 1, spl,
+                                 st), "filter E C");
+          CU_TRY(launch_cgemm<T>(0, 0, np, nband, np, Prec<T>::K(ctx), np, Cw, np, epi<T>(EPI_ACCUM, Z, np, (T)-1),
+                                 1, spl, st), "filter K Cw");
+        }
+      }
+      ProfScope ps(ctx, PW_PROF_GEMM_BACK);
       CU_TRY(launch_cgemm<T>(0, 0, npw, nband, np, Prec<T>::P(ctx), npw, Z, np, ce, 1, spl, st), "filter recurrence");
     } else {
+      ProfScope ps(ctx, PW_PROF_GEMM_BACK);
       CU_TRY(launch_cgemm<T>(0, 0, npw, nband, 0, Prec<T>::P(ctx), npw, Z, 1, ce, 1, spl, st), "filter recurrence");
     }
   }
@@ -341,6 +399,7 @@ int check_flag(pw_ctx* ctx, int* flag_dev, const char* what) {
 }
 
 int rr_impl(pw_ctx* ctx, double2* Y, int64_t ldy, int m, double2* hpsi_out, double* eig_h, double* resid_h) {
+  ProfScope rr_scope(ctx, PW_PROF_RR);
   const int npw = ctx->npw;
   const cudaStream_t st = ctx->stream;
   WS(HY, double2, WS_HY, (size_t)npw * m);
@@ -391,7 +450,8 @@ int rr_impl(pw_ctx* ctx, double2* Y, int64_t ldy, int m, double2* hpsi_out, doub
   CU_TRY(la_herm_sym(G, m, m, st), "reduced sym");
   PW_TRY(check_flag(ctx, scal, "Rayleigh-Ritz Cholesky"));
   int sweeps = 0;
-  PW_TRY(la_jacobi_eigh(G, m, U, eig, jac, norms, st, 40, 1e-15, &sweeps));
+  PW_TRY(la_jacobi_eigh(G, m, U, eig, jac, norms, st, 40, 1e-13, &sweeps));
+  ctx->last_sweeps = sweeps;
   // X = Linv^dagger U  -> tmp
   CU_TRY(launch_cgemm<double>(1, 0, m, m, m, Linv, m, U, m, epi<double>(EPI_STORE, tmp, m), 1, nullptr, st), "back-transform");
   // rotate Y, HY, SY
@@ -692,6 +752,7 @@ int create_impl(const pw_problem_desc* d, void* stream, pw_ctx** out) {
 void destroy_impl(pw_ctx* ctx) {
   if (!ctx) return;
   cudaStreamSynchronize(ctx->stream);
+  for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
   for (void* p : ctx->owned) cudaFree(p);
   for (auto& b : ctx->ws)
     if (b.p) cudaFree(b.p);
@@ -844,6 +905,36 @@ PW_API int pw_density_grad(pw_ctx* ctx, const void* a, const void* b, int64_t ld
   CU_TRY(cudaStreamSynchronize(st), "density sync");
   return PW_OK;
 }
+
+PW_API int pw_profile_enable(pw_ctx* ctx, int on) {
+  PW_TRY(check_ctx(ctx));
+  ctx->prof_on = (on != 0);
+  return PW_OK;
+}
+
+PW_API int pw_profile_read(pw_ctx* ctx, double* ms, int64_t* launches) {
+  PW_TRY(check_ctx(ctx));
+  CU_TRY(cudaStreamSynchronize(ctx->stream), "profile sync");
+  for (auto& r : ctx->prof_recs) {
+    float t = 0.f;
+    if (cudaEventElapsedTime(&t, r.a, r.b) == cudaSuccess) {
+      ctx->prof_ms[r.cls] += t;
+      ctx->prof_n[r.cls] += 1;
+    }
+  }
+  ctx->prof_recs.clear();
+  ctx->ev_used = 0;
+  for (int i = 0; i < PW_PROF_NCLASS; ++i) {
+    if (ms) ms[i] = ctx->prof_ms[i];
+    if (launches) launches[i] = ctx->prof_n[i];
+    ctx->prof_ms[i] = 0;
+    ctx->prof_n[i] = 0;
+    ctx->prof_open[i] = nullptr;
+  }
+  return PW_OK;
+}
+
+PW_API uint64_t pw_kernel_launches(void) { return g_launches.load(); }
 
 PW_API const char* pw_strerror(int status) {
   switch (status) {

@@ -9,6 +9,8 @@
 
 #include "../../include/pw.h"
 
+struct pw_ctx;
+
 namespace pw {
 
 // ---------------------------------------------------------------------------
@@ -107,7 +109,7 @@ template <typename T>
 cudaError_t launch_local_apply(const FftPlan& plan, const cplx<T>* tw, const SphereDev& sp,
                                const T* vperm, const T* kin, const cplx<T>* psi, int64_t ldpsi,
                                int nband, cplx<T>* out, int64_t ldout, cplx<T>* hb, int band_batch,
-                               cudaStream_t st);
+                               cudaStream_t st, ::pw_ctx* prof);
 
 template <typename T>
 cudaError_t launch_density(const FftPlan& plan, const cplx<T>* tw, const SphereDev& sp,
@@ -161,10 +163,21 @@ struct pw_ctx {
   double2* E64 = nullptr;   // E = (I - K P^dagger P) D
   float2* K32 = nullptr;
   float2* E32 = nullptr;
+  // kernel-class timing (pw_profile_*)
+  struct ProfRec { int cls; cudaEvent_t a, b; };
+  bool prof_on = false;
+  int prof_suspend = 0;  // >0 inside a Rayleigh-Ritz region: inner classes are not recorded
+  std::vector<cudaEvent_t> ev_pool;
+  size_t ev_used = 0;
+  std::vector<ProfRec> prof_recs;
+  cudaEvent_t prof_open[PW_PROF_NCLASS] = {};
+  double prof_ms[PW_PROF_NCLASS] = {};
+  int64_t prof_n[PW_PROF_NCLASS] = {};
   // grow-only workspaces
   struct Buf { void* p = nullptr; size_t bytes = 0; };
   Buf ws[32];
   bool poisoned = false;
+  int last_sweeps = 0;  // Jacobi sweeps of the last Rayleigh-Ritz step
 };
 
 namespace pw {
@@ -175,6 +188,11 @@ enum WsSlot {
   WS_LZ, WS_RQ, WS_DEN, WS_SCAL, WS_NUM
 };
 void* ws_get(pw_ctx* c, int slot, size_t bytes, int* status);
+// process-wide count of kernel launches issued by this library (diagnostics)
+void count_launch();
+// open / close a timed region of class `cls` on the context's stream (no-ops when off or ctx NULL)
+void prof_begin(pw_ctx* c, int cls);
+void prof_end(pw_ctx* c, int cls);
 int set_error(int status, const char* fmt, ...);
 int cuda_status(cudaError_t e, const char* where);
 }  // namespace pw

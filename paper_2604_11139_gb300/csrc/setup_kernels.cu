@@ -56,8 +56,8 @@ __global__ void k_colnorm_scale(double2* P, int npw, int ncol) {
 cudaError_t setup_projectors(int npw, const int* miller_dev, const ProjParams& pp, int natom, double2* P,
                              cudaStream_t st) {
   if (npw <= 0 || natom <= 0) return cudaSuccess;
-  k_projectors<<<dim3((npw + 127) / 128, natom), 128, 0, st>>>(npw, miller_dev, pp, P);
-  k_colnorm_scale<<<natom * pp.nchan * 4, 256, 0, st>>>(P, npw, natom * pp.nchan * 4);
+  k_projectors<<<dim3((npw + 127) / 128, natom), 128, 0, st>>>(npw, miller_dev, pp, P); count_launch();
+  k_colnorm_scale<<<natom * pp.nchan * 4, 256, 0, st>>>(P, npw, natom * pp.nchan * 4); count_launch();
   return cudaGetLastError();
 }
 
@@ -79,8 +79,8 @@ cudaError_t setup_vperm(const double* V, const int* n, int* const* rho, double s
                         cudaStream_t st) {
   const int64_t tot = (int64_t)n[0] * n[1] * n[2];
   const unsigned nb = (unsigned)((tot + 255) / 256);
-  k_vperm<double><<<nb, 256, 0, st>>>(V, n[0], n[1], n[2], rho[0], rho[1], rho[2], scale, out64);
-  k_vperm<float><<<nb, 256, 0, st>>>(V, n[0], n[1], n[2], rho[0], rho[1], rho[2], scale, out32);
+  k_vperm<double><<<nb, 256, 0, st>>>(V, n[0], n[1], n[2], rho[0], rho[1], rho[2], scale, out64); count_launch();
+  k_vperm<float><<<nb, 256, 0, st>>>(V, n[0], n[1], n[2], rho[0], rho[1], rho[2], scale, out32); count_launch();
   return cudaGetLastError();
 }
 
@@ -102,7 +102,7 @@ cudaError_t setup_unperm(const double* in, const int* n, int* const* rho, double
                          cudaStream_t st) {
   const int64_t tot = (int64_t)n[0] * n[1] * n[2];
   k_unperm<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(in, n[0], n[1], n[2], rho[0], rho[1], rho[2], out,
-                                                          accumulate);
+                                                          accumulate); count_launch();
   return cudaGetLastError();
 }
 
@@ -116,12 +116,12 @@ __global__ void k_z2c(const double2* a, float2* b, int64_t n) {
 }
 cudaError_t cast_d2f(const double* a, float* b, int64_t n, cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
-  k_d2f<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(a, b, n);
+  k_d2f<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(a, b, n); count_launch();
   return cudaGetLastError();
 }
 cudaError_t cast_z2c(const double2* a, float2* b, int64_t n, cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
-  k_z2c<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(a, b, n);
+  k_z2c<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(a, b, n); count_launch();
   return cudaGetLastError();
 }
 
@@ -132,7 +132,7 @@ __global__ void k_r2z(const double* a, double2* b, int64_t n) {
 }
 cudaError_t cast_r2z(const double* a, double2* b, int64_t n, cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
-  k_r2z<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(a, b, n);
+  k_r2z<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(a, b, n); count_launch();
   return cudaGetLastError();
 }
 
@@ -142,7 +142,7 @@ __global__ void k_add_diag(double2* A, int n, double shift) {
   if (i < n) A[i + (int64_t)i * n].x += shift;
 }
 cudaError_t add_diag(double2* A, int n, double shift, cudaStream_t st) {
-  k_add_diag<<<(n + 255) / 256, 256, 0, st>>>(A, n, shift);
+  k_add_diag<<<(n + 255) / 256, 256, 0, st>>>(A, n, shift); count_launch();
   return cudaGetLastError();
 }
 

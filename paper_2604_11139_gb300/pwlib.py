@@ -25,7 +25,10 @@ STATUS = {0: "PW_OK", -1: "PW_EINVAL", -2: "PW_ENOMEM", -3: "PW_ECUDA", -4: "PW_
 # every function declared in include/pw.h
 EXPORTS = ("pw_ctx_create", "pw_ctx_destroy", "pw_ctx_set_stream", "pw_ctx_info", "pw_ctx_gvectors",
            "pw_ctx_projectors", "pw_hamiltonian_apply", "pw_spectrum_bounds", "pw_chebyshev_filter",
-           "pw_rayleigh_ritz", "pw_chebfi_solve", "pw_density_grad", "pw_strerror", "pw_last_error")
+           "pw_rayleigh_ritz", "pw_chebfi_solve", "pw_density_grad", "pw_profile_enable", "pw_profile_read",
+           "pw_kernel_launches", "pw_strerror", "pw_last_error")
+
+PROF_CLASSES = ("plane_inv", "xline", "plane_fwd", "gemm_proj", "gemm_back", "small", "rr")
 
 
 class PWError(RuntimeError):
@@ -69,16 +72,23 @@ def load(path: Optional[str] = None):
     lib.pw_rayleigh_ritz.argtypes = [vp, vp, i64, ci, vp, pd, pd]
     lib.pw_chebfi_solve.argtypes = [vp, vp, i64, ci, ci, ci, ci, vp, ci, pd, pd, pd]
     lib.pw_density_grad.argtypes = [vp, vp, vp, i64, ci, pd, vp, ci]
+    lib.pw_profile_enable.argtypes = [vp, ci]
+    lib.pw_profile_read.argtypes = [vp, pd, ctypes.POINTER(ctypes.c_int64)]
+    lib.pw_kernel_launches.restype = ctypes.c_uint64
+    lib.pw_kernel_launches.argtypes = []
     lib.pw_strerror.restype = ctypes.c_char_p
     lib.pw_strerror.argtypes = [ci]
     lib.pw_last_error.restype = ctypes.c_char_p
     for name in EXPORTS:
-        f = getattr(lib, name)
-        if f.restype is None or f.restype is ctypes.c_int:
-            if name not in ("pw_strerror", "pw_last_error"):
-                f.restype = ctypes.c_int
+        if name not in ("pw_strerror", "pw_last_error", "pw_kernel_launches"):
+            getattr(lib, name).restype = ctypes.c_int
     _LIB = lib
     return lib
+
+
+def kernel_launches() -> int:
+    """Kernels launched by the library in this process so far."""
+    return int(load().pw_kernel_launches())
 
 
 def _check(status: int):
@@ -179,6 +189,17 @@ class Context:
         cur = torch.cuda.current_stream()
         if cur.cuda_stream != self.stream.cuda_stream:
             self.stream.wait_stream(cur)
+
+    # -- diagnostics ----------------------------------------------------------------
+    def profile(self, on=True):
+        _check(load().pw_profile_enable(self._h, 1 if on else 0))
+
+    def profile_read(self):
+        """{class: (milliseconds, launches)} accumulated since the last read."""
+        ms = np.zeros(len(PROF_CLASSES))
+        n = np.zeros(len(PROF_CLASSES), dtype=np.int64)
+        _check(load().pw_profile_read(self._h, _dptr(ms), n.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))))
+        return {c: (float(ms[i]), int(n[i])) for i, c in enumerate(PROF_CLASSES)}
 
     # -- queries --------------------------------------------------------------------
     def gvectors(self):

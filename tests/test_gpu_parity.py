@@ -265,3 +265,18 @@ def test_full_size_fp64_at_scale_sampled_bands():
         ctx.hamiltonian_apply(t32, h32, precision=pwlib.PW_MIXED)
         torch.cuda.synchronize()
         assert rel(h32.cpu().numpy().astype(np.complex128), ref).max() < 1e-5
+
+
+def test_rayleigh_ritz_many_bands():
+    """Jacobi eigensolver on a 200 x 200 reduced problem (odd pairing rounds, many sweeps)."""
+    prob = W.make_problem("tiny_gamma_fp64", nband=200)
+    ham = O.Hamiltonian.from_problem(prob)
+    with pwlib.Context.from_problem(prob) as ctx:
+        psi = W.random_block(109, ctx.npw, 199)   # odd band count: one idle slot per pairing round
+        t = to_dev(psi)
+        eig, res = ctx.rayleigh_ritz(t)
+        y = psi
+        for _ in range(2):
+            y, _ = O.s_ortho(y, ham.apply_s(y))
+        lam, *_ = O.rayleigh_ritz(y, ham.apply_h(y), ham.apply_s(y))
+        np.testing.assert_allclose(eig, lam, atol=1e-10, rtol=0)
