@@ -147,6 +147,20 @@ PW_API int pw_chebfi_solve(pw_ctx* ctx, void* psi, int64_t ldpsi, int nband, int
 PW_API int pw_density_grad(pw_ctx* ctx, const void* a, const void* b, int64_t ld, int nband,
                            const double* w, double* out, int accumulate);
 
+/* H psi = (T + V_loc + P D P^dagger) psi in FP64, like pw_hamiltonian_apply with
+ * spsi = NULL, but without allocating any device memory.  The paper has no
+ * counterpart; this exists for callers that may not call cudaMalloc/cudaFree at
+ * apply time (a framework allocator that owns all device memory, a hard memory
+ * cap, a loop that cannot absorb cudaFree's device-wide synchronisation).  All
+ * scratch lives in one static 32 MiB device array inside the library, held by
+ * every GPU that loads it until process exit.  The first call on a device looks
+ * up that array's address (cudaGetSymbolAddress); make it before any stream
+ * capture.  Calls share the array: calls that overlap on the GPU race.  Bands are
+ * processed in chunks that fit; PW_EINVAL if even one band's scratch (half-box
+ * planes + projections) exceeds 32 MiB.  psi, hpsi: complex128 device blocks. */
+PW_API int pw_hamiltonian_apply_noalloc(pw_ctx* ctx, const void* psi, int64_t ldpsi, int nband,
+                                        void* hpsi, int64_t ldout);
+
 /* Diagnostics.  Per-context timing of kernel classes with CUDA events recorded
  * on the context's stream around each launch (no extra synchronisation while
  * enabled).  pw_profile_read synchronises the stream, returns the accumulated

@@ -26,7 +26,7 @@ STATUS = {0: "PW_OK", -1: "PW_EINVAL", -2: "PW_ENOMEM", -3: "PW_ECUDA", -4: "PW_
 EXPORTS = ("pw_ctx_create", "pw_ctx_destroy", "pw_ctx_set_stream", "pw_ctx_info", "pw_ctx_gvectors",
            "pw_ctx_projectors", "pw_hamiltonian_apply", "pw_spectrum_bounds", "pw_chebyshev_filter",
            "pw_rayleigh_ritz", "pw_chebfi_solve", "pw_density_grad", "pw_profile_enable", "pw_profile_read",
-           "pw_kernel_launches", "pw_strerror", "pw_last_error")
+           "pw_kernel_launches", "pw_hamiltonian_apply_noalloc", "pw_strerror", "pw_last_error")
 
 PROF_CLASSES = ("plane_inv", "xline", "plane_fwd", "gemm_proj", "gemm_back", "small", "rr")
 
@@ -72,6 +72,7 @@ def load(path: Optional[str] = None):
     lib.pw_rayleigh_ritz.argtypes = [vp, vp, i64, ci, vp, pd, pd]
     lib.pw_chebfi_solve.argtypes = [vp, vp, i64, ci, ci, ci, ci, vp, ci, pd, pd, pd]
     lib.pw_density_grad.argtypes = [vp, vp, vp, i64, ci, pd, vp, ci]
+    lib.pw_hamiltonian_apply_noalloc.argtypes = [vp, vp, i64, ci, vp, i64]
     lib.pw_profile_enable.argtypes = [vp, ci]
     lib.pw_profile_read.argtypes = [vp, pd, ctypes.POINTER(ctypes.c_int64)]
     lib.pw_kernel_launches.restype = ctypes.c_uint64
@@ -231,6 +232,17 @@ class Context:
         self._sync_stream()
         _check(load().pw_hamiltonian_apply(self._h, ctypes.c_void_p(psi.data_ptr()), ld, m,
                                            ctypes.c_void_p(hpsi.data_ptr()), sp, ldo, precision))
+
+    def hamiltonian_apply_noalloc(self, psi, hpsi):
+        """H psi (FP64) using only the library's static scratch: no device allocation."""
+        import torch
+        psi, m, ld = _block(psi, torch.complex128, "psi")
+        hpsi, m2, ldo = _block(hpsi, torch.complex128, "hpsi")
+        if m2 < m:
+            raise ValueError("hpsi has fewer bands than psi")
+        self._sync_stream()
+        _check(load().pw_hamiltonian_apply_noalloc(self._h, ctypes.c_void_p(psi.data_ptr()), ld, m,
+                                                   ctypes.c_void_p(hpsi.data_ptr()), ldo))
 
     def spectrum_bounds(self, psi=None, lanczos_steps=10, v0=None):
         import torch
