@@ -310,14 +310,11 @@ def run_ours(args):
     ms_c, n_c = prof[dom]
     per_launch_s = ms_c / 1e3 / max(n_c, 1)
     c8 = 8  # complex64 bytes
-    nplane_planes = None
     box = prob.box
-    # half-box planes: 2r+1 x-planes with sphere content
     mill, _ = ctx.gvectors()
-    nplane = len(np.unique(mill[:, 0]))
-    bb = max(1, min(M, (256 << 20) // (nplane * box[1] * box[2] * 16)))
-    batches = [min(bb, M - i) for i in range(0, M, bb)]
-    nb_avg = M / len(batches)
+    nplane = len(np.unique(mill[:, 0]))       # x-planes holding sphere coefficients
+    batches = max(1, prof["plane_inv"][1] // max(1, args.steps * m))
+    nb_avg = M / batches                      # bands per FFT launch (library batching)
     half = nplane * box[1] * box[2]
     if dom == "plane_inv":
         bound, achieved_units = "hbm", nb_avg * (npw + half) * c8

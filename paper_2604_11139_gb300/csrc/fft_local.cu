@@ -121,10 +121,10 @@ __device__ __forceinline__ void fft_stage(C* buf, int nlines, int ls, int es, in
   }
 }
 
-// full in-place transform of a batch of lines.  S = +1: inverse (DIF), S = -1:
+// full in-place transform of a batch of lines (any length of the form 2^a 3^b 5^c).  S = +1: inverse (DIF), S = -1:
 // forward (DIT, stages reversed).  Ends with a block barrier.
 template <typename C, int S, bool LINE_FAST>
-__device__ void fft_lines(C* buf, int nlines, int ls, int es, const FftDim& d, const C* __restrict__ tw) {
+__device__ void fft_lines_generic(C* buf, int nlines, int ls, int es, const FftDim& d, const C* __restrict__ tw) {
   constexpr bool DIT = (S < 0);
   for (int s0 = 0; s0 < d.nst; ++s0) {
     const int s = DIT ? (d.nst - 1 - s0) : s0;
@@ -138,6 +138,120 @@ __device__ void fft_lines(C* buf, int nlines, int ls, int es, const FftDim& d, c
     }
     __syncthreads();
   }
+}
+
+
+// ---- the same transform with the length known at compile time --------------------
+// The radix plan is the one the host builds (greedy 8, 4, 5, 3, 2), so the stage
+// twiddle offsets in FftDim apply unchanged.  All index arithmetic is by
+// compile-time constants; one barrier per stage.
+struct CPlan {
+  int nst;
+  int radix[kMaxStages];
+  int L[kMaxStages];
+};
+constexpr CPlan make_cplan(int n) {
+  CPlan p{};
+  p.nst = 0;
+  int m = n;
+  const int order[5] = {8, 4, 5, 3, 2};
+  for (int i = 0; i < 5; ++i) {
+    const int r = order[i];
+    while (m > 1 && m % r == 0) {
+      p.radix[p.nst++] = r;
+      m /= r;
+    }
+  }
+  int L = n;
+  for (int s = 0; s < p.nst; ++s) {
+    p.L[s] = L;
+    L /= p.radix[s];
+  }
+  return p;
+}
+
+template <typename C, int S, bool DIT, bool LINE_FAST, int LF, int N, int R, int L>
+__device__ __forceinline__ void stage_c(C* buf, int nlines, int ls, int es, const C* __restrict__ tws) {
+  constexpr int Q = L / R, NBF = N / R;
+  const int total = LINE_FAST ? LF * NBF : nlines * NBF;
+  for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
+    int line, bf;
+    if (LINE_FAST) {
+      line = idx % LF;
+      bf = idx / LF;
+      if (line >= nlines) continue;
+    } else {
+      bf = idx % NBF;
+      line = idx / NBF;
+    }
+    const int blk = bf / Q, j = bf - blk * Q;
+    C* base = buf + line * ls + (blk * L + j) * es;
+    C x[R];
+#pragma unroll
+    for (int m = 0; m < R; ++m) x[m] = base[m * Q * es];
+    if (DIT) {
+      if (Q > 1 && j) {
+#pragma unroll
+        for (int m = 1; m < R; ++m) {
+          C w = tws[j * (R - 1) + m - 1];
+          if (S > 0) w = cconj(w);
+          x[m] = cmul(x[m], w);
+        }
+      }
+      dftR<C, S, R>(x);
+    } else {
+      dftR<C, S, R>(x);
+      if (Q > 1 && j) {
+#pragma unroll
+        for (int m = 1; m < R; ++m) {
+          C w = tws[j * (R - 1) + m - 1];
+          if (S > 0) w = cconj(w);
+          x[m] = cmul(x[m], w);
+        }
+      }
+    }
+#pragma unroll
+    for (int m = 0; m < R; ++m) base[m * Q * es] = x[m];
+  }
+}
+
+template <typename C, int S, bool LINE_FAST, int LF, int N, int S0>
+__device__ __forceinline__ void stages_c(C* buf, int nlines, int ls, int es, const C* __restrict__ tw,
+                                         const FftDim& d) {
+  constexpr CPlan P = make_cplan(N);
+  if constexpr (S0 < P.nst) {
+    constexpr bool DIT = (S < 0);
+    constexpr int s = DIT ? P.nst - 1 - S0 : S0;
+    stage_c<C, S, DIT, LINE_FAST, LF, N, P.radix[s], P.L[s]>(buf, nlines, ls, es, tw + d.tw_off[s]);
+    __syncthreads();
+    stages_c<C, S, LINE_FAST, LF, N, S0 + 1>(buf, nlines, ls, es, tw, d);
+  }
+}
+
+template <typename C, int S, bool LINE_FAST, int LF, int N>
+__device__ __noinline__ void fft_n(C* buf, int nlines, int ls, int es, const C* __restrict__ tw, FftDim d) {
+  stages_c<C, S, LINE_FAST, LF, N, 0>(buf, nlines, ls, es, tw, d);
+}
+
+// dispatch: specialised lengths of the bundled workloads, generic otherwise.  Ends with a barrier.
+template <typename C, int S, bool LINE_FAST, int LF = 1>
+__device__ void fft_lines(C* buf, int nlines, int ls, int es, const FftDim& d, const C* __restrict__ tw) {
+  if (!LINE_FAST || es == LF) {
+    switch (d.n) {
+      case 16: fft_n<C, S, LINE_FAST, LF, 16>(buf, nlines, ls, es, tw, d); return;
+      case 18: fft_n<C, S, LINE_FAST, LF, 18>(buf, nlines, ls, es, tw, d); return;
+      case 20: fft_n<C, S, LINE_FAST, LF, 20>(buf, nlines, ls, es, tw, d); return;
+      case 24: fft_n<C, S, LINE_FAST, LF, 24>(buf, nlines, ls, es, tw, d); return;
+      case 30: fft_n<C, S, LINE_FAST, LF, 30>(buf, nlines, ls, es, tw, d); return;
+      case 64: fft_n<C, S, LINE_FAST, LF, 64>(buf, nlines, ls, es, tw, d); return;
+      case 72: fft_n<C, S, LINE_FAST, LF, 72>(buf, nlines, ls, es, tw, d); return;
+      case 90: fft_n<C, S, LINE_FAST, LF, 90>(buf, nlines, ls, es, tw, d); return;
+      case 96: fft_n<C, S, LINE_FAST, LF, 96>(buf, nlines, ls, es, tw, d); return;
+      case 120: fft_n<C, S, LINE_FAST, LF, 120>(buf, nlines, ls, es, tw, d); return;
+      default: break;
+    }
+  }
+  fft_lines_generic<C, S, LINE_FAST>(buf, nlines, ls, es, d, tw);
 }
 
 __device__ __forceinline__ int pmod(int a, int n) { int r = a % n; return r < 0 ? r + n : r; }
@@ -205,13 +319,13 @@ __global__ void __launch_bounds__(kThreads) k_xline(cplx<T>* __restrict__ hb, in
     X[pmod(sp.plane_h[p], n1) * lyz + l] = base[(int64_t)p * nyz + yz0 + l];
   }
   __syncthreads();
-  fft_lines<C, +1, true>(X, ln, 1, lyz, plan.d[0], tw);
+  fft_lines<C, +1, true, 32>(X, ln, 1, lyz, plan.d[0], tw);
   for (int i = threadIdx.x; i < n1 * ln; i += blockDim.x) {
     const int x = i / ln, l = i - x * ln;
     X[x * lyz + l] = cscale(X[x * lyz + l], vperm[(int64_t)x * nyz + yz0 + l]);
   }
   __syncthreads();
-  fft_lines<C, -1, true>(X, ln, 1, lyz, plan.d[0], tw);
+  fft_lines<C, -1, true, 32>(X, ln, 1, lyz, plan.d[0], tw);
   for (int i = threadIdx.x; i < sp.nplane * ln; i += blockDim.x) {
     const int p = i / ln, l = i - p * ln;
     base[(int64_t)p * nyz + yz0 + l] = X[pmod(sp.plane_h[p], n1) * lyz + l];
@@ -296,8 +410,8 @@ __global__ void __launch_bounds__(kThreads) k_xline_density(const cplx<T>* __res
       if (two) Y[pmod(sp.plane_h[p], n1) * lyz + l] = hbb[off];
     }
     __syncthreads();
-    fft_lines<C, +1, true>(X, ln, 1, lyz, plan.d[0], tw);
-    if (two) fft_lines<C, +1, true>(Y, ln, 1, lyz, plan.d[0], tw);
+    fft_lines<C, +1, true, 8>(X, ln, 1, lyz, plan.d[0], tw);
+    if (two) fft_lines<C, +1, true, 8>(Y, ln, 1, lyz, plan.d[0], tw);
     const C* Bv = two ? Y : X;
     const double wb = (double)w[b];
 #pragma unroll

@@ -16,6 +16,7 @@
 #include "la.cuh"
 #include "pw_internal.cuh"
 #include "setup.cuh"
+#include "tc.cuh"
 
 namespace pw {
 
@@ -243,11 +244,104 @@ Epi<T> epi(int mode, cplx<T>* out, int64_t ldo, T alpha = 1) {
   return e;
 }
 
-int band_batch(const pw_ctx* ctx, int nband) {
-  // keep a batch's half-box planes around 256 MB
-  const size_t per = (size_t)ctx->sp.nplane * ctx->n[1] * ctx->n[2] * 16;
-  int bb = (int)std::max<size_t>(1, ((size_t)256 << 20) / std::max<size_t>(per, 1));
+// Bands per FFT batch.  complex64: keep a batch's half-box planes near 48 MB so that
+// pass 1 -> pass 2 -> pass 3 hand the planes over through the 129 MB L2 instead of
+// HBM; complex128 (DFMA-bound) batches near 256 MB for fewer, larger launches.
+int band_batch(const pw_ctx* ctx, int nband, size_t elem = 16) {
+  const size_t per = (size_t)ctx->sp.nplane * ctx->n[1] * ctx->n[2] * elem;
+  const size_t target = (elem == 8) ? ((size_t)48 << 20) : ((size_t)256 << 20);
+  int bb = (int)std::max<size_t>(1, target / std::max<size_t>(per, 1));
   return std::max(1, std::min(bb, nband));
+}
+
+// ---------------------------------------------------------------------------
+// tensor-core operands and helpers of the mixed path
+// ---------------------------------------------------------------------------
+int64_t round64(int64_t x) { return (x + 63) / 64 * 64; }
+
+int ensure_tc(pw_ctx* ctx) {
+  if (ctx->tc_built_pieces == ctx->tc_pieces && ctx->tcA1) return PW_OK;
+  if (!tc::available()) return set_error(PW_EUNSUPPORTED, "cuTensorMapEncodeTiled is not available");
+  const cudaStream_t st = ctx->stream;
+  CU_TRY(cudaStreamSynchronize(st), "tc sync");
+  if (ctx->tcA1) { cudaFree(ctx->tcA1); ctx->tcA1 = nullptr; }
+  if (ctx->tcA2) { cudaFree(ctx->tcA2); ctx->tcA2 = nullptr; }
+  const int np = ctx->nproj, npw = ctx->npw, pc = ctx->tc_pieces;
+  ctx->kp1 = round64(2 * (int64_t)npw);
+  ctx->kp2 = round64(2 * (int64_t)np);
+  CU_TRY(cudaMalloc(&ctx->tcA1, sizeof(__nv_bfloat16) * (size_t)pc * 2 * np * ctx->kp1), "tc A1 allocation");
+  CU_TRY(cudaMalloc(&ctx->tcA2, sizeof(__nv_bfloat16) * (size_t)pc * 2 * npw * ctx->kp2), "tc A2 allocation");
+  if (!ctx->tc_err) {
+    CU_TRY(cudaMalloc(&ctx->tc_err, sizeof(int)), "tc flag allocation");
+    CU_TRY(cudaMemsetAsync(ctx->tc_err, 0, sizeof(int), st), "tc flag reset");
+  }
+  CU_TRY(tc::build_a(ctx->P64, npw, np, pc, (__nv_bfloat16*)ctx->tcA1, ctx->kp1, 2 * (int64_t)np * ctx->kp1,
+                     (__nv_bfloat16*)ctx->tcA2, ctx->kp2, 2 * (int64_t)npw * ctx->kp2, st), "tc operands");
+  ctx->tc_built_pieces = pc;
+  return PW_OK;
+}
+
+int check_tc_flag(pw_ctx* ctx) {
+  if (!ctx->tc_err) return PW_OK;
+  int h = 0;
+  CU_TRY(cudaMemcpyAsync(&h, ctx->tc_err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream), "tc flag copy");
+  CU_TRY(cudaStreamSynchronize(ctx->stream), "tc flag sync");
+  if (h) {
+    ctx->poisoned = true;
+    return set_error(PW_ETIMEDOUT, "a tensor-core GEMM wait expired (stage %d)", h);
+  }
+  return PW_OK;
+}
+
+// bf16 pieces [pieces][nb][pitch] of a complex64 block (rows = 2 * nrow reals)
+int tc_split(pw_ctx* ctx, const float2* x, int64_t ld, int nrow, int nb, int64_t pitch, int slot,
+             __nv_bfloat16** out) {
+  const int pc = ctx->tc_pieces;
+  WS(buf, __nv_bfloat16, slot, (size_t)pc * nb * pitch);
+  CU_TRY(tc::split_f32((const float*)x, 2 * ld, 2 * nrow, nb, pc, buf, pitch, (int64_t)nb * pitch, ctx->stream),
+         "bf16 split");
+  *out = buf;
+  return PW_OK;
+}
+
+// C (np x nb complex64, ld np) = P^dagger Y from the bf16 pieces of Y
+int tc_project(pw_ctx* ctx, const __nv_bfloat16* ysplit, int nb, float2* Cout) {
+  const int np = ctx->nproj, npw = ctx->npw, pc = ctx->tc_pieces;
+  const int M = 2 * np, N = nb, K = 2 * npw;
+  // split K so that the persistent grid gets a whole number of units per SM (152 SMs)
+  const int tiles = ((M + 127) / 128) * ((N + 127) / 128);
+  int nsm = 152, dev = 0;
+  if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  int ns = 1;
+  double best = -1;
+  for (int c = 1; c <= std::max(1, std::min(64, K / 256)); ++c) {
+    const int cc = tc::split_count(K, c);
+    const int u = cc * tiles;
+    const double eff = (double)u / ((double)((u + nsm - 1) / nsm) * nsm);
+    if (eff > best + 1e-9) { best = eff; ns = cc; }
+  }
+  WS(part, float, WS_TCPART, (size_t)ns * M * N);
+  tc::Operand A{(const __nv_bfloat16*)ctx->tcA1, M, ctx->kp1, (int64_t)M * ctx->kp1};
+  tc::Operand B{ysplit, N, ctx->kp1, (int64_t)N * ctx->kp1};
+  tc::TcEpi e{};
+  e.mode = tc::TC_EPI_PARTIAL;
+  e.part = part;
+  e.part_ld = M;
+  e.part_split_stride = (int64_t)M * N;
+  CU_TRY(tc::gemm(A, B, M, N, K, pc, ns, e, ctx->tc_err, ctx->stream), "tc projection");
+  CU_TRY(tc::reduce_partials(part, ns, (int64_t)M * N, M, M, N, (float*)Cout, 2 * (int64_t)np, ctx->stream),
+         "tc reduce");
+  return PW_OK;
+}
+
+// back-projection Y (2 npw real rows x nb) (+)= P Z with the given epilogue (out / yk / split fields set by caller)
+int tc_backproject(pw_ctx* ctx, const __nv_bfloat16* zsplit, int nb, tc::TcEpi e) {
+  const int np = ctx->nproj, npw = ctx->npw, pc = ctx->tc_pieces;
+  const int M = 2 * npw, N = nb, K = 2 * np;
+  tc::Operand A{(const __nv_bfloat16*)ctx->tcA2, M, ctx->kp2, (int64_t)M * ctx->kp2};
+  tc::Operand B{zsplit, N, ctx->kp2, (int64_t)N * ctx->kp2};
+  CU_TRY(tc::gemm(A, B, M, N, K, pc, 1, e, ctx->tc_err, ctx->stream), "tc back-projection");
+  return PW_OK;
 }
 
 // ---------------------------------------------------------------------------
@@ -259,7 +353,7 @@ int apply_impl(pw_ctx* ctx, const cplx<T>* psi, int64_t ldpsi, int nband, cplx<T
   using C = cplx<T>;
   const int npw = ctx->npw, np = ctx->nproj;
   const cudaStream_t st = ctx->stream;
-  const int bb = band_batch(ctx, nband);
+  const int bb = band_batch(ctx, nband, sizeof(C));
   const int64_t hb_bs = (int64_t)ctx->sp.nplane * ctx->n[1] * ctx->n[2];
   WS(hb, C, WS_HB, hb_bs * bb);
   WS(Cm, C, WS_C, (size_t)np * nband);
@@ -268,7 +362,28 @@ int apply_impl(pw_ctx* ctx, const cplx<T>* psi, int64_t ldpsi, int nband, cplx<T
   WS(sp, C, WS_SPLIT, (size_t)ns * np * nband);
   CU_TRY(launch_local_apply<T>(ctx->plan, Prec<T>::tw(ctx), ctx->sp, Prec<T>::vp(ctx), Prec<T>::kin(ctx), psi,
                                ldpsi, nband, hpsi, ldout, hb, bb, st, ctx), "local apply");
-  if (np > 0) {
+  if (np > 0 && std::is_same<T, float>::value) {
+    // mixed precision: BF16-split tensor-core projector GEMMs
+    PW_TRY(ensure_tc(ctx));
+    __nv_bfloat16 *ys, *zs;
+    {
+      ProfScope ps(ctx, PW_PROF_GEMM_PROJ);
+      PW_TRY(tc_split(ctx, (const float2*)psi, ldpsi, npw, nband, ctx->kp1, WS_YSPLIT, &ys));
+      PW_TRY(tc_project(ctx, ys, nband, (float2*)Cm));
+    }
+    {
+      ProfScope ps(ctx, PW_PROF_SMALL);
+      CU_TRY(launch_dblock<T>(np, nband, Prec<T>::D(ctx), ctx->blk0, ctx->blklen, Cm, np, Z, np, st), "D block");
+      PW_TRY(tc_split(ctx, (const float2*)Z, np, np, nband, ctx->kp2, WS_ZSPLIT, &zs));
+    }
+    ProfScope ps(ctx, PW_PROF_GEMM_BACK);
+    tc::TcEpi e{};
+    e.mode = tc::TC_EPI_ACCUM;
+    e.out = (float*)hpsi;
+    e.ldo = 2 * ldout;
+    e.alpha = 1.f;
+    PW_TRY(tc_backproject(ctx, zs, nband, e));
+  } else if (np > 0) {
     {
       ProfScope ps(ctx, PW_PROF_GEMM_PROJ);
       CU_TRY(launch_cgemm<T>(1, 0, np, nband, npw, Prec<T>::P(ctx), npw, psi, ldpsi, epi<T>(EPI_STORE, Cm, np), ns,
@@ -308,7 +423,7 @@ int filter_impl(pw_ctx* ctx, cplx<T>* psi, int64_t ldpsi, int nband, int degree,
   if (!(b > a)) return set_error(PW_EINVAL, "filter interval needs upper > lower (a=%g, b=%g)", a, b);
   const int npw = ctx->npw, np = ctx->nproj;
   const cudaStream_t st = ctx->stream;
-  const int bb = band_batch(ctx, nband);
+  const int bb = band_batch(ctx, nband, sizeof(C));
   const int64_t hb_bs = (int64_t)ctx->sp.nplane * ctx->n[1] * ctx->n[2];
   WS(hb, C, WS_HB, hb_bs * bb);
   WS(Cm, C, WS_C, (size_t)np * nband);
@@ -321,6 +436,13 @@ int filter_impl(pw_ctx* ctx, cplx<T>* psi, int64_t ldpsi, int nband, int degree,
   C* buf[3] = {psi, Y1, Y2};
   const int64_t ld[3] = {ldpsi, npw, npw};
   const double cc = 0.5 * (b + a), e = 0.5 * (b - a);
+  constexpr bool kMixed = std::is_same<T, float>::value;
+  __nv_bfloat16* ys = nullptr;
+  if (kMixed && np > 0) {
+    PW_TRY(ensure_tc(ctx));
+    ProfScope ps(ctx, PW_PROF_GEMM_PROJ);
+    PW_TRY(tc_split(ctx, (const float2*)psi, ldpsi, npw, nband, ctx->kp1, WS_YSPLIT, &ys));
+  }
   for (int k = 0; k < degree; ++k) {
     C* cur = buf[k % 3];
     C* prev = buf[(k + 2) % 3];
@@ -330,6 +452,48 @@ int filter_impl(pw_ctx* ctx, cplx<T>* psi, int64_t ldpsi, int nband, int degree,
     // W = (T + V) Y_k
     CU_TRY(launch_local_apply<T>(ctx->plan, Prec<T>::tw(ctx), ctx->sp, Prec<T>::vp(ctx), Prec<T>::kin(ctx), cur,
                                  ldc, nband, dst, ldd, hb, bb, st, ctx), "filter local");
+    if (kMixed && np > 0) {
+      {
+        ProfScope ps(ctx, PW_PROF_GEMM_PROJ);
+        PW_TRY(tc_project(ctx, ys, nband, (float2*)Cm));
+        if (ctx->has_q) {
+          __nv_bfloat16* wsp;
+          PW_TRY(tc_split(ctx, (const float2*)dst, ldd, npw, nband, ctx->kp1, WS_WSPLIT, &wsp));
+          PW_TRY(tc_project(ctx, wsp, nband, (float2*)Cw));
+        }
+      }
+      __nv_bfloat16* zs;
+      {
+        ProfScope ps(ctx, PW_PROF_SMALL);
+        if (!ctx->has_q) {
+          CU_TRY(launch_dblock<T>(np, nband, Prec<T>::D(ctx), ctx->blk0, ctx->blklen, Cm, np, Z, np, st), "filter D");
+        } else {
+          CU_TRY(launch_cgemm<T>(0, 0, np, nband, np, Prec<T>::E(ctx), np, Cm, np, epi<T>(EPI_STORE, Z, np), 1, spl,
+                                 st), "filter E C");
+          CU_TRY(launch_cgemm<T>(0, 0, np, nband, np, Prec<T>::K(ctx), np, Cw, np, epi<T>(EPI_ACCUM, Z, np, (T)-1),
+                                 1, spl, st), "filter K Cw");
+        }
+        PW_TRY(tc_split(ctx, (const float2*)Z, np, np, nband, ctx->kp2, WS_ZSPLIT, &zs));
+      }
+      ProfScope ps(ctx, PW_PROF_GEMM_BACK);
+      tc::TcEpi te{};
+      te.mode = tc::TC_EPI_CHEB;
+      te.out = (float*)dst;
+      te.ldo = 2 * ldd;
+      te.yk = (const float*)cur;
+      te.ldyk = 2 * ldc;
+      te.ykm1 = (k == 0) ? nullptr : (const float*)prev;
+      te.ldykm1 = 2 * ldp;
+      te.alpha = (float)alpha;
+      te.beta = 1.f;
+      te.shift = (float)cc;
+      te.split = ys;
+      te.split_ld = ctx->kp1;
+      te.split_piece_stride = (int64_t)nband * ctx->kp1;
+      te.out_pieces = (k + 1 < degree) ? ctx->tc_pieces : 0;
+      PW_TRY(tc_backproject(ctx, zs, nband, te));
+      continue;
+    }
     Epi<T> ce = epi<T>(EPI_CHEB, dst, ldd, alpha);
     ce.beta = (T)1;
     ce.shift = (T)cc;
@@ -399,6 +563,7 @@ int check_flag(pw_ctx* ctx, int* flag_dev, const char* what) {
 }
 
 int rr_impl(pw_ctx* ctx, double2* Y, int64_t ldy, int m, double2* hpsi_out, double* eig_h, double* resid_h) {
+  PW_TRY(check_tc_flag(ctx));
   ProfScope rr_scope(ctx, PW_PROF_RR);
   const int npw = ctx->npw;
   const cudaStream_t st = ctx->stream;
@@ -752,6 +917,9 @@ int create_impl(const pw_problem_desc* d, void* stream, pw_ctx** out) {
 void destroy_impl(pw_ctx* ctx) {
   if (!ctx) return;
   cudaStreamSynchronize(ctx->stream);
+  if (ctx->tcA1) cudaFree(ctx->tcA1);
+  if (ctx->tcA2) cudaFree(ctx->tcA2);
+  if (ctx->tc_err) cudaFree(ctx->tc_err);
   for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
   for (void* p : ctx->owned) cudaFree(p);
   for (auto& b : ctx->ws)

@@ -163,6 +163,13 @@ struct pw_ctx {
   double2* E64 = nullptr;   // E = (I - K P^dagger P) D
   float2* K32 = nullptr;
   float2* E32 = nullptr;
+  // tensor-core operands of the mixed path: bf16 pieces of the real-ified P (built on first use)
+  int tc_pieces = 3;         // bf16 pieces per operand (2: 3 products, 3: 6 products)
+  int tc_built_pieces = 0;   // pieces the operands below were built with (0 = not built)
+  void* tcA1 = nullptr;      // [pieces][2 nproj][kp1]
+  void* tcA2 = nullptr;      // [pieces][2 npw][kp2]
+  int64_t kp1 = 0, kp2 = 0;  // pitches (elements): 2 npw and 2 nproj rounded up to 64
+  int* tc_err = nullptr;     // device flag set by a tensor-core kernel whose bounded wait expired
   // kernel-class timing (pw_profile_*)
   struct ProfRec { int cls; cudaEvent_t a, b; };
   bool prof_on = false;
@@ -183,6 +190,7 @@ struct pw_ctx {
 namespace pw {
 enum WsSlot {
   WS_HB = 0, WS_C, WS_Z, WS_SPLIT, WS_Y1, WS_Y2, WS_CW,      // H-apply and filter
+  WS_YSPLIT, WS_WSPLIT, WS_ZSPLIT, WS_TCPART, WS_TCERR,      // tensor-core mixed path
   WS_HY, WS_SY, WS_ROT, WS_Y32,                              // Rayleigh-Ritz / solve
   WS_GRAM, WS_GRAM2, WS_LINV, WS_TMP, WS_U, WS_JAC, WS_EIG,  // subspace matrices
   WS_LZ, WS_RQ, WS_DEN, WS_SCAL, WS_NUM
