@@ -18,6 +18,8 @@
 // (digit-reversed in, natural out); between them the data stays in the
 // digit-reversed (y,z) order and the potential grid is stored permuted to it,
 // so no transposition or bit-reversal pass exists.
+#include <math.h>
+
 #include "pw_internal.cuh"
 
 namespace pw {
@@ -71,12 +73,64 @@ template <typename C, int S> __device__ __forceinline__ void dft5(C* x) {
   x[1] = cadd(a1, b1); x[4] = csub(a1, b1);
   x[2] = cadd(a2, b2); x[3] = csub(a2, b2);
 }
+// exp(-2 pi i m / R) for the composite in-register radices, filled by fft_set_constants
+// (host cos/sin in double).  Offsets: R=6: 0, 9: 6, 10: 15, 12: 25, 15: 37, 16: 52.
+__constant__ double2 c_wtab64[68];
+__constant__ float2 c_wtab32[68];
+template <int R> struct WOff;
+template <> struct WOff<6> { static constexpr int v = 0; };
+template <> struct WOff<9> { static constexpr int v = 6; };
+template <> struct WOff<10> { static constexpr int v = 15; };
+template <> struct WOff<12> { static constexpr int v = 25; };
+template <> struct WOff<15> { static constexpr int v = 37; };
+template <> struct WOff<16> { static constexpr int v = 52; };
+
+template <typename C, int S, int R> __device__ __forceinline__ C wconst(int m) {
+  C w;
+  if constexpr (sizeof(C) == 16) { const double2 t = c_wtab64[WOff<R>::v + m]; w.x = t.x; w.y = t.y; }
+  else { const float2 t = c_wtab32[WOff<R>::v + m]; w.x = t.x; w.y = t.y; }
+  if (S > 0) w.y = -w.y;
+  return w;
+}
+
+template <typename C, int S, int R> __device__ __forceinline__ void dftR(C* x);
+
+// R = R1 R2 in registers: R2 DFTs of length R1 (stride R2), constant twiddles w_R^{b k1},
+// R1 DFTs of length R2; natural-order output X[k1 + R1 k2].
+template <typename C, int S, int R, int R1, int R2> __device__ __forceinline__ void dft_comp(C* x) {
+  C t[R];
+#pragma unroll
+  for (int b = 0; b < R2; ++b) {
+    C u[R1];
+#pragma unroll
+    for (int a = 0; a < R1; ++a) u[a] = x[b + R2 * a];
+    dftR<C, S, R1>(u);
+#pragma unroll
+    for (int k1 = 0; k1 < R1; ++k1) t[b + R2 * k1] = (b * k1 == 0) ? u[k1] : cmul(u[k1], wconst<C, S, R>(b * k1));
+  }
+#pragma unroll
+  for (int k1 = 0; k1 < R1; ++k1) {
+    C v[R2];
+#pragma unroll
+    for (int b = 0; b < R2; ++b) v[b] = t[b + R2 * k1];
+    dftR<C, S, R2>(v);
+#pragma unroll
+    for (int k2 = 0; k2 < R2; ++k2) x[k1 + R1 * k2] = v[k2];
+  }
+}
+
 template <typename C, int S, int R> __device__ __forceinline__ void dftR(C* x) {
   if constexpr (R == 2) dft2<C, S>(x[0], x[1]);
   else if constexpr (R == 3) dft3<C, S>(x);
   else if constexpr (R == 4) dft4<C, S>(x);
   else if constexpr (R == 5) dft5<C, S>(x);
-  else dft8<C, S>(x);
+  else if constexpr (R == 8) dft8<C, S>(x);
+  else if constexpr (R == 6) dft_comp<C, S, 6, 3, 2>(x);
+  else if constexpr (R == 9) dft_comp<C, S, 9, 3, 3>(x);
+  else if constexpr (R == 10) dft_comp<C, S, 10, 5, 2>(x);
+  else if constexpr (R == 12) dft_comp<C, S, 12, 4, 3>(x);
+  else if constexpr (R == 15) dft_comp<C, S, 15, 5, 3>(x);
+  else dft_comp<C, S, 16, 4, 4>(x);
 }
 
 // one radix-R stage over `nlines` lines (line stride ls, element stride es)
@@ -130,7 +184,13 @@ __device__ void fft_lines_generic(C* buf, int nlines, int ls, int es, const FftD
     const int s = DIT ? (d.nst - 1 - s0) : s0;
     const C* tws = tw + d.tw_off[s];
     switch (d.radix[s]) {
+      case 16: fft_stage<C, S, DIT, LINE_FAST, 16>(buf, nlines, ls, es, d.n, d.L[s], tws); break;
+      case 15: fft_stage<C, S, DIT, LINE_FAST, 15>(buf, nlines, ls, es, d.n, d.L[s], tws); break;
+      case 12: fft_stage<C, S, DIT, LINE_FAST, 12>(buf, nlines, ls, es, d.n, d.L[s], tws); break;
+      case 10: fft_stage<C, S, DIT, LINE_FAST, 10>(buf, nlines, ls, es, d.n, d.L[s], tws); break;
+      case 9: fft_stage<C, S, DIT, LINE_FAST, 9>(buf, nlines, ls, es, d.n, d.L[s], tws); break;
       case 8: fft_stage<C, S, DIT, LINE_FAST, 8>(buf, nlines, ls, es, d.n, d.L[s], tws); break;
+      case 6: fft_stage<C, S, DIT, LINE_FAST, 6>(buf, nlines, ls, es, d.n, d.L[s], tws); break;
       case 5: fft_stage<C, S, DIT, LINE_FAST, 5>(buf, nlines, ls, es, d.n, d.L[s], tws); break;
       case 4: fft_stage<C, S, DIT, LINE_FAST, 4>(buf, nlines, ls, es, d.n, d.L[s], tws); break;
       case 3: fft_stage<C, S, DIT, LINE_FAST, 3>(buf, nlines, ls, es, d.n, d.L[s], tws); break;
@@ -145,31 +205,6 @@ __device__ void fft_lines_generic(C* buf, int nlines, int ls, int es, const FftD
 // The radix plan is the one the host builds (greedy 8, 4, 5, 3, 2), so the stage
 // twiddle offsets in FftDim apply unchanged.  All index arithmetic is by
 // compile-time constants; one barrier per stage.
-struct CPlan {
-  int nst;
-  int radix[kMaxStages];
-  int L[kMaxStages];
-};
-constexpr CPlan make_cplan(int n) {
-  CPlan p{};
-  p.nst = 0;
-  int m = n;
-  const int order[5] = {8, 4, 5, 3, 2};
-  for (int i = 0; i < 5; ++i) {
-    const int r = order[i];
-    while (m > 1 && m % r == 0) {
-      p.radix[p.nst++] = r;
-      m /= r;
-    }
-  }
-  int L = n;
-  for (int s = 0; s < p.nst; ++s) {
-    p.L[s] = L;
-    L /= p.radix[s];
-  }
-  return p;
-}
-
 template <typename C, int S, bool DIT, bool LINE_FAST, int LF, int N, int R, int L>
 __device__ __forceinline__ void stage_c(C* buf, int nlines, int ls, int es, const C* __restrict__ tws) {
   constexpr int Q = L / R, NBF = N / R;
@@ -256,11 +291,260 @@ __device__ void fft_lines(C* buf, int nlines, int ls, int es, const FftDim& d, c
 
 __device__ __forceinline__ int pmod(int a, int n) { int r = a % n; return r < 0 ? r + n : r; }
 
+// ---- line-group engine: each line is transformed by a group of TL threads of one warp
+// (TL a power of two dividing the butterfly count of every stage), butterflies of a
+// stage spread over the group, stages separated by __syncwarp only.  Same radix plan,
+// twiddle table and digit-reversed ordering as the block-wide stages above.
+constexpr int cgcd(int a, int b) { return b ? cgcd(b, a % b) : a; }
+template <int N> struct LineCfg {
+  static constexpr CPlan P = make_cplan(N);
+  static constexpr int g01 = P.nst >= 2 ? cgcd(N / P.radix[0], N / P.radix[1]) : N / P.radix[0];
+  static constexpr int g = P.nst >= 3 ? cgcd(g01, N / P.radix[2]) : g01;
+  static constexpr int TL = (g % 8 == 0) ? 8 : (g % 4 == 0) ? 4 : (g % 2 == 0) ? 2 : 1;
+  static constexpr int NP = N + ((TL - N) % 16 + 16) % 16;  // padded line pitch (bank spread)
+  static constexpr int LPC = 64;                           // lines per CTA
+  static constexpr int THREADS = LPC * TL;
+};
+
+// twt: this dimension's twiddle table (stage s at twt + tw_off[s] - tw_base), normally a
+// shared-memory copy.  mask: lanes of the warp taking part (all lanes of active groups).
+template <typename C, int S, int N, int TL, int S0>
+__device__ __forceinline__ void line_stages(C* line, int t, const C* twt, const FftDim& d, unsigned mask) {
+  constexpr CPlan P = make_cplan(N);
+  if constexpr (S0 < P.nst) {
+    constexpr bool DIT = (S < 0);
+    constexpr int s = DIT ? P.nst - 1 - S0 : S0;
+    constexpr int R = P.radix[s], L = P.L[s], Q = L / R, NB = N / R;
+    static_assert(NB % TL == 0, "butterflies must split evenly over the line group");
+    const C* tws = twt + (d.tw_off[s] - d.tw_base);
+#pragma unroll
+    for (int i = 0; i < NB / TL; ++i) {
+      const int bf = t + TL * i;
+      const int blk = bf / Q, j = bf - blk * Q;
+      C* base = line + blk * L + j;
+      C x[R];
+#pragma unroll
+      for (int m = 0; m < R; ++m) x[m] = base[m * Q];
+      if (DIT) {
+        if (Q > 1 && j) {
+#pragma unroll
+          for (int m = 1; m < R; ++m) {
+            C w = tws[j * (R - 1) + m - 1];
+            if (S > 0) w = cconj(w);
+            x[m] = cmul(x[m], w);
+          }
+        }
+        dftR<C, S, R>(x);
+      } else {
+        dftR<C, S, R>(x);
+        if (Q > 1 && j) {
+#pragma unroll
+          for (int m = 1; m < R; ++m) {
+            C w = tws[j * (R - 1) + m - 1];
+            if (S > 0) w = cconj(w);
+            x[m] = cmul(x[m], w);
+          }
+        }
+      }
+#pragma unroll
+      for (int m = 0; m < R; ++m) base[m * Q] = x[m];
+    }
+    __syncwarp(mask);
+    line_stages<C, S, N, TL, S0 + 1>(line, t, twt, d, mask);
+  }
+}
+
+// copy one dimension's twiddles to shared memory (caller synchronises)
+template <typename C>
+__device__ __forceinline__ void load_tw(C* dst, const C* __restrict__ tw, const FftDim& d) {
+  for (int i = threadIdx.x; i < d.tw_count; i += blockDim.x) dst[i] = tw[d.tw_base + i];
+}
+
+// Transform `nlines` lines (line k at buf + k * pitch, unit element stride) with groups of
+// TL threads; all threads of the block call this (it contains no block barrier).
+template <typename C, int S, int N, int TL>
+__device__ __forceinline__ void lines_lg(C* buf, int pitch, int nlines, const C* twt, const FftDim& d) {
+  const int g = threadIdx.x / TL, t = threadIdx.x % TL, ng = blockDim.x / TL;
+  for (int k0 = 0; k0 < nlines; k0 += ng) {
+    const int k = k0 + g;
+    const unsigned mask = __ballot_sync(0xffffffffu, k < nlines);
+    if (k < nlines) line_stages<C, S, N, TL, 0>(buf + k * pitch, t, twt, d, mask);
+  }
+}
+
+// x-line pass with the line-group engine: inverse x (DIF), times V / n1n2n3 at the
+// digit-reversed positions, forward x (DIT); only the sphere planes are read and written.
+template <typename T, int N1>
+__global__ void __launch_bounds__(LineCfg<N1>::THREADS) k_xline_lg(cplx<T>* __restrict__ hb, int64_t hb_bs,
+                                                                   const T* __restrict__ vperm, SphereDev sp,
+                                                                   FftPlan plan, const cplx<T>* __restrict__ tw) {
+  using C = cplx<T>;
+  using LC = LineCfg<N1>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* X = reinterpret_cast<C*>(smem_raw);  // [LPC][NP]
+  C* twt = X + LC::LPC * LC::NP;
+  const int nyz = plan.n[1] * plan.n[2];
+  const int yz0 = blockIdx.x * LC::LPC, b = blockIdx.y;
+  const int ln = min(LC::LPC, nyz - yz0);
+  for (int i = threadIdx.x; i < LC::LPC * LC::NP; i += blockDim.x) X[i] = czero<C>();
+  load_tw(twt, tw, plan.d[0]);
+  __syncthreads();
+  C* base = hb + (int64_t)b * hb_bs;
+  for (int i = threadIdx.x; i < sp.nplane * ln; i += blockDim.x) {
+    const int p = i / ln, l = i - p * ln;
+    X[l * LC::NP + pmod(sp.plane_h[p], N1)] = base[(int64_t)p * nyz + yz0 + l];
+  }
+  __syncthreads();
+  const int l = threadIdx.x / LC::TL, t = threadIdx.x % LC::TL;
+  C* line = X + l * LC::NP;
+  line_stages<C, +1, N1, LC::TL, 0>(line, t, twt, plan.d[0], 0xffffffffu);
+  if (l < ln) {
+#pragma unroll 4
+    for (int m = t; m < N1; m += LC::TL) line[m] = cscale(line[m], vperm[(int64_t)m * nyz + yz0 + l]);
+  }
+  __syncwarp();
+  line_stages<C, -1, N1, LC::TL, 0>(line, t, twt, plan.d[0], 0xffffffffu);
+  __syncthreads();
+  for (int i = threadIdx.x; i < sp.nplane * ln; i += blockDim.x) {
+    const int p = i / ln, l2 = i - p * ln;
+    base[(int64_t)p * nyz + yz0 + l2] = X[l2 * LC::NP + pmod(sp.plane_h[p], N1)];
+  }
+}
+
+// x-line pass fused in registers (2-stage plans N1 = R1 R2): the first inverse stage
+// reads the sphere planes straight from the half-box buffer, the last inverse stage,
+// the V multiply and the first forward stage share registers, and the last forward
+// stage writes only the sphere planes back.  Shared memory holds each line once
+// between stages (two exchanges per line instead of a full staging per stage).
+template <typename T, int N1>
+__global__ void __launch_bounds__(LineCfg<N1>::THREADS) k_xline_fused(cplx<T>* __restrict__ hb, int64_t hb_bs,
+                                                                      const T* __restrict__ vperm, SphereDev sp,
+                                                                      FftPlan plan,
+                                                                      const cplx<T>* __restrict__ tw) {
+  using C = cplx<T>;
+  using LC = LineCfg<N1>;
+  constexpr CPlan P = make_cplan(N1);
+  static_assert(P.nst == 2, "two-stage plan expected");
+  constexpr int R1 = P.radix[0], R2 = P.radix[1], Q1 = R2;  // stage 1: L = N1, stride R2
+  constexpr int TL = LC::TL, NB1 = N1 / R1, NB2 = N1 / R2;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* X = reinterpret_cast<C*>(smem_raw);  // [LPC][NP]
+  C* twt = X + LC::LPC * LC::NP;
+  int* pidx = reinterpret_cast<int*>(twt + plan.d[0].tw_count);  // x -> plane index or -1
+  const int nyz = plan.n[1] * plan.n[2];
+  const int yz0 = blockIdx.x * LC::LPC, b = blockIdx.y;
+  const int ln = min(LC::LPC, nyz - yz0);
+  load_tw(twt, tw, plan.d[0]);
+  for (int i = threadIdx.x; i < N1; i += blockDim.x) pidx[i] = -1;
+  __syncthreads();
+  for (int i = threadIdx.x; i < sp.nplane; i += blockDim.x) pidx[pmod(sp.plane_h[i], N1)] = i;
+  __syncthreads();
+  const C* tw1 = twt + (plan.d[0].tw_off[0] - plan.d[0].tw_base);
+  const int l = threadIdx.x / TL, t = threadIdx.x % TL;
+  const bool live = l < ln;
+  C* line = X + l * LC::NP;
+  C* hbb = hb + (int64_t)b * hb_bs + yz0 + l;
+  // stage 1 of the inverse transform (DIF radix R1, stride Q1): inputs from the planes
+#pragma unroll
+  for (int i = 0; i < NB1 / TL; ++i) {
+    const int j = t + TL * i;
+    C x[R1];
+#pragma unroll
+    for (int a = 0; a < R1; ++a) {
+      const int p = pidx[j + Q1 * a];
+      x[a] = (live && p >= 0) ? hbb[(int64_t)p * nyz] : czero<C>();
+    }
+    dftR<C, +1, R1>(x);
+    if (j) {
+#pragma unroll
+      for (int m = 1; m < R1; ++m) x[m] = cmul(x[m], cconj(tw1[j * (R1 - 1) + m - 1]));
+    }
+#pragma unroll
+    for (int m = 0; m < R1; ++m) line[j + Q1 * m] = x[m];
+  }
+  __syncwarp();
+  // stage 2 inverse (radix R2 on contiguous blocks), times V at the digit-reversed
+  // positions, stage 2 forward (DIT: first stage, no twiddles since its block length is R2)
+  const T* vb = vperm + yz0 + l;
+#pragma unroll
+  for (int i = 0; i < NB2 / TL; ++i) {
+    const int blk = t + TL * i;
+    C x[R2];
+#pragma unroll
+    for (int m = 0; m < R2; ++m) x[m] = line[blk * R2 + m];
+    dftR<C, +1, R2>(x);
+#pragma unroll
+    for (int m = 0; m < R2; ++m) x[m] = cscale(x[m], live ? vb[(int64_t)(blk * R2 + m) * nyz] : (T)0);
+    dftR<C, -1, R2>(x);
+#pragma unroll
+    for (int m = 0; m < R2; ++m) line[blk * R2 + m] = x[m];
+  }
+  __syncwarp();
+  // stage 1 forward (DIT radix R1): twiddles, DFT, write the sphere planes
+#pragma unroll
+  for (int i = 0; i < NB1 / TL; ++i) {
+    const int j = t + TL * i;
+    C x[R1];
+#pragma unroll
+    for (int m = 0; m < R1; ++m) x[m] = line[j + Q1 * m];
+    if (j) {
+#pragma unroll
+      for (int m = 1; m < R1; ++m) x[m] = cmul(x[m], tw1[j * (R1 - 1) + m - 1]);
+    }
+    dftR<C, -1, R1>(x);
+#pragma unroll
+    for (int a = 0; a < R1; ++a) {
+      const int p = pidx[j + Q1 * a];
+      if (live && p >= 0) hbb[(int64_t)p * nyz] = x[a];
+    }
+  }
+}
+
+template <typename T, int N1>
+static cudaError_t launch_xline_fused(cplx<T>* hb, int64_t hb_bs, const T* vperm, const SphereDev& sp,
+                                      const FftPlan& plan, const cplx<T>* tw, int nb, cudaStream_t st) {
+  using LC = LineCfg<N1>;
+  const size_t sm = sizeof(cplx<T>) * ((size_t)LC::LPC * LC::NP + plan.d[0].tw_count) + sizeof(int) * N1;
+  cudaError_t e = cudaFuncSetAttribute(k_xline_fused<T, N1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e) return e;
+  const int nyz = plan.n[1] * plan.n[2];
+  k_xline_fused<T, N1><<<dim3((nyz + LC::LPC - 1) / LC::LPC, nb), LC::THREADS, sm, st>>>(hb, hb_bs, vperm, sp, plan, tw); count_launch();
+  return cudaGetLastError();
+}
+
+template <typename T, int N1>
+static cudaError_t launch_xline_lg(cplx<T>* hb, int64_t hb_bs, const T* vperm, const SphereDev& sp,
+                                   const FftPlan& plan, const cplx<T>* tw, int nb, cudaStream_t st) {
+  using LC = LineCfg<N1>;
+  const size_t sm = sizeof(cplx<T>) * ((size_t)LC::LPC * LC::NP + plan.d[0].tw_count);
+  cudaError_t e = cudaFuncSetAttribute(k_xline_lg<T, N1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e) return e;
+  const int nyz = plan.n[1] * plan.n[2];
+  k_xline_lg<T, N1><<<dim3((nyz + LC::LPC - 1) / LC::LPC, nb), LC::THREADS, sm, st>>>(hb, hb_bs, vperm, sp, plan, tw); count_launch();
+  return cudaGetLastError();
+}
+
+// returns cudaErrorNotSupported when n1 has no line-group instantiation
+template <typename T>
+static cudaError_t xline_lg(cplx<T>* hb, int64_t hb_bs, const T* vperm, const SphereDev& sp, const FftPlan& plan,
+                            const cplx<T>* tw, int nb, cudaStream_t st) {
+  switch (plan.n[0]) {
+    case 24: return launch_xline_fused<T, 24>(hb, hb_bs, vperm, sp, plan, tw, nb, st);
+    case 64: return launch_xline_fused<T, 64>(hb, hb_bs, vperm, sp, plan, tw, nb, st);
+    case 72: return launch_xline_fused<T, 72>(hb, hb_bs, vperm, sp, plan, tw, nb, st);
+    case 90: return launch_xline_fused<T, 90>(hb, hb_bs, vperm, sp, plan, tw, nb, st);
+    case 96: return launch_xline_fused<T, 96>(hb, hb_bs, vperm, sp, plan, tw, nb, st);
+    case 120: return launch_xline_fused<T, 120>(hb, hb_bs, vperm, sp, plan, tw, nb, st);
+    default: return cudaErrorNotSupported;
+  }
+}
+
+
 constexpr int kThreads = 256;
 
 // ---- pass 1: sphere plane -> inverse (z, y) -> half-box plane ---------------------
 template <typename T>
-__global__ void __launch_bounds__(kThreads) k_plane_inv(const cplx<T>* __restrict__ psi, int64_t ldpsi,
+__global__ void __launch_bounds__(kThreads, 2) k_plane_inv(const cplx<T>* __restrict__ psi, int64_t ldpsi,
                                                         cplx<T>* __restrict__ hb, int64_t hb_bs,
                                                         SphereDev sp, FftPlan plan,
                                                         const cplx<T>* __restrict__ tw, int cz) {
@@ -302,7 +586,7 @@ __global__ void __launch_bounds__(kThreads) k_plane_inv(const cplx<T>* __restric
 
 // ---- pass 2: x-lines: inverse x, times V, forward x ---------------------------------
 template <typename T>
-__global__ void __launch_bounds__(kThreads) k_xline(cplx<T>* __restrict__ hb, int64_t hb_bs,
+__global__ void __launch_bounds__(kThreads, 2) k_xline(cplx<T>* __restrict__ hb, int64_t hb_bs,
                                                     const T* __restrict__ vperm, SphereDev sp,
                                                     FftPlan plan, const cplx<T>* __restrict__ tw, int lyz) {
   using C = cplx<T>;
@@ -334,7 +618,7 @@ __global__ void __launch_bounds__(kThreads) k_xline(cplx<T>* __restrict__ hb, in
 
 // ---- pass 3: half-box plane -> forward (y, z) -> sphere, + kinetic ------------------
 template <typename T>
-__global__ void __launch_bounds__(kThreads) k_plane_fwd(const cplx<T>* __restrict__ hb, int64_t hb_bs,
+__global__ void __launch_bounds__(kThreads, 2) k_plane_fwd(const cplx<T>* __restrict__ hb, int64_t hb_bs,
                                                         SphereDev sp, FftPlan plan,
                                                         const cplx<T>* __restrict__ tw, int cz,
                                                         const T* __restrict__ kin,
@@ -380,7 +664,7 @@ __global__ void __launch_bounds__(kThreads) k_plane_fwd(const cplx<T>* __restric
 
 // ---- density: inverse x-lines for a and b, accumulate w Re(conj(a) b) ---------------
 template <typename T>
-__global__ void __launch_bounds__(kThreads) k_xline_density(const cplx<T>* __restrict__ hba,
+__global__ void __launch_bounds__(kThreads, 2) k_xline_density(const cplx<T>* __restrict__ hba,
                                                             const cplx<T>* __restrict__ hbb, int64_t hb_bs,
                                                             int nb, const T* __restrict__ w, SphereDev sp,
                                                             FftPlan plan, const cplx<T>* __restrict__ tw,
@@ -435,7 +719,169 @@ __global__ void __launch_bounds__(kThreads) k_xline_density(const cplx<T>* __res
   }
 }
 
+// ---- plane passes with the line-group engine ------------------------------------
+template <typename T> struct PlaneCh { static constexpr int v = (sizeof(T) == 4) ? 64 : 32; };
+
+template <typename T, int N2, int N3>
+__global__ void __launch_bounds__(256) k_plane_inv_lg(const cplx<T>* __restrict__ psi, int64_t ldpsi,
+                                                      cplx<T>* __restrict__ hb, int64_t hb_bs, SphereDev sp,
+                                                      FftPlan plan, const cplx<T>* __restrict__ tw) {
+  using C = cplx<T>;
+  constexpr int NP2 = LineCfg<N2>::NP, NP3 = LineCfg<N3>::NP, CH = PlaneCh<T>::v;
+  constexpr int TL2 = LineCfg<N2>::TL, TL3 = LineCfg<N3>::TL;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* R = reinterpret_cast<C*>(smem_raw);  // [max_rows][NP3]
+  C* W = R + sp.max_rows * NP3;           // [CH][NP2]
+  C* tw2 = W + CH * NP2;
+  C* tw3 = tw2 + plan.d[1].tw_count;
+  const int p = blockIdx.x, b = blockIdx.y;
+  const int r0 = sp.plane_row0[p], nr = sp.plane_row0[p + 1] - r0;
+  const C* src = psi + (int64_t)b * ldpsi;
+  for (int i = threadIdx.x; i < nr * NP3; i += blockDim.x) R[i] = czero<C>();
+  load_tw(tw2, tw, plan.d[1]);
+  load_tw(tw3, tw, plan.d[2]);
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int row = warp; row < nr; row += nw) {
+    const int g0 = sp.row_g0[r0 + row], cnt = sp.row_cnt[r0 + row], l0 = sp.row_l0[r0 + row];
+    for (int t = lane; t < cnt; t += 32) R[row * NP3 + pmod(l0 + t, N3)] = src[g0 + t];
+  }
+  __syncthreads();
+  lines_lg<C, +1, N3, TL3>(R, NP3, nr, tw3, plan.d[2]);
+  __syncthreads();
+  C* dst = hb + (int64_t)b * hb_bs + (int64_t)p * N2 * N3;
+  for (int zc0 = 0; zc0 < N3; zc0 += CH) {
+    const int czn = min(CH, N3 - zc0);
+    for (int i = threadIdx.x; i < czn * NP2; i += blockDim.x) W[i] = czero<C>();
+    __syncthreads();
+    for (int i = threadIdx.x; i < nr * czn; i += blockDim.x) {
+      const int row = i / czn, zc = i - row * czn;
+      W[zc * NP2 + pmod(sp.row_k[r0 + row], N2)] = R[row * NP3 + zc0 + zc];
+    }
+    __syncthreads();
+    lines_lg<C, +1, N2, TL2>(W, NP2, czn, tw2, plan.d[1]);
+    __syncthreads();
+    for (int i = threadIdx.x; i < N2 * czn; i += blockDim.x) {
+      const int y = i / czn, zc = i - y * czn;
+      dst[(int64_t)y * N3 + zc0 + zc] = W[zc * NP2 + y];
+    }
+    __syncthreads();
+  }
+}
+
+template <typename T, int N2, int N3>
+__global__ void __launch_bounds__(256) k_plane_fwd_lg(const cplx<T>* __restrict__ hb, int64_t hb_bs, SphereDev sp,
+                                                      FftPlan plan, const cplx<T>* __restrict__ tw,
+                                                      const T* __restrict__ kin, const cplx<T>* __restrict__ psi,
+                                                      int64_t ldpsi, cplx<T>* __restrict__ out, int64_t ldout) {
+  using C = cplx<T>;
+  constexpr int NP2 = LineCfg<N2>::NP, NP3 = LineCfg<N3>::NP, CH = PlaneCh<T>::v;
+  constexpr int TL2 = LineCfg<N2>::TL, TL3 = LineCfg<N3>::TL;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* R = reinterpret_cast<C*>(smem_raw);
+  C* W = R + sp.max_rows * NP3;
+  C* tw2 = W + CH * NP2;
+  C* tw3 = tw2 + plan.d[1].tw_count;
+  const int p = blockIdx.x, b = blockIdx.y;
+  const int r0 = sp.plane_row0[p], nr = sp.plane_row0[p + 1] - r0;
+  const C* srcp = hb + (int64_t)b * hb_bs + (int64_t)p * N2 * N3;
+  load_tw(tw2, tw, plan.d[1]);
+  load_tw(tw3, tw, plan.d[2]);
+  for (int zc0 = 0; zc0 < N3; zc0 += CH) {
+    const int czn = min(CH, N3 - zc0);
+    for (int i = threadIdx.x; i < N2 * czn; i += blockDim.x) {
+      const int y = i / czn, zc = i - y * czn;
+      W[zc * NP2 + y] = srcp[(int64_t)y * N3 + zc0 + zc];
+    }
+    __syncthreads();
+    lines_lg<C, -1, N2, TL2>(W, NP2, czn, tw2, plan.d[1]);
+    __syncthreads();
+    for (int i = threadIdx.x; i < nr * czn; i += blockDim.x) {
+      const int row = i / czn, zc = i - row * czn;
+      R[row * NP3 + zc0 + zc] = W[zc * NP2 + pmod(sp.row_k[r0 + row], N2)];
+    }
+    __syncthreads();
+  }
+  lines_lg<C, -1, N3, TL3>(R, NP3, nr, tw3, plan.d[2]);
+  __syncthreads();
+  const C* y = psi + (int64_t)b * ldpsi;
+  C* o = out + (int64_t)b * ldout;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int row = warp; row < nr; row += nw) {
+    const int g0 = sp.row_g0[r0 + row], cnt = sp.row_cnt[r0 + row], l0 = sp.row_l0[r0 + row];
+    for (int t = lane; t < cnt; t += 32) {
+      const int g = g0 + t;
+      const C v = R[row * NP3 + pmod(l0 + t, N3)];
+      const C yy = y[g];
+      const T k = kin[g];
+      o[g] = mk<C>(k * yy.x + v.x, k * yy.y + v.y);
+    }
+  }
+}
+
+template <typename T, int N2, int N3>
+static size_t plane_lg_smem(const SphereDev& sp, const FftPlan& plan) {
+  return sizeof(cplx<T>) * ((size_t)sp.max_rows * LineCfg<N3>::NP + (size_t)PlaneCh<T>::v * LineCfg<N2>::NP +
+                            plan.d[1].tw_count + plan.d[2].tw_count);
+}
+
+template <typename T, int N2, int N3>
+static cudaError_t plane_lg_pair(int which, const cplx<T>* psi, int64_t ldpsi, cplx<T>* hb, int64_t hb_bs,
+                                 const SphereDev& sp, const FftPlan& plan, const cplx<T>* tw, const T* kin,
+                                 cplx<T>* out, int64_t ldout, int nb, cudaStream_t st) {
+  const size_t sm = plane_lg_smem<T, N2, N3>(sp, plan);
+  cudaError_t e;
+  if (which == 0) {
+    if ((e = cudaFuncSetAttribute(k_plane_inv_lg<T, N2, N3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm)))
+      return e;
+    k_plane_inv_lg<T, N2, N3><<<dim3(sp.nplane, nb), 256, sm, st>>>(psi, ldpsi, hb, hb_bs, sp, plan, tw); count_launch();
+  } else {
+    if ((e = cudaFuncSetAttribute(k_plane_fwd_lg<T, N2, N3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm)))
+      return e;
+    k_plane_fwd_lg<T, N2, N3><<<dim3(sp.nplane, nb), 256, sm, st>>>(hb, hb_bs, sp, plan, tw, kin, psi, ldpsi, out,
+                                                                    ldout); count_launch();
+  }
+  return cudaGetLastError();
+}
+
+// which = 0: pass 1, 1: pass 3.  cudaErrorNotSupported when (n2, n3) has no instantiation
+// or the shared-memory footprint does not fit.
+template <typename T>
+static cudaError_t plane_lg(int which, const cplx<T>* psi, int64_t ldpsi, cplx<T>* hb, int64_t hb_bs,
+                            const SphereDev& sp, const FftPlan& plan, const cplx<T>* tw, const T* kin, cplx<T>* out,
+                            int64_t ldout, int nb, cudaStream_t st) {
+  const int n2 = plan.n[1], n3 = plan.n[2];
+#define PW_PLANE_CASE(A, B)                                                                              \
+  if (n2 == A && n3 == B) {                                                                              \
+    if (plane_lg_smem<T, A, B>(sp, plan) > 227 * 1024) return cudaErrorNotSupported;                     \
+    return plane_lg_pair<T, A, B>(which, psi, ldpsi, hb, hb_bs, sp, plan, tw, kin, out, ldout, nb, st); \
+  }
+  PW_PLANE_CASE(24, 24)
+  PW_PLANE_CASE(64, 64)
+  PW_PLANE_CASE(72, 90)
+  PW_PLANE_CASE(96, 96)
+  PW_PLANE_CASE(120, 120)
+#undef PW_PLANE_CASE
+  return cudaErrorNotSupported;
+}
+
 // ---- launchers ------------------------------------------------------------------
+cudaError_t fft_set_constants() {
+  const int Rs[6] = {6, 9, 10, 12, 15, 16};
+  double2 t64[68];
+  float2 t32[68];
+  int o = 0;
+  for (int r : Rs)
+    for (int m = 0; m < r; ++m, ++o) {
+      const double ang = -2.0 * 3.14159265358979323846264338327950288 * (double)m / (double)r;
+      t64[o] = make_double2(cos(ang), sin(ang));
+      t32[o] = make_float2((float)t64[o].x, (float)t64[o].y);
+    }
+  cudaError_t e = cudaMemcpyToSymbol(c_wtab64, t64, sizeof(t64));
+  if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_wtab32, t32, sizeof(t32));
+  return e;
+}
+
 static int pick_cz(int n3) { return n3 < 16 ? n3 : 16; }
 
 template <typename T>
@@ -462,14 +908,32 @@ cudaError_t launch_local_apply(const FftPlan& plan, const cplx<T>* tw, const Sph
   for (int b0 = 0; b0 < nband; b0 += band_batch) {
     const int nb = min(band_batch, nband - b0);
     prof_begin(prof, PW_PROF_PLANE_INV);
-    k_plane_inv<T><<<dim3(sp.nplane, nb), kThreads, sm1, st>>>(psi + b0 * ldpsi, ldpsi, hb, hb_bs, sp, plan, tw, cz); count_launch();
+    e = plane_lg<T>(0, psi + b0 * ldpsi, ldpsi, hb, hb_bs, sp, plan, tw, kin, nullptr, 0, nb, st);
+    if (e == cudaErrorNotSupported) {
+      (void)cudaGetLastError();
+      k_plane_inv<T><<<dim3(sp.nplane, nb), kThreads, sm1, st>>>(psi + b0 * ldpsi, ldpsi, hb, hb_bs, sp, plan, tw, cz); count_launch();
+    } else if (e != cudaSuccess) {
+      return e;
+    }
     prof_end(prof, PW_PROF_PLANE_INV);
     prof_begin(prof, PW_PROF_XLINE);
-    k_xline<T><<<dim3((nyz + lyz - 1) / lyz, nb), kThreads, sm2, st>>>(hb, hb_bs, vperm, sp, plan, tw, lyz); count_launch();
+    e = xline_lg<T>(hb, hb_bs, vperm, sp, plan, tw, nb, st);
+    if (e == cudaErrorNotSupported) {
+      (void)cudaGetLastError();
+      k_xline<T><<<dim3((nyz + lyz - 1) / lyz, nb), kThreads, sm2, st>>>(hb, hb_bs, vperm, sp, plan, tw, lyz); count_launch();
+    } else if (e != cudaSuccess) {
+      return e;
+    }
     prof_end(prof, PW_PROF_XLINE);
     prof_begin(prof, PW_PROF_PLANE_FWD);
-    k_plane_fwd<T><<<dim3(sp.nplane, nb), kThreads, sm1, st>>>(hb, hb_bs, sp, plan, tw, cz, kin,
-                                                                psi + b0 * ldpsi, ldpsi, out + b0 * ldout, ldout); count_launch();
+    e = plane_lg<T>(1, psi + b0 * ldpsi, ldpsi, hb, hb_bs, sp, plan, tw, kin, out + b0 * ldout, ldout, nb, st);
+    if (e == cudaErrorNotSupported) {
+      (void)cudaGetLastError();
+      k_plane_fwd<T><<<dim3(sp.nplane, nb), kThreads, sm1, st>>>(hb, hb_bs, sp, plan, tw, cz, kin,
+                                                                  psi + b0 * ldpsi, ldpsi, out + b0 * ldout, ldout); count_launch();
+    } else if (e != cudaSuccess) {
+      return e;
+    }
     prof_end(prof, PW_PROF_PLANE_FWD);
   }
   return cudaGetLastError();

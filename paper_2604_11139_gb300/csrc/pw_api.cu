@@ -127,23 +127,13 @@ constexpr double kPi = 3.14159265358979323846264338327950288;
 // host-side planning
 // ---------------------------------------------------------------------------
 bool factorize(int n, FftDim& d) {
+  const CPlan p = make_cplan(n);
+  if (n < 1 || p.nst < 0 || (n > 1 && p.nst == 0)) return false;
   d.n = n;
-  d.nst = 0;
-  int m = n;
-  const int order[5] = {8, 4, 5, 3, 2};
-  for (int r : order) {
-    while (m % r == 0 && m > 1) {
-      if (r == 8 && m % 8 != 0) break;
-      if (d.nst >= kMaxStages) return false;
-      d.radix[d.nst++] = r;
-      m /= r;
-    }
-  }
-  if (m != 1 || n < 1) return false;
-  int L = n;
-  for (int s = 0; s < d.nst; ++s) {
-    d.L[s] = L;
-    L /= d.radix[s];
+  d.nst = p.nst;
+  for (int s = 0; s < p.nst; ++s) {
+    d.radix[s] = p.radix[s];
+    d.L[s] = p.L[s];
   }
   return true;
 }
@@ -801,6 +791,7 @@ int create_impl(const pw_problem_desc* d, void* stream, pw_ctx** out) {
   std::vector<double2> tw;
   for (int dd = 0; dd < 3; ++dd) {
     FftDim& f = ctx->plan.d[dd];
+    f.tw_base = (int)tw.size();
     for (int s = 0; s < f.nst; ++s) {
       f.tw_off[s] = (int)tw.size();
       const int L = f.L[s], r = f.radix[s], q = L / r;
@@ -811,6 +802,7 @@ int create_impl(const pw_problem_desc* d, void* stream, pw_ctx** out) {
           tw.push_back(make_double2(cos(ang), sin(ang)));
         }
     }
+    f.tw_count = (int)tw.size() - f.tw_base;
   }
   std::vector<float2> tw32(tw.size());
   for (size_t i = 0; i < tw.size(); ++i) tw32[i] = make_float2((float)tw[i].x, (float)tw[i].y);
@@ -821,6 +813,7 @@ int create_impl(const pw_problem_desc* d, void* stream, pw_ctx** out) {
     PW_TRY(upload(ctx, &ctx->rho_perm[dd], r.data(), r.size()));
   }
   const cudaStream_t st = ctx->stream;
+  CU_TRY(fft_set_constants(), "FFT constants");
   // permuted potential, scaled by 1 / n1n2n3 (the forward DFT normalisation)
   const size_t ntot = (size_t)d->box[0] * d->box[1] * d->box[2];
   double* vraw;

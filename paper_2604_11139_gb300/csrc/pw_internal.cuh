@@ -67,11 +67,73 @@ struct FftDim {
   int radix[kMaxStages];
   int L[kMaxStages];      // block length at each stage (n, n/r1, ...)
   int tw_off[kMaxStages]; // offset of the stage's twiddles in the table
+  int tw_base, tw_count;  // this dimension's contiguous range of the table
 };
 struct FftPlan {
   int n[3];
   FftDim d[3];
 };
+
+// Radix plan of one FFT length, shared by host and device code.  Stages use the
+// in-register radices {16, 15, 12, 10, 9, 8, 6, 5, 4, 3, 2}; the plan has the fewest
+// stages, then the smallest largest radix, then the largest leading radices.
+struct CPlan {
+  int nst;
+  int radix[kMaxStages];
+  int L[kMaxStages];
+};
+__host__ __device__ constexpr int radix_at(int i) {
+  return i == 0 ? 16 : i == 1 ? 15 : i == 2 ? 12 : i == 3 ? 10 : i == 4 ? 9 : i == 5 ? 8 : i == 6 ? 6 : i == 7 ? 5
+       : i == 8 ? 4 : i == 9 ? 3 : 2;
+}
+__host__ __device__ constexpr bool is_radix(int f) {
+  for (int i = 0; i < 11; ++i)
+    if (radix_at(i) == f) return true;
+  return false;
+}
+__host__ __device__ constexpr CPlan make_cplan(int n) {
+  CPlan p{};
+  p.nst = 0;
+  int f[kMaxStages] = {0, 0, 0, 0, 0, 0, 0, 0};
+  int nf = 0;
+  if (n > 1 && is_radix(n)) {
+    f[0] = n;
+    nf = 1;
+  }
+  if (nf == 0 && n > 1) {
+    int bmax = 1 << 30;
+    for (int i = 0; i < 11; ++i) {
+      const int a = radix_at(i);
+      if (n % a || !is_radix(n / a)) continue;
+      const int b = n / a, mx = a > b ? a : b;
+      if (mx < bmax || (mx == bmax && a > f[0])) { bmax = mx; f[0] = a; f[1] = b; nf = 2; }
+    }
+  }
+  if (nf == 0 && n > 1) {
+    int bmax = 1 << 30;
+    for (int i = 0; i < 11; ++i)
+      for (int j = 0; j < 11; ++j) {
+        const int a = radix_at(i), b = radix_at(j);
+        if (n % (a * b) || !is_radix(n / (a * b))) continue;
+        const int c = n / (a * b);
+        int mx = a > b ? a : b;
+        mx = mx > c ? mx : c;
+        if (mx < bmax || (mx == bmax && (a > f[0] || (a == f[0] && b > f[1])))) {
+          bmax = mx; f[0] = a; f[1] = b; f[2] = c; nf = 3;
+        }
+      }
+  }
+  if (nf == 0 && n > 1) {  // longer lengths: greedy over the radix set
+    int m = n;
+    for (int i = 0; i < 11 && m > 1; ++i)
+      while (m > 1 && m % radix_at(i) == 0 && nf < kMaxStages) { f[nf++] = radix_at(i); m /= radix_at(i); }
+    if (m != 1) nf = -1;
+  }
+  p.nst = nf;
+  int L = n;
+  for (int s = 0; s < nf; ++s) { p.radix[s] = f[s]; p.L[s] = L; L /= f[s]; }
+  return p;
+}
 
 // plane-wave sphere decomposition: planes (fixed h) -> rows (fixed h,k) -> runs of l
 struct SphereDev {
@@ -110,6 +172,9 @@ cudaError_t launch_local_apply(const FftPlan& plan, const cplx<T>* tw, const Sph
                                const T* vperm, const T* kin, const cplx<T>* psi, int64_t ldpsi,
                                int nband, cplx<T>* out, int64_t ldout, cplx<T>* hb, int band_batch,
                                cudaStream_t st, ::pw_ctx* prof);
+
+// fills the constant twiddles of the composite in-register radices on the current device
+cudaError_t fft_set_constants();
 
 template <typename T>
 cudaError_t launch_density(const FftPlan& plan, const cplx<T>* tw, const SphereDev& sp,
