@@ -819,6 +819,260 @@ __global__ void __launch_bounds__(256) k_plane_fwd_lg(const cplx<T>* __restrict_
   }
 }
 
+// ---- plane passes fused in registers (2-stage plans for n2 and n3) -----------------
+// Pass 1: z-lines read their run of sphere coefficients straight into the first stage,
+// y-lines read the transformed rows straight from shared memory (zeros elsewhere) and the
+// last y stage writes the half-box plane.  Pass 3 mirrors it: the first y stage reads
+// the half-box plane, the last y stage fills only the rows holding coefficients, and the
+// last z stage gathers the sphere coefficients with the kinetic term.
+constexpr int kYGroups = 64;  // y-lines in flight per CTA
+
+template <typename T, int N2, int N3> struct PlaneF {
+  static constexpr CPlan P2 = make_cplan(N2), P3 = make_cplan(N3);
+  static constexpr int TL2 = LineCfg<N2>::TL, TL3 = LineCfg<N3>::TL;
+  static constexpr int NP2 = LineCfg<N2>::NP, NP3 = LineCfg<N3>::NP;
+  static constexpr bool ok = (P2.nst == 2 && P3.nst == 2);
+};
+
+template <typename T, int N2, int N3>
+__global__ void __launch_bounds__(256) k_plane_inv_f(const cplx<T>* __restrict__ psi, int64_t ldpsi,
+                                                     cplx<T>* __restrict__ hb, int64_t hb_bs, SphereDev sp,
+                                                     FftPlan plan, const cplx<T>* __restrict__ tw) {
+  using C = cplx<T>;
+  using PF = PlaneF<T, N2, N3>;
+  constexpr int TL2 = PF::TL2, TL3 = PF::TL3, NP2 = PF::NP2, NP3 = PF::NP3;
+  constexpr int Z1 = PF::P3.radix[0], Z2 = PF::P3.radix[1];  // z stages: radix Z1 stride Z2, then blocks of Z2
+  constexpr int Y1 = PF::P2.radix[0], Y2 = PF::P2.radix[1];
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* R = reinterpret_cast<C*>(smem_raw);        // [max_rows][NP3]
+  C* Wl = R + sp.max_rows * NP3;                // [kYGroups][NP2]
+  C* tw2 = Wl + kYGroups * NP2;
+  C* tw3 = tw2 + plan.d[1].tw_count;
+  int* ymap = reinterpret_cast<int*>(tw3 + plan.d[2].tw_count);  // y -> row or -1
+  const int p = blockIdx.x, b = blockIdx.y;
+  const int r0 = sp.plane_row0[p], nr = sp.plane_row0[p + 1] - r0;
+  const C* src = psi + (int64_t)b * ldpsi;
+  load_tw(tw2, tw, plan.d[1]);
+  load_tw(tw3, tw, plan.d[2]);
+  for (int i = threadIdx.x; i < N2; i += blockDim.x) ymap[i] = -1;
+  __syncthreads();
+  for (int i = threadIdx.x; i < nr; i += blockDim.x) ymap[pmod(sp.row_k[r0 + i], N2)] = i;
+  const C* tz1 = tw3 + (plan.d[2].tw_off[0] - plan.d[2].tw_base);
+  const C* ty1 = tw2 + (plan.d[1].tw_off[0] - plan.d[1].tw_base);
+  // z-lines: one row per group of TL3 threads
+  {
+    const int g = threadIdx.x / TL3, t = threadIdx.x % TL3, ng = blockDim.x / TL3;
+    for (int r00 = 0; r00 < nr; r00 += ng) {
+      const int row = r00 + g;
+      const bool has = row < nr;
+      const unsigned mask = __ballot_sync(0xffffffffu, has);
+      if (has) {
+        const int g0 = sp.row_g0[r0 + row], cnt = sp.row_cnt[r0 + row], l0 = sp.row_l0[r0 + row];
+        C* line = R + row * NP3;
+#pragma unroll
+        for (int i = 0; i < (N3 / Z1) / TL3; ++i) {
+          const int j = t + TL3 * i;
+          C x[Z1];
+#pragma unroll
+          for (int a = 0; a < Z1; ++a) {
+            const int idx = pmod(j + Z2 * a - l0, N3);
+            x[a] = idx < cnt ? src[g0 + idx] : czero<C>();
+          }
+          dftR<C, +1, Z1>(x);
+          if (j) {
+#pragma unroll
+            for (int m = 1; m < Z1; ++m) x[m] = cmul(x[m], cconj(tz1[j * (Z1 - 1) + m - 1]));
+          }
+#pragma unroll
+          for (int m = 0; m < Z1; ++m) line[j + Z2 * m] = x[m];
+        }
+        __syncwarp(mask);
+#pragma unroll
+        for (int i = 0; i < (N3 / Z2) / TL3; ++i) {
+          const int blk = t + TL3 * i;
+          C x[Z2];
+#pragma unroll
+          for (int m = 0; m < Z2; ++m) x[m] = line[blk * Z2 + m];
+          dftR<C, +1, Z2>(x);
+#pragma unroll
+          for (int m = 0; m < Z2; ++m) line[blk * Z2 + m] = x[m];
+        }
+      }
+    }
+  }
+  __syncthreads();
+  // y-lines: one column per group of TL2 threads, kYGroups columns per wave
+  C* dst = hb + (int64_t)b * hb_bs + (int64_t)p * N2 * N3;
+  {
+    const int g = threadIdx.x / TL2, t = threadIdx.x % TL2;
+    const bool in_wave = g < kYGroups;
+    C* line = Wl + g * NP2;
+    for (int c0 = 0; c0 < N3; c0 += kYGroups) {
+      const int col = c0 + g;
+      const bool has = in_wave && col < N3;
+      const unsigned mask = __ballot_sync(0xffffffffu, has);
+      if (has) {
+#pragma unroll
+        for (int i = 0; i < (N2 / Y1) / TL2; ++i) {
+          const int j = t + TL2 * i;
+          C x[Y1];
+#pragma unroll
+          for (int a = 0; a < Y1; ++a) {
+            const int r = ymap[j + Y2 * a];
+            x[a] = r >= 0 ? R[r * NP3 + col] : czero<C>();
+          }
+          dftR<C, +1, Y1>(x);
+          if (j) {
+#pragma unroll
+            for (int m = 1; m < Y1; ++m) x[m] = cmul(x[m], cconj(ty1[j * (Y1 - 1) + m - 1]));
+          }
+#pragma unroll
+          for (int m = 0; m < Y1; ++m) line[j + Y2 * m] = x[m];
+        }
+        __syncwarp(mask);
+#pragma unroll
+        for (int i = 0; i < (N2 / Y2) / TL2; ++i) {
+          const int blk = t + TL2 * i;
+          C x[Y2];
+#pragma unroll
+          for (int m = 0; m < Y2; ++m) x[m] = line[blk * Y2 + m];
+          dftR<C, +1, Y2>(x);
+#pragma unroll
+          for (int m = 0; m < Y2; ++m) dst[(int64_t)(blk * Y2 + m) * N3 + col] = x[m];
+        }
+        __syncwarp(mask);
+      }
+    }
+  }
+}
+
+template <typename T, int N2, int N3>
+__global__ void __launch_bounds__(256) k_plane_fwd_f(const cplx<T>* __restrict__ hb, int64_t hb_bs, SphereDev sp,
+                                                     FftPlan plan, const cplx<T>* __restrict__ tw,
+                                                     const T* __restrict__ kin, const cplx<T>* __restrict__ psi,
+                                                     int64_t ldpsi, cplx<T>* __restrict__ out, int64_t ldout) {
+  using C = cplx<T>;
+  using PF = PlaneF<T, N2, N3>;
+  constexpr int TL2 = PF::TL2, TL3 = PF::TL3, NP2 = PF::NP2, NP3 = PF::NP3;
+  constexpr int Z1 = PF::P3.radix[0], Z2 = PF::P3.radix[1];
+  constexpr int Y1 = PF::P2.radix[0], Y2 = PF::P2.radix[1];
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* R = reinterpret_cast<C*>(smem_raw);
+  C* Wl = R + sp.max_rows * NP3;
+  C* tw2 = Wl + kYGroups * NP2;
+  C* tw3 = tw2 + plan.d[1].tw_count;
+  int* ymap = reinterpret_cast<int*>(tw3 + plan.d[2].tw_count);
+  const int p = blockIdx.x, b = blockIdx.y;
+  const int r0 = sp.plane_row0[p], nr = sp.plane_row0[p + 1] - r0;
+  const C* srcp = hb + (int64_t)b * hb_bs + (int64_t)p * N2 * N3;
+  load_tw(tw2, tw, plan.d[1]);
+  load_tw(tw3, tw, plan.d[2]);
+  for (int i = threadIdx.x; i < N2; i += blockDim.x) ymap[i] = -1;
+  __syncthreads();
+  for (int i = threadIdx.x; i < nr; i += blockDim.x) ymap[pmod(sp.row_k[r0 + i], N2)] = i;
+  __syncthreads();
+  const C* tz1 = tw3 + (plan.d[2].tw_off[0] - plan.d[2].tw_base);
+  const C* ty1 = tw2 + (plan.d[1].tw_off[0] - plan.d[1].tw_base);
+  // y-lines (forward DIT: blocks of Y2 first, read from the half-box plane)
+  {
+    const int g = threadIdx.x / TL2, t = threadIdx.x % TL2;
+    const bool in_wave = g < kYGroups;
+    C* line = Wl + g * NP2;
+    for (int c0 = 0; c0 < N3; c0 += kYGroups) {
+      const int col = c0 + g;
+      const bool has = in_wave && col < N3;
+      const unsigned mask = __ballot_sync(0xffffffffu, has);
+      if (has) {
+#pragma unroll
+        for (int i = 0; i < (N2 / Y2) / TL2; ++i) {
+          const int blk = t + TL2 * i;
+          C x[Y2];
+#pragma unroll
+          for (int m = 0; m < Y2; ++m) x[m] = srcp[(int64_t)(blk * Y2 + m) * N3 + col];
+          dftR<C, -1, Y2>(x);
+#pragma unroll
+          for (int m = 0; m < Y2; ++m) line[blk * Y2 + m] = x[m];
+        }
+        __syncwarp(mask);
+#pragma unroll
+        for (int i = 0; i < (N2 / Y1) / TL2; ++i) {
+          const int j = t + TL2 * i;
+          C x[Y1];
+#pragma unroll
+          for (int m = 0; m < Y1; ++m) x[m] = line[j + Y2 * m];
+          if (j) {
+#pragma unroll
+            for (int m = 1; m < Y1; ++m) x[m] = cmul(x[m], ty1[j * (Y1 - 1) + m - 1]);
+          }
+          dftR<C, -1, Y1>(x);
+#pragma unroll
+          for (int a = 0; a < Y1; ++a) {
+            const int r = ymap[j + Y2 * a];
+            if (r >= 0) R[r * NP3 + col] = x[a];
+          }
+        }
+        __syncwarp(mask);
+      }
+    }
+  }
+  __syncthreads();
+  // z-lines: blocks of Z2 in place, then the radix-Z1 stage straight to the sphere
+  const C* yv = psi + (int64_t)b * ldpsi;
+  C* o = out + (int64_t)b * ldout;
+  {
+    const int g = threadIdx.x / TL3, t = threadIdx.x % TL3, ng = blockDim.x / TL3;
+    for (int r00 = 0; r00 < nr; r00 += ng) {
+      const int row = r00 + g;
+      const bool has = row < nr;
+      const unsigned mask = __ballot_sync(0xffffffffu, has);
+      if (has) {
+        C* line = R + row * NP3;
+#pragma unroll
+        for (int i = 0; i < (N3 / Z2) / TL3; ++i) {
+          const int blk = t + TL3 * i;
+          C x[Z2];
+#pragma unroll
+          for (int m = 0; m < Z2; ++m) x[m] = line[blk * Z2 + m];
+          dftR<C, -1, Z2>(x);
+#pragma unroll
+          for (int m = 0; m < Z2; ++m) line[blk * Z2 + m] = x[m];
+        }
+        __syncwarp(mask);
+        const int g0 = sp.row_g0[r0 + row], cnt = sp.row_cnt[r0 + row], l0 = sp.row_l0[r0 + row];
+#pragma unroll
+        for (int i = 0; i < (N3 / Z1) / TL3; ++i) {
+          const int j = t + TL3 * i;
+          C x[Z1];
+#pragma unroll
+          for (int m = 0; m < Z1; ++m) x[m] = line[j + Z2 * m];
+          if (j) {
+#pragma unroll
+            for (int m = 1; m < Z1; ++m) x[m] = cmul(x[m], tz1[j * (Z1 - 1) + m - 1]);
+          }
+          dftR<C, -1, Z1>(x);
+#pragma unroll
+          for (int a = 0; a < Z1; ++a) {
+            const int idx = pmod(j + Z2 * a - l0, N3);
+            if (idx < cnt) {
+              const int gg = g0 + idx;
+              const C yy = yv[gg];
+              const T k = kin[gg];
+              o[gg] = mk<C>(k * yy.x + x[a].x, k * yy.y + x[a].y);
+            }
+          }
+        }
+      }
+    }
+  }
+}
+
+template <typename T, int N2, int N3>
+static size_t plane_f_smem(const SphereDev& sp, const FftPlan& plan) {
+  using PF = PlaneF<T, N2, N3>;
+  return sizeof(cplx<T>) * ((size_t)sp.max_rows * PF::NP3 + (size_t)kYGroups * PF::NP2 + plan.d[1].tw_count +
+                            plan.d[2].tw_count) + sizeof(int) * N2;
+}
+
 template <typename T, int N2, int N3>
 static size_t plane_lg_smem(const SphereDev& sp, const FftPlan& plan) {
   return sizeof(cplx<T>) * ((size_t)sp.max_rows * LineCfg<N3>::NP + (size_t)PlaneCh<T>::v * LineCfg<N2>::NP +
@@ -829,8 +1083,26 @@ template <typename T, int N2, int N3>
 static cudaError_t plane_lg_pair(int which, const cplx<T>* psi, int64_t ldpsi, cplx<T>* hb, int64_t hb_bs,
                                  const SphereDev& sp, const FftPlan& plan, const cplx<T>* tw, const T* kin,
                                  cplx<T>* out, int64_t ldout, int nb, cudaStream_t st) {
-  const size_t sm = plane_lg_smem<T, N2, N3>(sp, plan);
   cudaError_t e;
+  if constexpr (PlaneF<T, N2, N3>::ok) {
+    const size_t smf = plane_f_smem<T, N2, N3>(sp, plan);
+    if (smf <= 227 * 1024) {
+      if (which == 0) {
+        if ((e = cudaFuncSetAttribute(k_plane_inv_f<T, N2, N3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)smf)))
+          return e;
+        k_plane_inv_f<T, N2, N3><<<dim3(sp.nplane, nb), 256, smf, st>>>(psi, ldpsi, hb, hb_bs, sp, plan, tw); count_launch();
+      } else {
+        if ((e = cudaFuncSetAttribute(k_plane_fwd_f<T, N2, N3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)smf)))
+          return e;
+        k_plane_fwd_f<T, N2, N3><<<dim3(sp.nplane, nb), 256, smf, st>>>(hb, hb_bs, sp, plan, tw, kin, psi, ldpsi, out,
+                                                                       ldout); count_launch();
+      }
+      return cudaGetLastError();
+    }
+  }
+  const size_t sm = plane_lg_smem<T, N2, N3>(sp, plan);
   if (which == 0) {
     if ((e = cudaFuncSetAttribute(k_plane_inv_lg<T, N2, N3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm)))
       return e;
