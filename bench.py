@@ -215,6 +215,7 @@ def run_ours(args):
     Y0 = torch.from_numpy(psi0).cuda()                       # complex128, resident
     Y0_32 = Y0.to(torch.complex64)
     rqmin, a, b = ctx.spectrum_bounds(Y0, 10, v0)
+    tune_ms = ctx.autotune(M, pwlib.PW_MIXED)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
     Y32 = torch.empty_like(Y0_32)
     Y64 = torch.empty_like(Y0)
@@ -347,7 +348,7 @@ def run_ours(args):
               "scaling": "weak", "vs_baseline": None, "dtype": "c64", "data": "synthetic",
               "config": workload_config(prob, npw, nproj),
               "precision": "filter: complex64 FFTs + FP32 SIMT projector GEMMs; RR: FP64",
-              "filter_ms": 1e3 * t_filter / args.steps, "wall_s": wall,
+              "filter_ms": 1e3 * t_filter / args.steps, "wall_s": wall, "autotune_local_ms": tune_ms,
               "fp64": fp64, "eig_err_vs_fp64": eig_err,
               "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": bytes_psi,
                       "d2h_bytes_per_step": bytes_psi + 8 * M,

@@ -177,6 +177,12 @@ enum pw_prof_class {
   PW_PROF_RR = 6,         /* S-Ortho + Rayleigh-Ritz (whole step) */
   PW_PROF_NCLASS = 7
 };
+/* Autotuner: times the local-potential FFT passes on nband bands for several band
+ * batch sizes (the batch's half-box planes from 16 MB to 2 GB) and keeps the fastest
+ * for `precision` in the context.  Synchronises the stream; *best_ms (may be NULL)
+ * receives the best time of one apply. */
+PW_API int pw_autotune(pw_ctx* ctx, int nband, int precision, double* best_ms);
+
 PW_API int pw_profile_enable(pw_ctx* ctx, int on);
 PW_API int pw_profile_read(pw_ctx* ctx, double* ms, int64_t* launches);
 PW_API uint64_t pw_kernel_launches(void);

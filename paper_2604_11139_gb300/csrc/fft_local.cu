@@ -430,14 +430,13 @@ __global__ void __launch_bounds__(LineCfg<N1>::THREADS) k_xline_fused(cplx<T>* _
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* X = reinterpret_cast<C*>(smem_raw);  // [LPC][NP]
   C* twt = X + LC::LPC * LC::NP;
-  int* pidx = reinterpret_cast<int*>(twt + plan.d[0].tw_count);  // x -> plane index or -1
   const int nyz = plan.n[1] * plan.n[2];
   const int yz0 = blockIdx.x * LC::LPC, b = blockIdx.y;
   const int ln = min(LC::LPC, nyz - yz0);
+  // the sphere's x-planes are the contiguous Miller range h0 .. h0 + nplane - 1
+  const int h0 = sp.plane_h[0], np = sp.nplane;
+  auto pidx = [&](int x) { const int p = pmod(x - h0, N1); return p < np ? p : -1; };
   load_tw(twt, tw, plan.d[0]);
-  for (int i = threadIdx.x; i < N1; i += blockDim.x) pidx[i] = -1;
-  __syncthreads();
-  for (int i = threadIdx.x; i < sp.nplane; i += blockDim.x) pidx[pmod(sp.plane_h[i], N1)] = i;
   __syncthreads();
   const C* tw1 = twt + (plan.d[0].tw_off[0] - plan.d[0].tw_base);
   const int l = threadIdx.x / TL, t = threadIdx.x % TL;
@@ -451,7 +450,7 @@ __global__ void __launch_bounds__(LineCfg<N1>::THREADS) k_xline_fused(cplx<T>* _
     C x[R1];
 #pragma unroll
     for (int a = 0; a < R1; ++a) {
-      const int p = pidx[j + Q1 * a];
+      const int p = pidx(j + Q1 * a);
       x[a] = (live && p >= 0) ? hbb[(int64_t)p * nyz] : czero<C>();
     }
     dftR<C, +1, R1>(x);
@@ -494,7 +493,7 @@ __global__ void __launch_bounds__(LineCfg<N1>::THREADS) k_xline_fused(cplx<T>* _
     dftR<C, -1, R1>(x);
 #pragma unroll
     for (int a = 0; a < R1; ++a) {
-      const int p = pidx[j + Q1 * a];
+      const int p = pidx(j + Q1 * a);
       if (live && p >= 0) hbb[(int64_t)p * nyz] = x[a];
     }
   }
@@ -504,7 +503,7 @@ template <typename T, int N1>
 static cudaError_t launch_xline_fused(cplx<T>* hb, int64_t hb_bs, const T* vperm, const SphereDev& sp,
                                       const FftPlan& plan, const cplx<T>* tw, int nb, cudaStream_t st) {
   using LC = LineCfg<N1>;
-  const size_t sm = sizeof(cplx<T>) * ((size_t)LC::LPC * LC::NP + plan.d[0].tw_count) + sizeof(int) * N1;
+  const size_t sm = sizeof(cplx<T>) * ((size_t)LC::LPC * LC::NP + plan.d[0].tw_count);
   cudaError_t e = cudaFuncSetAttribute(k_xline_fused<T, N1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e) return e;
   const int nyz = plan.n[1] * plan.n[2];

@@ -239,7 +239,7 @@ Epi<T> epi(int mode, cplx<T>* out, int64_t ldo, T alpha = 1) {
 // HBM; complex128 (DFMA-bound) batches near 256 MB for fewer, larger launches.
 int band_batch(const pw_ctx* ctx, int nband, size_t elem = 16) {
   const size_t per = (size_t)ctx->sp.nplane * ctx->n[1] * ctx->n[2] * elem;
-  const size_t target = (elem == 8) ? ((size_t)48 << 20) : ((size_t)256 << 20);
+  const size_t target = ctx->fft_batch_bytes[elem == 8 ? 0 : 1];
   int bb = (int)std::max<size_t>(1, target / std::max<size_t>(per, 1));
   return std::max(1, std::min(bb, nband));
 }
@@ -768,6 +768,8 @@ int create_impl(const pw_problem_desc* d, void* stream, pw_ctx** out) {
   }
   pl_row0.push_back((int)rk.size());
   if (ctx->npw == 0) return set_error(PW_EINVAL, "empty plane-wave sphere");
+  for (size_t p = 0; p < pl_h.size(); ++p)
+    if (pl_h[p] != pl_h[0] + (int)p) return set_error(PW_EINVAL, "sphere x-planes are not a contiguous range");
   for (int c = 0; c < 3; ++c)
     if (mx[c] - mn[c] >= d->box[c]) return set_error(PW_EINVAL, "plane-wave sphere does not fit in the FFT box");
   ctx->sp.npw = ctx->npw;
@@ -1064,6 +1066,59 @@ PW_API int pw_density_grad(pw_ctx* ctx, const void* a, const void* b, int64_t ld
   }
   CU_TRY(setup_unperm(den, ctx->n, ctx->rho_perm, out, accumulate, st), "density unpermute");
   CU_TRY(cudaStreamSynchronize(st), "density sync");
+  return PW_OK;
+}
+
+PW_API int pw_autotune(pw_ctx* ctx, int nband, int precision, double* best_ms) {
+  PW_TRY(check_ctx(ctx));
+  if (nband <= 0) return set_error(PW_EINVAL, "nband must be positive");
+  if (precision != PW_FP64 && precision != PW_MIXED) return set_error(PW_EINVAL, "unknown precision");
+  const int slot = precision == PW_MIXED ? 0 : 1;
+  const size_t elem = precision == PW_MIXED ? 8 : 16;
+  const cudaStream_t st = ctx->stream;
+  const size_t per = (size_t)ctx->sp.nplane * ctx->n[1] * ctx->n[2] * elem;
+  // candidate batch footprints (bytes of half-box planes per launch)
+  const size_t cand[7] = {(size_t)16 << 20, (size_t)48 << 20, (size_t)128 << 20, (size_t)256 << 20,
+                          (size_t)512 << 20, (size_t)1024 << 20, (size_t)2048 << 20};
+  WS(xin, unsigned char, WS_Y1, elem * (size_t)ctx->npw * nband);
+  WS(xout, unsigned char, WS_Y2, elem * (size_t)ctx->npw * nband);
+  CU_TRY(cudaMemsetAsync(xin, 0, elem * (size_t)ctx->npw * nband, st), "autotune input");
+  size_t max_hb = 0;
+  for (size_t c : cand) max_hb = std::max(max_hb, std::min<size_t>(std::max<size_t>(c / std::max<size_t>(per, 1), 1), nband) * per);
+  WS(hb, unsigned char, WS_HB, max_hb);
+  cudaEvent_t e0, e1;
+  CU_TRY(cudaEventCreate(&e0), "event");
+  CU_TRY(cudaEventCreate(&e1), "event");
+  double best = 1e30;
+  size_t best_c = ctx->fft_batch_bytes[slot];
+  const int64_t hb_bs = (int64_t)ctx->sp.nplane * ctx->n[1] * ctx->n[2];
+  for (size_t c : cand) {
+    const int bb = (int)std::max<size_t>(1, std::min<size_t>(c / std::max<size_t>(per, 1), nband));
+    if (c != cand[0] && bb * per > c && bb == 1) continue;
+    float tot = 0.f;
+    for (int rep = 0; rep < 4; ++rep) {
+      cudaEventRecord(e0, st);
+      cudaError_t e;
+      if (precision == PW_MIXED)
+        e = launch_local_apply<float>(ctx->plan, ctx->tw32, ctx->sp, ctx->vperm32, ctx->kin32, (const float2*)xin,
+                                      ctx->npw, nband, (float2*)xout, ctx->npw, (float2*)hb, bb, st, nullptr);
+      else
+        e = launch_local_apply<double>(ctx->plan, ctx->tw64, ctx->sp, ctx->vperm64, ctx->kin64, (const double2*)xin,
+                                       ctx->npw, nband, (double2*)xout, ctx->npw, (double2*)hb, bb, st, nullptr);
+      cudaEventRecord(e1, st);
+      if (e != cudaSuccess) { cudaEventDestroy(e0); cudaEventDestroy(e1); ctx->poisoned = true; return cuda_status(e, "autotune"); }
+      CU_TRY(cudaEventSynchronize(e1), "autotune sync");
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (rep > 0) tot += ms;  // first repetition warms up
+    }
+    (void)hb_bs;
+    if (tot / 3.0 < best) { best = tot / 3.0; best_c = c; }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  ctx->fft_batch_bytes[slot] = best_c;
+  if (best_ms) *best_ms = best;
   return PW_OK;
 }
 

@@ -249,6 +249,8 @@ struct pw_ctx {
   struct Buf { void* p = nullptr; size_t bytes = 0; };
   Buf ws[32];
   bool poisoned = false;
+  // tuning: bytes of half-box planes per FFT band batch (complex64, complex128); set by pw_autotune
+  size_t fft_batch_bytes[2] = {(size_t)48 << 20, (size_t)256 << 20};
   int last_sweeps = 0;  // Jacobi sweeps of the last Rayleigh-Ritz step
 };
 

@@ -26,7 +26,7 @@ STATUS = {0: "PW_OK", -1: "PW_EINVAL", -2: "PW_ENOMEM", -3: "PW_ECUDA", -4: "PW_
 EXPORTS = ("pw_ctx_create", "pw_ctx_destroy", "pw_ctx_set_stream", "pw_ctx_info", "pw_ctx_gvectors",
            "pw_ctx_projectors", "pw_hamiltonian_apply", "pw_spectrum_bounds", "pw_chebyshev_filter",
            "pw_rayleigh_ritz", "pw_chebfi_solve", "pw_density_grad", "pw_profile_enable", "pw_profile_read",
-           "pw_kernel_launches", "pw_hamiltonian_apply_noalloc", "pw_strerror", "pw_last_error")
+           "pw_kernel_launches", "pw_hamiltonian_apply_noalloc", "pw_autotune", "pw_strerror", "pw_last_error")
 
 PROF_CLASSES = ("plane_inv", "xline", "plane_fwd", "gemm_proj", "gemm_back", "small", "rr")
 
@@ -73,6 +73,7 @@ def load(path: Optional[str] = None):
     lib.pw_chebfi_solve.argtypes = [vp, vp, i64, ci, ci, ci, ci, vp, ci, pd, pd, pd]
     lib.pw_density_grad.argtypes = [vp, vp, vp, i64, ci, pd, vp, ci]
     lib.pw_hamiltonian_apply_noalloc.argtypes = [vp, vp, i64, ci, vp, i64]
+    lib.pw_autotune.argtypes = [vp, ci, ci, pd]
     lib.pw_profile_enable.argtypes = [vp, ci]
     lib.pw_profile_read.argtypes = [vp, pd, ctypes.POINTER(ctypes.c_int64)]
     lib.pw_kernel_launches.restype = ctypes.c_uint64
@@ -191,7 +192,13 @@ class Context:
         if cur.cuda_stream != self.stream.cuda_stream:
             self.stream.wait_stream(cur)
 
-    # -- diagnostics ----------------------------------------------------------------
+    # -- tuning / diagnostics -------------------------------------------------------
+    def autotune(self, nband, precision=PW_MIXED):
+        """Picks the FFT band-batch size for `nband` bands; returns the best apply time (ms)."""
+        ms = ctypes.c_double(0.0)
+        _check(load().pw_autotune(self._h, int(nband), precision, ctypes.byref(ms)))
+        return ms.value
+
     def profile(self, on=True):
         _check(load().pw_profile_enable(self._h, 1 if on else 0))
 
