@@ -147,6 +147,28 @@ PW_API int pw_chebfi_solve(pw_ctx* ctx, void* psi, int64_t ldpsi, int nband, int
 PW_API int pw_density_grad(pw_ctx* ctx, const void* a, const void* b, int64_t ld, int nband,
                            const double* w, double* out, int accumulate);
 
+/* ---- k-point batches (Sec. 2.4: k-points are independent; one launch for all) ----
+ * A batch groups contexts of one cell at different k-points (ragged sphere sizes).
+ * pw_batch_filter runs the Chebyshev filter of every k-point; the first call for a
+ * given (blocks, nband, degree, precision) runs the launches directly and captures
+ * them into one CUDA graph (k-points spread over 4 streams), later calls replay that
+ * graph with one launch, the filter intervals being read from device memory.
+ * A context's workspaces growing (a larger call made on it directly) forces a new
+ * capture.  Blocks psi[k] (device, ld[k] >= npw_k) are complex128 for PW_FP64 and
+ * complex64 for PW_MIXED; a[k] < b[k] are host arrays.  The contexts must outlive
+ * the batch and must not be used concurrently with it; their profiling must be off. */
+typedef struct pw_batch pw_batch;
+PW_API int pw_batch_create(pw_ctx* const* ctxs, int nk, void* stream, pw_batch** out);
+PW_API int pw_batch_destroy(pw_batch* batch);
+PW_API int pw_batch_filter(pw_batch* batch, void* const* psi, const int64_t* ld, int nband, int degree,
+                           const double* a, const double* b, int precision);
+/* ChebFi on every k-point (Alg. 12 per k): Lanczos bounds from v0[k] (complex128,
+ * device), `cycles` times [batched filter -> per-k FP64 Rayleigh-Ritz].  psi[k]:
+ * complex128 device blocks; eig (host, nk x nband) and resid (host, may be NULL). */
+PW_API int pw_batch_chebfi_solve(pw_batch* batch, void* const* psi, const int64_t* ld, int nband, int degree,
+                                 int cycles, int lanczos_steps, void* const* v0, int precision, double* eig,
+                                 double* resid);
+
 /* H psi = (T + V_loc + P D P^dagger) psi in FP64, like pw_hamiltonian_apply with
  * spsi = NULL, but without allocating any device memory.  The paper has no
  * counterpart; this exists for callers that may not call cudaMalloc/cudaFree at

@@ -18,7 +18,9 @@ __device__ __forceinline__ void epi_apply(const Epi<T>& e, int m, int n, cplx<T>
     case EPI_CHEB: {
       const C w = *o;
       const C yk = e.yk[m + (int64_t)n * e.ldy];
-      C r = cscale(csub(cadd(w, v), cscale(yk, e.shift)), e.alpha);
+      T alpha = e.alpha, shift = e.shift;
+      if (e.dev_ce) { shift = (T)e.dev_ce[0]; alpha = (T)((e.first ? 1.0 : 2.0) / e.dev_ce[1]); }
+      C r = cscale(csub(cadd(w, v), cscale(yk, shift)), alpha);
       if (e.ykm1) r = csub(r, cscale(e.ykm1[m + (int64_t)n * e.ldy2], e.beta));
       *o = r;
     } break;

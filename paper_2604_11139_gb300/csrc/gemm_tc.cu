@@ -318,6 +318,11 @@ __global__ void __launch_bounds__(192, 1) k_tc_gemm(const __grid_constant__ CUte
           float* __restrict__ o = epi.out + (int64_t)jc * epi.ldo + r;
           const float* __restrict__ yk = epi.yk + (int64_t)jc * epi.ldyk + r;
           const float* __restrict__ ym = epi.ykm1 ? epi.ykm1 + (int64_t)jc * epi.ldykm1 + r : nullptr;
+          float alpha = epi.alpha, shift = epi.shift;
+          if (epi.dev_ce) {
+            shift = (float)epi.dev_ce[0];
+            alpha = (float)((epi.first ? 1.0 : 2.0) / epi.dev_ce[1]);
+          }
           // issue all loads of the 32 columns before using any of them
           float wv[32], y1[32], y2[32];
 #pragma unroll
@@ -330,7 +335,7 @@ __global__ void __launch_bounds__(192, 1) k_tc_gemm(const __grid_constant__ CUte
 #pragma unroll
           for (int i = 0; i < 32; ++i) {
             if (jc + i < N) {
-              const float y = epi.alpha * (wv[i] + acc[i] - epi.shift * y1[i]) - epi.beta * y2[i];
+              const float y = alpha * (wv[i] + acc[i] - shift * y1[i]) - epi.beta * y2[i];
               o[(int64_t)i * epi.ldo] = y;
               if (epi.out_pieces > 0) split_store(epi, r, jc + i, y);
             }

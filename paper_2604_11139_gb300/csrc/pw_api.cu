@@ -53,6 +53,7 @@ void* ws_get(pw_ctx* c, int slot, size_t bytes, int* status) {
     return nullptr;
   }
   b.bytes = bytes;
+  c->ws_gen++;
   return b.p;
 }
 
@@ -231,6 +232,7 @@ Epi<T> epi(int mode, cplx<T>* out, int64_t ldo, T alpha = 1) {
   Epi<T> e;
   e.mode = mode; e.out = out; e.ldo = ldo; e.alpha = alpha; e.beta = 0; e.shift = 0;
   e.yk = nullptr; e.ykm1 = nullptr; e.ldy = 0; e.ldy2 = 0;
+  e.dev_ce = nullptr; e.first = 0;
   return e;
 }
 
@@ -407,10 +409,11 @@ int apply_impl(pw_ctx* ctx, const cplx<T>* psi, int64_t ldpsi, int nband, cplx<T
 // Chebyshev filter (Alg. 7 / Alg. 12)
 // ---------------------------------------------------------------------------
 template <typename T>
-int filter_impl(pw_ctx* ctx, cplx<T>* psi, int64_t ldpsi, int nband, int degree, double a, double b) {
+int filter_impl(pw_ctx* ctx, cplx<T>* psi, int64_t ldpsi, int nband, int degree, double a, double b,
+                const double* dev_ce = nullptr) {
   using C = cplx<T>;
   if (degree <= 0 || nband <= 0) return PW_OK;
-  if (!(b > a)) return set_error(PW_EINVAL, "filter interval needs upper > lower (a=%g, b=%g)", a, b);
+  if (!dev_ce && !(b > a)) return set_error(PW_EINVAL, "filter interval needs upper > lower (a=%g, b=%g)", a, b);
   const int npw = ctx->npw, np = ctx->nproj;
   const cudaStream_t st = ctx->stream;
   const int bb = band_batch(ctx, nband, sizeof(C));
@@ -477,6 +480,8 @@ int filter_impl(pw_ctx* ctx, cplx<T>* psi, int64_t ldpsi, int nband, int degree,
       te.alpha = (float)alpha;
       te.beta = 1.f;
       te.shift = (float)cc;
+      te.dev_ce = dev_ce;
+      te.first = (k == 0);
       te.split = ys;
       te.split_ld = ctx->kp1;
       te.split_piece_stride = (int64_t)nband * ctx->kp1;
@@ -491,6 +496,8 @@ int filter_impl(pw_ctx* ctx, cplx<T>* psi, int64_t ldpsi, int nband, int degree,
     ce.ldy = ldc;
     ce.ykm1 = (k == 0) ? nullptr : prev;
     ce.ldy2 = ldp;
+    ce.dev_ce = dev_ce;
+    ce.first = (k == 0);
     if (np > 0) {
       {
         ProfScope ps(ctx, PW_PROF_GEMM_PROJ);
@@ -924,6 +931,134 @@ void destroy_impl(pw_ctx* ctx) {
 
 }  // namespace
 
+// ---------------------------------------------------------------------------
+// k-point batches: every k-point's filter captured into one CUDA graph
+// ---------------------------------------------------------------------------
+struct pw_batch {
+  std::vector<pw_ctx*> ctx;
+  cudaStream_t stream = nullptr;  // the caller's stream
+  cudaStream_t cap = nullptr;     // the batch's own stream (captured, replayed)
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+  std::vector<cudaStream_t> side;
+  std::vector<cudaEvent_t> ev;
+  double* dev_ce = nullptr;  // {c, e} per k-point
+  std::vector<double> host_ce;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  std::vector<void*> key_psi;
+  std::vector<int64_t> key_ld;
+  std::vector<uint64_t> key_gen;
+  int key_nband = -1, key_degree = -1, key_prec = -1;
+  std::vector<void*> y32;  // complex64 copies for the mixed solve
+  std::vector<size_t> y32_bytes;
+  bool poisoned = false;
+};
+
+namespace {
+
+constexpr int kBatchStreams = 4;
+
+void batch_free_graph(pw_batch* bt) {
+  if (bt->exec) cudaGraphExecDestroy(bt->exec);
+  if (bt->graph) cudaGraphDestroy(bt->graph);
+  bt->exec = nullptr;
+  bt->graph = nullptr;
+}
+
+int batch_run_one(pw_batch* bt, int k, void* psi, int64_t ld, int nband, int degree, int precision) {
+  pw_ctx* ctx = bt->ctx[k];
+  if (precision == PW_FP64)
+    return filter_impl<double>(ctx, (double2*)psi, ld, nband, degree, 0.0, 1.0, bt->dev_ce + 2 * k);
+  return filter_impl<float>(ctx, (float2*)psi, ld, nband, degree, 0.0, 1.0, bt->dev_ce + 2 * k);
+}
+
+int batch_filter_body(pw_batch* bt, void* const* psi, const int64_t* ld, int nband, int degree, int precision) {
+  const int nk = (int)bt->ctx.size();
+  cudaError_t e;
+  bool same = bt->exec && bt->key_nband == nband && bt->key_degree == degree && bt->key_prec == precision;
+  for (int k = 0; same && k < nk; ++k)
+    same = bt->key_psi[k] == psi[k] && bt->key_ld[k] == ld[k] && bt->key_gen[k] == bt->ctx[k]->ws_gen;
+  if (same) {
+    e = cudaGraphLaunch(bt->exec, bt->cap);
+    if (e != cudaSuccess) { bt->poisoned = true; return cuda_status(e, "batch graph launch"); }
+    return PW_OK;
+  }
+  // first call for this shape: run eagerly (allocates every workspace), then capture the
+  // same launches, fanned out over kBatchStreams streams, for the following calls
+  batch_free_graph(bt);
+  std::vector<cudaStream_t> saved(nk);
+  for (int k = 0; k < nk; ++k) {
+    if (bt->ctx[k]->prof_on) return set_error(PW_EINVAL, "disable profiling on batched contexts");
+    saved[k] = bt->ctx[k]->stream;
+    bt->ctx[k]->stream = bt->cap;
+  }
+  int st = PW_OK;
+  for (int k = 0; k < nk && st == PW_OK; ++k) st = batch_run_one(bt, k, psi[k], ld[k], nband, degree, precision);
+  if (st != PW_OK) {
+    for (int k = 0; k < nk; ++k) bt->ctx[k]->stream = saved[k];
+    return st;
+  }
+  e = cudaStreamBeginCapture(bt->cap, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) {
+    const int ns = (int)bt->side.size();
+    cudaEventRecord(bt->ev[0], bt->cap);
+    for (int i = 0; i < ns; ++i) cudaStreamWaitEvent(bt->side[i], bt->ev[0], 0);
+    for (int k = 0; k < nk && st == PW_OK; ++k) {
+      bt->ctx[k]->stream = bt->side[k % ns];
+      st = batch_run_one(bt, k, psi[k], ld[k], nband, degree, precision);
+    }
+    for (int i = 0; i < ns; ++i) {
+      cudaEventRecord(bt->ev[1 + i], bt->side[i]);
+      cudaStreamWaitEvent(bt->cap, bt->ev[1 + i], 0);
+    }
+    cudaGraph_t g = nullptr;
+    const cudaError_t e2 = cudaStreamEndCapture(bt->cap, &g);
+    if (st == PW_OK && e2 == cudaSuccess && g) {
+      bt->graph = g;
+      e = cudaGraphInstantiate(&bt->exec, g, 0);
+      if (e != cudaSuccess) { batch_free_graph(bt); st = cuda_status(e, "batch graph instantiate"); }
+    } else {
+      if (g) cudaGraphDestroy(g);
+      if (st == PW_OK) st = cuda_status(e2 == cudaSuccess ? cudaErrorStreamCaptureInvalidated : e2, "batch capture");
+    }
+  } else {
+    st = cuda_status(e, "batch capture begin");
+  }
+  for (int k = 0; k < nk; ++k) bt->ctx[k]->stream = saved[k];
+  if (st != PW_OK) return st;
+  bt->key_psi.assign(psi, psi + nk);
+  bt->key_ld.assign(ld, ld + nk);
+  bt->key_gen.resize(nk);
+  for (int k = 0; k < nk; ++k) bt->key_gen[k] = bt->ctx[k]->ws_gen;
+  bt->key_nband = nband;
+  bt->key_degree = degree;
+  bt->key_prec = precision;
+  return PW_OK;
+}
+
+// the caller's stream -> batch stream (interval upload, graph or first run) -> the caller's stream
+int batch_filter_impl(pw_batch* bt, void* const* psi, const int64_t* ld, int nband, int degree, const double* a,
+                      const double* b, int precision) {
+  const int nk = (int)bt->ctx.size();
+  for (int k = 0; k < nk; ++k) {
+    if (!(b[k] > a[k])) return set_error(PW_EINVAL, "k-point %d: filter interval needs upper > lower", k);
+    bt->host_ce[2 * k] = 0.5 * (b[k] + a[k]);
+    bt->host_ce[2 * k + 1] = 0.5 * (b[k] - a[k]);
+  }
+  cudaError_t e = cudaEventRecord(bt->ev_in, bt->stream);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(bt->cap, bt->ev_in, 0);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(bt->dev_ce, bt->host_ce.data(), sizeof(double) * 2 * nk, cudaMemcpyHostToDevice, bt->cap);
+  if (e != cudaSuccess) { bt->poisoned = true; return cuda_status(e, "batch interval upload"); }
+  const int st = batch_filter_body(bt, psi, ld, nband, degree, precision);
+  e = cudaEventRecord(bt->ev_out, bt->cap);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(bt->stream, bt->ev_out, 0);
+  if (e != cudaSuccess) { bt->poisoned = true; return cuda_status(e, "batch join"); }
+  return st;
+}
+
+}  // namespace
+
 // ===========================================================================
 // exported C ABI
 // ===========================================================================
@@ -1151,6 +1286,135 @@ PW_API int pw_profile_read(pw_ctx* ctx, double* ms, int64_t* launches) {
 }
 
 PW_API uint64_t pw_kernel_launches(void) { return g_launches.load(); }
+
+PW_API int pw_batch_create(pw_ctx* const* ctxs, int nk, void* stream, pw_batch** out) {
+  if (!ctxs || !out || nk <= 0) return set_error(PW_EINVAL, "bad batch arguments");
+  *out = nullptr;
+  for (int k = 0; k < nk; ++k) PW_TRY(check_ctx(ctxs[k]));
+  pw_batch* bt = new (std::nothrow) pw_batch();
+  if (!bt) return set_error(PW_ENOMEM, "host allocation");
+  bt->ctx.assign(ctxs, ctxs + nk);
+  bt->stream = (cudaStream_t)stream;
+  bt->host_ce.assign(2 * nk, 0.0);
+  cudaError_t e = cudaMalloc(&bt->dev_ce, sizeof(double) * 2 * nk);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&bt->cap, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&bt->ev_in, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&bt->ev_out, cudaEventDisableTiming);
+  const int ns = std::min(kBatchStreams, nk);
+  for (int i = 0; i < ns && e == cudaSuccess; ++i) {
+    cudaStream_t s;
+    e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+    if (e == cudaSuccess) bt->side.push_back(s);
+  }
+  for (int i = 0; i < ns + 1 && e == cudaSuccess; ++i) {
+    cudaEvent_t ev;
+    e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+    if (e == cudaSuccess) bt->ev.push_back(ev);
+  }
+  if (e != cudaSuccess) {
+    pw_batch_destroy(bt);
+    return cuda_status(e, "batch creation");
+  }
+  *out = bt;
+  return PW_OK;
+}
+
+PW_API int pw_batch_destroy(pw_batch* bt) {
+  if (!bt) return PW_OK;
+  if (bt->cap) cudaStreamSynchronize(bt->cap);
+  batch_free_graph(bt);
+  if (bt->cap) cudaStreamDestroy(bt->cap);
+  if (bt->ev_in) cudaEventDestroy(bt->ev_in);
+  if (bt->ev_out) cudaEventDestroy(bt->ev_out);
+  for (cudaStream_t s : bt->side) { cudaStreamSynchronize(s); cudaStreamDestroy(s); }
+  for (cudaEvent_t ev : bt->ev) cudaEventDestroy(ev);
+  for (void* p : bt->y32) if (p) cudaFree(p);
+  if (bt->dev_ce) cudaFree(bt->dev_ce);
+  delete bt;
+  return PW_OK;
+}
+
+PW_API int pw_batch_filter(pw_batch* bt, void* const* psi, const int64_t* ld, int nband, int degree, const double* a,
+                           const double* b, int precision) {
+  if (!bt || !psi || !ld || !a || !b) return set_error(PW_EINVAL, "NULL argument");
+  if (bt->poisoned) return set_error(PW_ECUDA, "batch poisoned by an earlier CUDA error");
+  if (precision != PW_FP64 && precision != PW_MIXED) return set_error(PW_EINVAL, "unknown precision");
+  if (degree < 0 || nband < 0) return set_error(PW_EINVAL, "negative degree or nband");
+  for (size_t k = 0; k < bt->ctx.size(); ++k) {
+    PW_TRY(check_ctx(bt->ctx[k]));
+    PW_TRY(check_block(bt->ctx[k], psi[k], ld[k], nband));
+  }
+  if (degree == 0 || nband == 0) return PW_OK;
+  return batch_filter_impl(bt, psi, ld, nband, degree, a, b, precision);
+}
+
+PW_API int pw_batch_chebfi_solve(pw_batch* bt, void* const* psi, const int64_t* ld, int nband, int degree, int cycles,
+                                 int lanczos_steps, void* const* v0, int precision, double* eig, double* resid) {
+  if (!bt || !psi || !ld || !eig) return set_error(PW_EINVAL, "NULL argument");
+  if (precision != PW_FP64 && precision != PW_MIXED) return set_error(PW_EINVAL, "unknown precision");
+  const int nk = (int)bt->ctx.size();
+  for (int k = 0; k < nk; ++k) {
+    PW_TRY(check_ctx(bt->ctx[k]));
+    PW_TRY(check_block(bt->ctx[k], psi[k], ld[k], nband));
+  }
+  if (nband == 0) return PW_OK;
+  std::vector<double> a(nk), b(nk);
+  for (int k = 0; k < nk; ++k) {
+    pw_ctx* ctx = bt->ctx[k];
+    const cudaStream_t saved = ctx->stream;
+    ctx->stream = bt->stream;
+    double lo = 0;
+    const int s = bounds_impl(ctx, (const double2*)psi[k], ld[k], nband, lanczos_steps,
+                              v0 ? (const double2*)v0[k] : nullptr, &lo, &a[k], &b[k]);
+    ctx->stream = saved;
+    if (s != PW_OK) return s;
+  }
+  std::vector<void*> fpsi(nk);
+  std::vector<int64_t> fld(nk);
+  if (precision == PW_MIXED) {
+    bt->y32.resize(nk, nullptr);
+    bt->y32_bytes.resize(nk, 0);
+    for (int k = 0; k < nk; ++k) {
+      const size_t need = sizeof(float2) * (size_t)bt->ctx[k]->npw * nband;
+      if (bt->y32_bytes[k] < need) {
+        if (bt->y32[k]) cudaFree(bt->y32[k]);
+        cudaError_t e = cudaMalloc(&bt->y32[k], need);
+        if (e != cudaSuccess) { bt->y32[k] = nullptr; bt->y32_bytes[k] = 0; return cuda_status(e, "batch c64 buffer"); }
+        bt->y32_bytes[k] = need;
+      }
+      fpsi[k] = bt->y32[k];
+      fld[k] = bt->ctx[k]->npw;
+    }
+  } else {
+    for (int k = 0; k < nk; ++k) { fpsi[k] = psi[k]; fld[k] = ld[k]; }
+  }
+  for (int c = 0; c < cycles; ++c) {
+    if (precision == PW_MIXED)
+      for (int k = 0; k < nk; ++k) {
+        cudaError_t e = la_to_c64((const double2*)psi[k], ld[k], (float2*)fpsi[k], fld[k], bt->ctx[k]->npw, nband,
+                                  bt->stream);
+        if (e != cudaSuccess) { bt->poisoned = true; return cuda_status(e, "to c64"); }
+      }
+    PW_TRY(batch_filter_impl(bt, fpsi.data(), fld.data(), nband, degree, a.data(), b.data(), precision));
+    if (precision == PW_MIXED)
+      for (int k = 0; k < nk; ++k) {
+        cudaError_t e = la_to_c128((const float2*)fpsi[k], fld[k], (double2*)psi[k], ld[k], bt->ctx[k]->npw, nband,
+                                   bt->stream);
+        if (e != cudaSuccess) { bt->poisoned = true; return cuda_status(e, "to c128"); }
+      }
+    for (int k = 0; k < nk; ++k) {
+      pw_ctx* ctx = bt->ctx[k];
+      const cudaStream_t saved = ctx->stream;
+      ctx->stream = bt->stream;
+      const int s = rr_impl(ctx, (double2*)psi[k], ld[k], nband, nullptr, eig + (size_t)k * nband,
+                            resid ? resid + (size_t)k * nband : nullptr);
+      ctx->stream = saved;
+      if (s != PW_OK) return s;
+      a[k] = eig[(size_t)k * nband + nband - 1];
+    }
+  }
+  return PW_OK;
+}
 
 PW_API const char* pw_strerror(int status) {
   switch (status) {

@@ -162,6 +162,10 @@ template <typename T> struct Epi {
   const cplx<T>* yk;
   const cplx<T>* ykm1;
   int64_t ldy, ldy2;
+  // optional device {c, e}: when set, shift = c and alpha = (first ? 1 : 2) / e are read on
+  // the device, so a captured graph stays valid when the filter interval changes
+  const double* dev_ce;
+  int first;
 };
 
 // ---------------------------------------------------------------------------
@@ -249,6 +253,7 @@ struct pw_ctx {
   struct Buf { void* p = nullptr; size_t bytes = 0; };
   Buf ws[32];
   bool poisoned = false;
+  uint64_t ws_gen = 0;  // bumped whenever a workspace is (re)allocated (captured graphs check it)
   // tuning: bytes of half-box planes per FFT band batch (complex64, complex128); set by pw_autotune
   size_t fft_batch_bytes[2] = {(size_t)48 << 20, (size_t)256 << 20};
   int last_sweeps = 0;  // Jacobi sweeps of the last Rayleigh-Ritz step

@@ -23,6 +23,8 @@ struct TcEpi {
   const float* ykm1;
   int64_t ldykm1;
   float alpha, beta, shift;
+  const double* dev_ce;  // optional device {c, e}: shift = c, alpha = (first ? 1 : 2) / e
+  int first;
   // optional bf16 pieces of the CHEB output: split[p * split_piece_stride + j * split_ld + r]
   __nv_bfloat16* split;
   int64_t split_ld, split_piece_stride;

@@ -26,7 +26,8 @@ STATUS = {0: "PW_OK", -1: "PW_EINVAL", -2: "PW_ENOMEM", -3: "PW_ECUDA", -4: "PW_
 EXPORTS = ("pw_ctx_create", "pw_ctx_destroy", "pw_ctx_set_stream", "pw_ctx_info", "pw_ctx_gvectors",
            "pw_ctx_projectors", "pw_hamiltonian_apply", "pw_spectrum_bounds", "pw_chebyshev_filter",
            "pw_rayleigh_ritz", "pw_chebfi_solve", "pw_density_grad", "pw_profile_enable", "pw_profile_read",
-           "pw_kernel_launches", "pw_hamiltonian_apply_noalloc", "pw_autotune", "pw_strerror", "pw_last_error")
+           "pw_kernel_launches", "pw_hamiltonian_apply_noalloc", "pw_autotune", "pw_batch_create",
+           "pw_batch_destroy", "pw_batch_filter", "pw_batch_chebfi_solve", "pw_strerror", "pw_last_error")
 
 PROF_CLASSES = ("plane_inv", "xline", "plane_fwd", "gemm_proj", "gemm_back", "small", "rr")
 
@@ -74,6 +75,12 @@ def load(path: Optional[str] = None):
     lib.pw_density_grad.argtypes = [vp, vp, vp, i64, ci, pd, vp, ci]
     lib.pw_hamiltonian_apply_noalloc.argtypes = [vp, vp, i64, ci, vp, i64]
     lib.pw_autotune.argtypes = [vp, ci, ci, pd]
+    pvp = ctypes.POINTER(vp)
+    pi64 = ctypes.POINTER(ctypes.c_int64)
+    lib.pw_batch_create.argtypes = [pvp, ci, vp, pvp]
+    lib.pw_batch_destroy.argtypes = [vp]
+    lib.pw_batch_filter.argtypes = [vp, pvp, pi64, ci, ci, pd, pd, ci]
+    lib.pw_batch_chebfi_solve.argtypes = [vp, pvp, pi64, ci, ci, ci, ci, pvp, ci, pd, pd]
     lib.pw_profile_enable.argtypes = [vp, ci]
     lib.pw_profile_read.argtypes = [vp, pd, ctypes.POINTER(ctypes.c_int64)]
     lib.pw_kernel_launches.restype = ctypes.c_uint64
@@ -319,3 +326,65 @@ class Context:
         _check(load().pw_density_grad(self._h, ctypes.c_void_p(a.data_ptr()), bp, ld, m, _dptr(w),
                                       ctypes.c_void_p(out.data_ptr()), 1 if accumulate else 0))
         return out
+
+
+class Batch:
+    """k-point batch (pw_batch): every context's filter in one captured CUDA graph."""
+
+    def __init__(self, contexts, stream=None):
+        import torch
+        lib = load()
+        self.contexts = list(contexts)
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self.stream = stream
+        arr = (ctypes.c_void_p * len(self.contexts))(*[c._h.value for c in self.contexts])
+        h = ctypes.c_void_p()
+        _check(lib.pw_batch_create(arr, len(self.contexts), ctypes.c_void_p(stream.cuda_stream), ctypes.byref(h)))
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            load().pw_batch_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def _blocks(self, psis, dtype):
+        ptrs, lds, m = [], [], None
+        for ctx, p in zip(self.contexts, psis):
+            p, mm, ld = _block(p, dtype, "psi")
+            if m is None:
+                m = mm
+            elif mm != m:
+                raise ValueError("every k-point needs the same number of bands")
+            ptrs.append(p.data_ptr())
+            lds.append(ld)
+        return (ctypes.c_void_p * len(ptrs))(*ptrs), (ctypes.c_int64 * len(lds))(*lds), m
+
+    def filter(self, psis, degree, a, b, precision=PW_FP64):
+        pa, pl, m = self._blocks(psis, _dtype(precision))
+        a = np.ascontiguousarray(np.asarray(a, dtype=np.float64))
+        b = np.ascontiguousarray(np.asarray(b, dtype=np.float64))
+        _check(load().pw_batch_filter(self._h, pa, pl, m, int(degree), _dptr(a), _dptr(b), precision))
+
+    def chebfi_solve(self, psis, degree, cycles, v0s, lanczos_steps=10, precision=PW_FP64):
+        import torch
+        pa, pl, m = self._blocks(psis, torch.complex128)
+        vptr = (ctypes.c_void_p * len(v0s))(*[_block(v, torch.complex128, "v0")[0].data_ptr() for v in v0s])
+        nk = len(self.contexts)
+        eig = np.zeros((nk, m))
+        res = np.zeros((nk, m))
+        _check(load().pw_batch_chebfi_solve(self._h, pa, pl, m, int(degree), int(cycles), int(lanczos_steps), vptr,
+                                            precision, _dptr(eig), _dptr(res)))
+        return eig, res
