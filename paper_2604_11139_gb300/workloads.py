@@ -209,7 +209,7 @@ def mp_kpoints(grid=(4, 4, 2)) -> np.ndarray:
     return np.array(ks)
 
 
-def ecut_jitter(seed: int, nk: int, base: float, lo=0.85, hi=1.12) -> np.ndarray:
+def ecut_jitter(seed: int, nk: int, base: float, lo=0.86, hi=1.10) -> np.ndarray:
     """Per-k cut-off factors that spread the sphere sizes (ragged batches)."""
     rng = np.random.default_rng(seed + 31337)
     return base * rng.uniform(lo, hi, size=nk)
