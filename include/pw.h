@@ -169,6 +169,57 @@ PW_API int pw_batch_chebfi_solve(pw_batch* batch, void* const* psi, const int64_
                                  int cycles, int lanczos_steps, void* const* v0, int precision, double* eig,
                                  double* resid);
 
+/* ---- differentiation form (S = I): reverse-mode adjoint of ChebFi ----
+ * The parameters of H are V_loc(r_j) and D.  pw_ctx_set_vloc / pw_ctx_set_D replace
+ * them in a context (V_loc: n1*n2*n3 doubles in C order; D: nproj*nproj doubles,
+ * column-major, zero outside the context's D blocks; host or device pointers, read
+ * during the call; pw_ctx_set_D needs Q == NULL).
+ * pw_local_apply: out = alpha V psi for an arbitrary real potential v on the FFT grid
+ * (device, n1*n2*n3 doubles, C order) through the same sphere -> box FFT, multiply and
+ * box -> sphere FFT as the local part of H (Sec. 3.2); no kinetic or nonlocal term.
+ * psi, out: device blocks of the precision's element type (complex128 / complex64).
+ * It is the adjoint of the density (Alg. 3 density step): for
+ * rho(r) = sum_i w |psi_i(r)|^2 and a loss gradient rho_bar(r), the gradient of psi_i
+ * is pw_local_apply with v = rho_bar and alpha = 2 w n1n2n3. */
+PW_API int pw_ctx_set_vloc(pw_ctx* ctx, const double* vloc);
+PW_API int pw_ctx_set_D(pw_ctx* ctx, const double* D);
+PW_API int pw_local_apply(pw_ctx* ctx, const double* v, double alpha, const void* psi, int64_t ld,
+                          int nband, void* out, int64_t ldo, int precision);
+
+/* A differentiation handle holds the tape of `cycles` ChebFi cycles of degree `degree`
+ * on nband bands: per cycle the filter iterates (pairs (Y_{js}, Y_{js+1}) of every
+ * segment of ckpt steps; ckpt <= 2 keeps them all), P^dagger Y_k, the S-orthonormal
+ * block Q, the Rayleigh-Ritz rotation X and (Q^dagger Y_m)^-dagger.  precision PW_MIXED
+ * runs the filter and its adjoint in complex64 with BF16-split tensor-core projector
+ * GEMMs; the Rayleigh-Ritz step and its adjoint are FP64 in both precisions.  The
+ * handle allocates all its device memory at creation (pw_diff_tape_bytes reports it). */
+typedef struct pw_diff pw_diff;
+PW_API int pw_diff_create(pw_ctx* ctx, int nband, int degree, int cycles, int ckpt, int precision,
+                          pw_diff** out);
+PW_API int pw_diff_destroy(pw_diff* diff);
+PW_API int pw_diff_tape_bytes(const pw_diff* diff, int64_t* bytes);
+/* Forward: the ChebFi cycles of pw_chebfi_solve (Alg. 12), recording the tape.  psi:
+ * complex128 device block (ld), overwritten with the Ritz vectors.  The filter
+ * interval is stop-gradient: bounds_in (host, 1 + cycles doubles: the upper bound b,
+ * then the cut a of every cycle) replays given bounds; NULL computes them (Lanczos
+ * from v0 with lanczos_steps steps, cycle-1 cut = max Rayleigh quotient of psi, later
+ * cuts = largest Ritz value).  eig (host, nband) and bounds_out (host, 1 + cycles) may
+ * be NULL. */
+PW_API int pw_diff_forward(pw_diff* diff, void* psi, int64_t ld, int lanczos_steps, const void* v0,
+                           const double* bounds_in, double* eig, double* bounds_out);
+/* Backward: given the adjoints of the last cycle's Ritz values (eig_bar, host, nband,
+ * NULL = 0) and Ritz vectors (psi_bar, complex128 device block, NULL = 0), in PyTorch's
+ * convention (psi_bar = dL/dRe psi + i dL/dIm psi), writes (accumulate = 0) or adds
+ * dL/dV_loc(r_j) to dV (device, n1*n2*n3 doubles, C order) and dL/dD_ab, entries taken
+ * as independent, to dD (device, nproj*nproj doubles, column-major); either may be NULL.
+ * split < 0 keeps every eigenvector-coupling pair (i, j) of the last cycle; split >= 0
+ * keeps only pairs with one band below split and one at or above it, which is exact
+ * when the loss does not change under rotations among bands [0, split) and among
+ * [split, nband) (e.g. sums of occupied eigenvalues and the occupied density) and
+ * avoids dividing by small gaps.  PW_EINVAL if V_loc or D changed since the forward. */
+PW_API int pw_diff_backward(pw_diff* diff, const double* eig_bar, const void* psi_bar, int64_t ld,
+                            int split, double* dV, double* dD, int accumulate);
+
 /* H psi = (T + V_loc + P D P^dagger) psi in FP64, like pw_hamiltonian_apply with
  * spsi = NULL, but without allocating any device memory.  The paper has no
  * counterpart; this exists for callers that may not call cudaMalloc/cudaFree at

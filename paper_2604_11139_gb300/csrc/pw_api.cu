@@ -534,6 +534,87 @@ int filter_impl(pw_ctx* ctx, cplx<T>* psi, int64_t ldpsi, int nband, int degree,
   return PW_OK;
 }
 
+// One step of the three-term recurrence with explicit coefficients, S = I:
+//   dst = alpha ((H - shift) cur) - beta prev     (prev may be NULL)
+// The forward filter steps and the steps of its adjoint (H is Hermitian, so the
+// adjoint recurrence applies H itself) both have this form.  C_out (nproj x nband,
+// ld nproj, may be NULL) receives P^dagger cur.
+template <typename T>
+int recur_step(pw_ctx* ctx, const cplx<T>* cur, int64_t ldc, const cplx<T>* prev, int64_t ldp, cplx<T>* dst,
+               int64_t ldd, int nband, double alpha, double beta, double shift, cplx<T>* C_out) {
+  using C = cplx<T>;
+  if (ctx->has_q) return set_error(PW_EUNSUPPORTED, "the explicit recurrence step needs S = I (Q == NULL)");
+  if (nband <= 0) return PW_OK;
+  const int npw = ctx->npw, np = ctx->nproj;
+  const cudaStream_t st = ctx->stream;
+  const int bb = band_batch(ctx, nband, sizeof(C));
+  const int64_t hb_bs = (int64_t)ctx->sp.nplane * ctx->n[1] * ctx->n[2];
+  WS(hb, C, WS_HB, hb_bs * bb);
+  WS(Cm, C, WS_C, (size_t)np * nband);
+  WS(Z, C, WS_Z, (size_t)np * nband);
+  const int ns = nsplit_for(np, nband, npw);
+  WS(spl, C, WS_SPLIT, (size_t)ns * np * nband);
+  C* Cp = C_out ? C_out : Cm;
+  CU_TRY(launch_local_apply<T>(ctx->plan, Prec<T>::tw(ctx), ctx->sp, Prec<T>::vp(ctx), Prec<T>::kin(ctx), cur, ldc,
+                               nband, dst, ldd, hb, bb, st, ctx), "recurrence local");
+  if constexpr (std::is_same<T, float>::value) {
+    if (np > 0) {
+      PW_TRY(ensure_tc(ctx));
+      __nv_bfloat16 *ys, *zs;
+      {
+        ProfScope ps(ctx, PW_PROF_GEMM_PROJ);
+        PW_TRY(tc_split(ctx, (const float2*)cur, ldc, npw, nband, ctx->kp1, WS_YSPLIT, &ys));
+        PW_TRY(tc_project(ctx, ys, nband, (float2*)Cp));
+      }
+      {
+        ProfScope ps(ctx, PW_PROF_SMALL);
+        CU_TRY(launch_dblock<T>(np, nband, Prec<T>::D(ctx), ctx->blk0, ctx->blklen, Cp, np, Z, np, st),
+               "recurrence D");
+        PW_TRY(tc_split(ctx, (const float2*)Z, np, np, nband, ctx->kp2, WS_ZSPLIT, &zs));
+      }
+      ProfScope ps(ctx, PW_PROF_GEMM_BACK);
+      tc::TcEpi te{};
+      te.mode = tc::TC_EPI_CHEB;
+      te.out = (float*)dst;
+      te.ldo = 2 * ldd;
+      te.yk = (const float*)cur;
+      te.ldyk = 2 * ldc;
+      te.ykm1 = prev ? (const float*)prev : nullptr;
+      te.ldykm1 = 2 * ldp;
+      te.alpha = (float)alpha;
+      te.beta = (float)beta;
+      te.shift = (float)shift;
+      PW_TRY(tc_backproject(ctx, zs, nband, te));
+      return PW_OK;
+    }
+  }
+  Epi<T> ce = epi<T>(EPI_CHEB, dst, ldd, (T)alpha);
+  ce.beta = (T)beta;
+  ce.shift = (T)shift;
+  ce.yk = cur;
+  ce.ldy = ldc;
+  ce.ykm1 = prev;
+  ce.ldy2 = ldp;
+  if (np > 0) {
+    {
+      ProfScope ps(ctx, PW_PROF_GEMM_PROJ);
+      CU_TRY(launch_cgemm<T>(1, 0, np, nband, npw, Prec<T>::P(ctx), npw, cur, ldc, epi<T>(EPI_STORE, Cp, np), ns,
+                             spl, st), "recurrence projection");
+    }
+    {
+      ProfScope ps(ctx, PW_PROF_SMALL);
+      CU_TRY(launch_dblock<T>(np, nband, Prec<T>::D(ctx), ctx->blk0, ctx->blklen, Cp, np, Z, np, st),
+             "recurrence D");
+    }
+    ProfScope ps(ctx, PW_PROF_GEMM_BACK);
+    CU_TRY(launch_cgemm<T>(0, 0, npw, nband, np, Prec<T>::P(ctx), npw, Z, np, ce, 1, spl, st), "recurrence");
+  } else {
+    ProfScope ps(ctx, PW_PROF_GEMM_BACK);
+    CU_TRY(launch_cgemm<T>(0, 0, npw, nband, 0, Prec<T>::P(ctx), npw, Z, 1, ce, 1, spl, st), "recurrence");
+  }
+  return PW_OK;
+}
+
 // ---------------------------------------------------------------------------
 // S-Ortho (Alg. 9) and Rayleigh-Ritz (Alg. 5), FP64
 // ---------------------------------------------------------------------------
@@ -559,7 +640,10 @@ int check_flag(pw_ctx* ctx, int* flag_dev, const char* what) {
   return PW_OK;
 }
 
-int rr_impl(pw_ctx* ctx, double2* Y, int64_t ldy, int m, double2* hpsi_out, double* eig_h, double* resid_h) {
+// q_out (ld npw): the S-orthonormal block Q before the rotation; x_out (m x m): the rotation X
+// (Psi = Q X); eig_dev_out (device, m): the Ritz values.  Each may be NULL.
+int rr_impl(pw_ctx* ctx, double2* Y, int64_t ldy, int m, double2* hpsi_out, double* eig_h, double* resid_h,
+            double2* q_out = nullptr, double2* x_out = nullptr, double* eig_dev_out = nullptr) {
   PW_TRY(check_tc_flag(ctx));
   ProfScope rr_scope(ctx, PW_PROF_RR);
   const int npw = ctx->npw;
@@ -595,6 +679,9 @@ int rr_impl(pw_ctx* ctx, double2* Y, int64_t ldy, int m, double2* hpsi_out, doub
                              cudaMemcpyDeviceToDevice, st), "s-ortho copy");
   }
   PW_TRY(check_flag(ctx, scal, "S-Ortho Cholesky"));
+  if (q_out)
+    CU_TRY(cudaMemcpy2DAsync(q_out, sizeof(double2) * npw, Y, sizeof(double2) * ldy, sizeof(double2) * npw, m,
+                             cudaMemcpyDeviceToDevice, st), "copy Q");
   // H Psi, S Psi
   PW_TRY(apply_impl<double>(ctx, Y, ldy, m, HY, ctx->has_q ? SYb : nullptr, npw));
   const double2* SY = ctx->has_q ? SYb : Y;
@@ -616,6 +703,9 @@ int rr_impl(pw_ctx* ctx, double2* Y, int64_t ldy, int m, double2* hpsi_out, doub
   ctx->last_sweeps = sweeps;
   // X = Linv^dagger U  -> tmp
   CU_TRY(launch_cgemm<double>(1, 0, m, m, m, Linv, m, U, m, epi<double>(EPI_STORE, tmp, m), 1, nullptr, st), "back-transform");
+  if (x_out) CU_TRY(cudaMemcpyAsync(x_out, tmp, sizeof(double2) * m * m, cudaMemcpyDeviceToDevice, st), "copy X");
+  if (eig_dev_out)
+    CU_TRY(cudaMemcpyAsync(eig_dev_out, eig, sizeof(double) * m, cudaMemcpyDeviceToDevice, st), "copy eig");
   // rotate Y, HY, SY
   CU_TRY(launch_cgemm<double>(0, 0, npw, m, m, Y, ldy, tmp, m, epi<double>(EPI_STORE, ROT, npw), 1, nullptr, st), "rotate Y");
   CU_TRY(cudaMemcpy2DAsync(Y, sizeof(double2) * ldy, ROT, sizeof(double2) * npw, sizeof(double2) * npw, m,
@@ -857,6 +947,8 @@ int create_impl(const pw_problem_desc* d, void* stream, pw_ctx** out) {
   PW_TRY(upload(ctx, &ctx->D64, Dh.data(), Dh.size()));
   PW_TRY(upload(ctx, &ctx->D32, (const float*)nullptr, Dh.size()));
   CU_TRY(cast_d2f(ctx->D64, ctx->D32, (int64_t)Dh.size(), st), "D cast");
+  ctx->blk0_h = b0;
+  ctx->blklen_h = bl;
   PW_TRY(upload(ctx, &ctx->blk0, b0.data(), std::max<size_t>(b0.size(), 1)));
   PW_TRY(upload(ctx, &ctx->blklen, bl.data(), std::max<size_t>(bl.size(), 1)));
   // Woodbury matrices for S^-1 (Sec. 3.3): K = (Q^-1 + P^dagger P)^-1, E = (I - K P^dagger P) D
@@ -930,6 +1022,38 @@ void destroy_impl(pw_ctx* ctx) {
 }
 
 }  // namespace
+
+// ---------------------------------------------------------------------------
+// internal entry points used by the adjoint translation unit (api.cuh)
+// ---------------------------------------------------------------------------
+namespace pw {
+namespace api {
+int check(pw_ctx* ctx) { return check_ctx(ctx); }
+int check_blk(pw_ctx* ctx, const void* p, int64_t ld, int nband) { return check_block(ctx, p, ld, nband); }
+int apply64(pw_ctx* ctx, const double2* psi, int64_t ld, int nband, double2* hpsi, int64_t ldo) {
+  return apply_impl<double>(ctx, psi, ld, nband, hpsi, nullptr, ldo);
+}
+template <typename T>
+int recur(pw_ctx* ctx, const cplx<T>* cur, int64_t ldc, const cplx<T>* prev, int64_t ldp, cplx<T>* dst, int64_t ldd,
+          int nband, double alpha, double beta, double shift, cplx<T>* C_out) {
+  return recur_step<T>(ctx, cur, ldc, prev, ldp, dst, ldd, nband, alpha, beta, shift, C_out);
+}
+template int recur<double>(pw_ctx*, const double2*, int64_t, const double2*, int64_t, double2*, int64_t, int, double,
+                           double, double, double2*);
+template int recur<float>(pw_ctx*, const float2*, int64_t, const float2*, int64_t, float2*, int64_t, int, double,
+                          double, double, float2*);
+int rr(pw_ctx* ctx, double2* Y, int64_t ldy, int m, double* eig_h, double2* q_out, double2* x_out,
+       double* eig_dev_out) {
+  return rr_impl(ctx, Y, ldy, m, nullptr, eig_h, nullptr, q_out, x_out, eig_dev_out);
+}
+int bounds(pw_ctx* ctx, const double2* psi, int64_t ld, int nband, int steps, const double2* v0, double* rq_max,
+           double* upper) {
+  return bounds_impl(ctx, psi, ld, nband, steps, v0, nullptr, rq_max, upper);
+}
+int fft_band_batch(const pw_ctx* ctx, int nband, size_t elem) { return band_batch(ctx, nband, elem); }
+int gemm_nsplit(int m, int n, int k) { return nsplit_for(m, n, k); }
+}  // namespace api
+}  // namespace pw
 
 // ---------------------------------------------------------------------------
 // k-point batches: every k-point's filter captured into one CUDA graph

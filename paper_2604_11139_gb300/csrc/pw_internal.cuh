@@ -225,6 +225,8 @@ struct pw_ctx {
   float* D32 = nullptr;
   int* blk0 = nullptr;      // per projector: first index of its D block
   int* blklen = nullptr;
+  std::vector<int> blk0_h, blklen_h;  // host copies of the D block structure
+  uint64_t param_gen = 0;   // bumped whenever V_loc or D is replaced
   double* Q64 = nullptr;
   int* qblk0 = nullptr;     // per projector: first index of its Q block
   int* qblklen = nullptr;
@@ -265,7 +267,7 @@ enum WsSlot {
   WS_YSPLIT, WS_WSPLIT, WS_ZSPLIT, WS_TCPART, WS_TCERR,      // tensor-core mixed path
   WS_HY, WS_SY, WS_ROT, WS_Y32,                              // Rayleigh-Ritz / solve
   WS_GRAM, WS_GRAM2, WS_LINV, WS_TMP, WS_U, WS_JAC, WS_EIG,  // subspace matrices
-  WS_LZ, WS_RQ, WS_DEN, WS_SCAL, WS_NUM
+  WS_LZ, WS_RQ, WS_DEN, WS_SCAL, WS_VPOT, WS_NUM
 };
 void* ws_get(pw_ctx* c, int slot, size_t bytes, int* status);
 // process-wide count of kernel launches issued by this library (diagnostics)

@@ -10,6 +10,7 @@ from __future__ import annotations
 
 import ctypes
 import os
+import weakref
 from typing import Optional
 
 import numpy as np
@@ -27,7 +28,9 @@ EXPORTS = ("pw_ctx_create", "pw_ctx_destroy", "pw_ctx_set_stream", "pw_ctx_info"
            "pw_ctx_projectors", "pw_hamiltonian_apply", "pw_spectrum_bounds", "pw_chebyshev_filter",
            "pw_rayleigh_ritz", "pw_chebfi_solve", "pw_density_grad", "pw_profile_enable", "pw_profile_read",
            "pw_kernel_launches", "pw_hamiltonian_apply_noalloc", "pw_autotune", "pw_batch_create",
-           "pw_batch_destroy", "pw_batch_filter", "pw_batch_chebfi_solve", "pw_strerror", "pw_last_error")
+           "pw_batch_destroy", "pw_batch_filter", "pw_batch_chebfi_solve", "pw_ctx_set_vloc", "pw_ctx_set_D",
+           "pw_local_apply", "pw_diff_create", "pw_diff_destroy", "pw_diff_tape_bytes", "pw_diff_forward",
+           "pw_diff_backward", "pw_strerror", "pw_last_error")
 
 PROF_CLASSES = ("plane_inv", "xline", "plane_fwd", "gemm_proj", "gemm_back", "small", "rr")
 
@@ -81,6 +84,14 @@ def load(path: Optional[str] = None):
     lib.pw_batch_destroy.argtypes = [vp]
     lib.pw_batch_filter.argtypes = [vp, pvp, pi64, ci, ci, pd, pd, ci]
     lib.pw_batch_chebfi_solve.argtypes = [vp, pvp, pi64, ci, ci, ci, ci, pvp, ci, pd, pd]
+    lib.pw_ctx_set_vloc.argtypes = [vp, vp]
+    lib.pw_ctx_set_D.argtypes = [vp, vp]
+    lib.pw_local_apply.argtypes = [vp, vp, cd, vp, i64, ci, vp, i64, ci]
+    lib.pw_diff_create.argtypes = [vp, ci, ci, ci, ci, ci, pvp]
+    lib.pw_diff_destroy.argtypes = [vp]
+    lib.pw_diff_tape_bytes.argtypes = [vp, pi64]
+    lib.pw_diff_forward.argtypes = [vp, vp, i64, ci, vp, pd, pd, pd]
+    lib.pw_diff_backward.argtypes = [vp, pd, vp, i64, ci, vp, vp, ci]
     lib.pw_profile_enable.argtypes = [vp, ci]
     lib.pw_profile_read.argtypes = [vp, pd, ctypes.POINTER(ctypes.c_int64)]
     lib.pw_kernel_launches.restype = ctypes.c_uint64
@@ -170,6 +181,7 @@ class Context:
         self.npw, self.nproj = npw.value, nproj.value
         self.box = tuple(int(b) for b in box)
         self.has_q = Q is not None
+        self._dependents = weakref.WeakSet()   # handles that borrow this context
 
     @classmethod
     def from_problem(cls, prob, kpt=None, ecut=None, stream=None):
@@ -177,6 +189,8 @@ class Context:
                    prob.vloc, prob.tau, prob.sigmas, prob.D, prob.Q, stream=stream)
 
     def close(self):
+        for d in list(getattr(self, "_dependents", ())):
+            d.close()
         if getattr(self, "_h", None) is not None and self._h.value:
             load().pw_ctx_destroy(self._h)
             self._h = ctypes.c_void_p()
@@ -326,6 +340,123 @@ class Context:
         _check(load().pw_density_grad(self._h, ctypes.c_void_p(a.data_ptr()), bp, ld, m, _dptr(w),
                                       ctypes.c_void_p(out.data_ptr()), 1 if accumulate else 0))
         return out
+
+    # -- differentiation form ---------------------------------------------------------
+    def set_vloc(self, vloc):
+        """Replaces V_loc(r) (n1 x n2 x n3 float64, host array or CUDA tensor)."""
+        import torch
+        if isinstance(vloc, torch.Tensor):
+            v = vloc.detach().to(torch.float64).contiguous()
+            size, ptr = v.numel(), v.data_ptr()
+        else:
+            v = np.ascontiguousarray(np.asarray(vloc, dtype=np.float64))
+            size, ptr = v.size, v.ctypes.data
+        if size != int(np.prod(self.box)):
+            raise ValueError("vloc size does not match the box")
+        self._sync_stream()
+        _check(load().pw_ctx_set_vloc(self._h, ctypes.c_void_p(ptr)))
+
+    def set_D(self, D):
+        """Replaces D (nproj x nproj float64, host array or CUDA tensor; S = I contexts)."""
+        import torch
+        if isinstance(D, torch.Tensor):
+            Dc = D.detach().to(torch.float64).t().contiguous()   # column-major view of D
+            self._sync_stream()
+            _check(load().pw_ctx_set_D(self._h, ctypes.c_void_p(Dc.data_ptr())))
+        else:
+            Dc = np.asfortranarray(np.asarray(D, dtype=np.float64))
+            _check(load().pw_ctx_set_D(self._h, ctypes.c_void_p(Dc.ctypes.data)))
+
+    def local_apply(self, v, psi, out=None, alpha=1.0, precision=PW_FP64):
+        """out = alpha V psi for a real potential v (n1 x n2 x n3 float64 CUDA tensor)."""
+        import torch
+        dt = _dtype(precision)
+        psi, m, ld = _block(psi, dt, "psi")
+        if out is None:
+            out = torch.empty((m, self.npw), dtype=dt, device="cuda")
+        out, m2, ldo = _block(out, dt, "out")
+        if m2 < m:
+            raise ValueError("out has fewer bands than psi")
+        v = v.detach().to(torch.float64).contiguous()
+        if v.numel() != int(np.prod(self.box)) or not v.is_cuda:
+            raise ValueError("v must be a CUDA tensor with n1*n2*n3 entries")
+        self._sync_stream()
+        _check(load().pw_local_apply(self._h, ctypes.c_void_p(v.data_ptr()), float(alpha),
+                                     ctypes.c_void_p(psi.data_ptr()), ld, m, ctypes.c_void_p(out.data_ptr()), ldo,
+                                     precision))
+        return out
+
+
+class Diff:
+    """Differentiation handle (pw_diff): taped ChebFi forward and its reverse-mode adjoint."""
+
+    def __init__(self, context, nband, degree, cycles, ckpt=2, precision=PW_FP64):
+        self.context = context
+        self.nband, self.degree, self.cycles, self.precision = int(nband), int(degree), int(cycles), precision
+        h = ctypes.c_void_p()
+        _check(load().pw_diff_create(context._h, self.nband, self.degree, self.cycles, int(ckpt), precision,
+                                     ctypes.byref(h)))
+        self._h = h
+        context._dependents.add(self)
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            load().pw_diff_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def tape_bytes(self):
+        b = ctypes.c_int64(0)
+        _check(load().pw_diff_tape_bytes(self._h, ctypes.byref(b)))
+        return b.value
+
+    def forward(self, psi, v0=None, lanczos_steps=10, bounds=None):
+        """psi (complex128 CUDA block) is overwritten with the Ritz vectors; returns
+        (eigenvalues, bounds = [upper, cut of every cycle])."""
+        import torch
+        psi, m, ld = _block(psi, torch.complex128, "psi")
+        if m != self.nband:
+            raise ValueError("psi must have nband bands")
+        vp = None
+        if v0 is not None:
+            v0, _, _ = _block(v0, torch.complex128, "v0")
+            vp = ctypes.c_void_p(v0.data_ptr())
+        bin_ = None
+        if bounds is not None:
+            # [upper, a_1, ..., a_cycles] or (upper, [a_1, ..., a_cycles])
+            bin_ = np.ascontiguousarray(np.concatenate([np.atleast_1d(np.asarray(x, dtype=np.float64)).ravel()
+                                                        for x in bounds]))
+            if bin_.shape[0] != 1 + self.cycles:
+                raise ValueError("bounds needs 1 + cycles values")
+        eig = np.zeros(m)
+        bout = np.zeros(1 + self.cycles)
+        self.context._sync_stream()
+        _check(load().pw_diff_forward(self._h, ctypes.c_void_p(psi.data_ptr()), ld, int(lanczos_steps), vp,
+                                      None if bin_ is None else _dptr(bin_), _dptr(eig), _dptr(bout)))
+        return eig, bout
+
+    def backward(self, eig_bar=None, psi_bar=None, split=-1):
+        """Returns (dL/dV_loc as an n1 x n2 x n3 float64 CUDA tensor, dL/dD as nproj x nproj)."""
+        import torch
+        ctx = self.context
+        eb = None
+        if eig_bar is not None:
+            eb = np.ascontiguousarray(np.asarray(eig_bar, dtype=np.float64).reshape(-1))
+        pp, ld = None, ctx.npw
+        if psi_bar is not None:
+            psi_bar, m, ld = _block(psi_bar, torch.complex128, "psi_bar")
+            pp = ctypes.c_void_p(psi_bar.data_ptr())
+        dV = torch.empty(ctx.box, dtype=torch.float64, device="cuda")
+        dDc = torch.empty((max(ctx.nproj, 1), max(ctx.nproj, 1)), dtype=torch.float64, device="cuda")
+        ctx._sync_stream()
+        _check(load().pw_diff_backward(self._h, None if eb is None else _dptr(eb), pp, ld, int(split),
+                                       ctypes.c_void_p(dV.data_ptr()), ctypes.c_void_p(dDc.data_ptr()), 0))
+        return dV, dDc.t()[:ctx.nproj, :ctx.nproj]
 
 
 class Batch:
