@@ -900,13 +900,15 @@ __global__ void __launch_bounds__(256) k_plane_inv_f(const cplx<T>* __restrict__
     }
   }
   __syncthreads();
-  // y-lines: one column per group of TL2 threads, kYGroups columns per wave
+  // y-lines: one column per group of TL2 threads, up to kYGroups columns per wave (fewer
+  // when the block has fewer groups, e.g. 32 groups of 8 threads)
   C* dst = hb + (int64_t)b * hb_bs + (int64_t)p * N2 * N3;
   {
     const int g = threadIdx.x / TL2, t = threadIdx.x % TL2;
-    const bool in_wave = g < kYGroups;
+    const int wave = min(kYGroups, (int)blockDim.x / TL2);
+    const bool in_wave = g < wave;
     C* line = Wl + g * NP2;
-    for (int c0 = 0; c0 < N3; c0 += kYGroups) {
+    for (int c0 = 0; c0 < N3; c0 += wave) {
       const int col = c0 + g;
       const bool has = in_wave && col < N3;
       const unsigned mask = __ballot_sync(0xffffffffu, has);
@@ -975,9 +977,10 @@ __global__ void __launch_bounds__(256) k_plane_fwd_f(const cplx<T>* __restrict__
   // y-lines (forward DIT: blocks of Y2 first, read from the half-box plane)
   {
     const int g = threadIdx.x / TL2, t = threadIdx.x % TL2;
-    const bool in_wave = g < kYGroups;
+    const int wave = min(kYGroups, (int)blockDim.x / TL2);
+    const bool in_wave = g < wave;
     C* line = Wl + g * NP2;
-    for (int c0 = 0; c0 < N3; c0 += kYGroups) {
+    for (int c0 = 0; c0 < N3; c0 += wave) {
       const int col = c0 + g;
       const bool has = in_wave && col < N3;
       const unsigned mask = __ballot_sync(0xffffffffu, has);

@@ -26,6 +26,10 @@ SMALL = {
     "box_2_3_5": dict(name="differentiation", box=(20, 24, 30), ecut=3.0, natom=4, nband=9, with_q=True,
                       kpt=[0.0, 0.5, 0.25]),
     "tiny_24_aliasing": dict(name="tiny_gamma_fp64", nband=16),
+    # radix plans 8 x 8 (64) and 16 x 8 (128): line groups of 8 threads
+    "box_64_tl8": dict(name="differentiation", box=(64, 64, 64), ecut=1.5, natom=2, nband=6),
+    "box_128_x": dict(name="differentiation", box=(128, 20, 64), ecut=1.5, natom=2, nband=5,
+                      kpt=[0.25, 0.0, 0.5]),
 }
 
 
@@ -260,6 +264,47 @@ def test_full_size_fp64_at_scale_sampled_bands():
         torch.cuda.synchronize()
         ref = ham.apply_h(psi)
         assert rel(h.cpu().numpy()[:, :ctx.npw], ref).max() < 1e-11
+        t32 = to_dev(psi, torch.complex64)
+        h32 = torch.zeros_like(t32)
+        ctx.hamiltonian_apply(t32, h32, precision=pwlib.PW_MIXED)
+        torch.cuda.synchronize()
+        assert rel(h32.cpu().numpy().astype(np.complex128), ref).max() < 1e-5
+
+
+FULL_SIZE = {
+    "differentiation_64": dict(name="differentiation"),
+    "batched_kpoints_72x72x90": dict(name="batched_kpoints", kpt_index=5),
+    "paw_precision_120": dict(name="paw_precision"),
+}
+
+
+@pytest.mark.parametrize("key", list(FULL_SIZE))
+def test_full_size_other_boxes_sampled_bands(key):
+    """The full-size boxes of the other workloads (64^3: radix plan 8 x 8; 72 x 72 x 90:
+    9 x 8 and 10 x 9; 120^3: 12 x 10, with Q): 2 sampled bands of H psi (and S psi) against
+    the oracle, FP64 and mixed."""
+    kw = dict(FULL_SIZE[key])
+    prob = W.make_problem(kw.pop("name"))
+    kpt, ecut = None, None
+    if "kpt_index" in kw:
+        i = kw.pop("kpt_index")
+        kpt = W.mp_kpoints()[i]
+        ecut = W.ecut_jitter(prob.seed, len(W.mp_kpoints()), prob.ecut)[i]
+    ham = O.Hamiltonian.from_problem(prob, kpt=kpt, ecut=ecut)
+    with pwlib.Context.from_problem(prob, kpt=kpt, ecut=ecut) as ctx:
+        assert ctx.npw == ham.npw
+        psi = W.psi0(prob.seed, ctx.npw, 2)
+        t = to_dev(psi, ld=ctx.npw + 5)
+        h = torch.zeros_like(t)
+        sp = torch.zeros_like(t) if prob.Q is not None else None
+        ctx.hamiltonian_apply(t, h, sp)
+        torch.cuda.synchronize()
+        ref = ham.apply_h(psi)
+        err = rel(h.cpu().numpy()[:, :ctx.npw], ref).max()
+        print(f"{key}: H psi FP64 rel err {err:.2e}")
+        assert err < 1e-11
+        if sp is not None:
+            assert rel(sp.cpu().numpy()[:, :ctx.npw], ham.apply_s(psi)).max() < 1e-12
         t32 = to_dev(psi, torch.complex64)
         h32 = torch.zeros_like(t32)
         ctx.hamiltonian_apply(t32, h32, precision=pwlib.PW_MIXED)
