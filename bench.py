@@ -453,12 +453,96 @@ def run_batched(args):
     return 0
 
 
+# ------------------------------------------------------------------------- differentiation
+def run_diff(args):
+    """One autograd step of the differentiation workload per timed step: ChebFi forward with
+    its tape (3 cycles, degree 10, 128 bands on the 64^3 box), the occupied density, the loss
+    sum_{i<64} lambda_i + (Omega/n) sum_r (rho - rho_t)^2 and the backward to dL/dV_loc, dL/dD."""
+    import torch
+    from paper_2604_11139_gb300 import pwlib
+    from paper_2604_11139_gb300 import autograd as AG
+    torch.cuda.set_device(0)
+    prob = W.make_problem("differentiation")
+    M, m, C, nocc = prob.nband, prob.degree, prob.cycles, 64
+    ctx = pwlib.Context.from_problem(prob)
+    ctx.autotune(M, pwlib.PW_MIXED)
+    ctx.autotune(M, pwlib.PW_FP64)
+    omega = abs(float(np.linalg.det(prob.lattice)))
+    n = float(np.prod(prob.box))
+    y0 = torch.from_numpy(W.psi0(prob.seed, ctx.npw, M)).cuda()
+    v0 = torch.from_numpy(W.lanczos_v0(prob.seed, ctx.npw)[None]).cuda()
+    yn = y0[:nocc] / torch.linalg.vector_norm(y0[:nocc], dim=1, keepdim=True)
+    field = torch.from_numpy(W.smooth_field(prob.seed, prob.lattice, prob.box)).cuda()
+    rho_t = AG.density(yn, 1.0 / omega, ctx) * (1.0 + 0.05 * field)
+    handles = {p: pwlib.Diff(ctx, M, m, C, ckpt=2, precision=p) for p in (pwlib.PW_MIXED, pwlib.PW_FP64)}
+    bounds = handles[pwlib.PW_FP64].forward(y0.clone(), v0=v0)[1]
+    st = torch.cuda.current_stream()
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+
+    def step(prec):
+        V = torch.from_numpy(prob.vloc).cuda().requires_grad_(True)
+        D = torch.from_numpy(prob.D).cuda().requires_grad_(True)
+        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        e0.record(st)
+        eig, psi = AG.chebfi_rr(V, D, handles[prec], y0, bounds=bounds, split=nocc)
+        rho = AG.density(psi[:nocc], 1.0 / omega, ctx)
+        L = eig[:nocc].sum() + (omega / n) * ((rho - rho_t) ** 2).sum()
+        e1.record(st)
+        L.backward()
+        e2.record(st)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / 1e3, e1.elapsed_time(e2) / 1e3, V.grad, D.grad
+
+    applies = M * (2 * m * C + C + 1)   # filter + adjoint recurrence, one H Psi per RR, H Q of the last RR
+    res = {}
+    for prec in (pwlib.PW_FP64, pwlib.PW_MIXED):
+        steps = args.steps if prec == pwlib.PW_MIXED else max(1, args.fp64_steps)
+        for _ in range(args.warmup if prec == pwlib.PW_MIXED else 1):
+            step(prec)
+        clocks = ClockSampler(0) if prec == pwlib.PW_MIXED else None
+        if clocks:
+            clocks.start()
+        l0 = pwlib.kernel_launches()
+        tf, tb = [], []
+        for _ in range(steps):
+            flush.zero_()
+            a, b, gV, gD = step(prec)
+            tf.append(a)
+            tb.append(b)
+        res[prec] = dict(tf=statistics.mean(tf), tb=statistics.mean(tb), gV=gV, gD=gD, steps=steps,
+                         launches=pwlib.kernel_launches() - l0, clk=clocks.stop() if clocks else None)
+    mx, fp = res[pwlib.PW_MIXED], res[pwlib.PW_FP64]
+    t_mx, t_fp = mx["tf"] + mx["tb"], fp["tf"] + fp["tb"]
+    err_v = float((mx["gV"] - fp["gV"]).abs().max() / fp["gV"].abs().max())
+    err_d = float((mx["gD"] - fp["gD"]).abs().max() / fp["gD"].abs().max())
+    emit({"metric": "band·H-applies/s, ChebFi forward + adjoint (autograd step), mixed vs FP64 GPU",
+          "value": applies / t_mx, "unit": UNIT, "n_gpus": 1, "steps": mx["steps"], "warmup": args.warmup,
+          "ms_per_step": 1e3 * t_mx, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+          "dtype": "c64", "data": "synthetic",
+          "config": {"workload": f"differentiation: {prob.box[0]}^3 box, {ctx.npw} plane waves, {prob.natom} atoms / "
+                                 f"{ctx.nproj} projectors, {M} bands ({nocc} occupied), degree {m}, {C} cycles, "
+                                 "checkpoint pairs every 2 steps",
+                     "band_applies_per_step": applies, "tape_bytes": handles[pwlib.PW_MIXED].tape_bytes(),
+                     "l2": "flushed between steps (256 MB write)"},
+          "forward_ms": 1e3 * mx["tf"], "backward_ms": 1e3 * mx["tb"],
+          "fp64": {"value": applies / t_fp, "unit": UNIT, "forward_ms": 1e3 * fp["tf"], "backward_ms": 1e3 * fp["tb"],
+                   "tape_bytes": handles[pwlib.PW_FP64].tape_bytes()},
+          "grad_rel_err_vs_fp64": {"dV": err_v, "dD": err_d},
+          "gpu_launches": int(mx["launches"]), "clocks": mx["clk"]})
+    for h in handles.values():
+        h.close()
+    ctx.close()
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
     if args.workload == "batched_kpoints":
         return run_batched(args)
+    if args.workload == "differentiation":
+        return run_diff(args)
     return run_ours(args)
 
 

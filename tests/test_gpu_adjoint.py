@@ -199,3 +199,78 @@ def test_errors(case):
     cq = pwlib.Context.from_problem(pq)
     with pytest.raises(pwlib.PWError):
         pwlib.Diff(cq, 4, DEG, CYC)
+
+
+def test_full_size_differentiation_workload():
+    """The differentiation workload at full size (64^3 box, 16 atoms / 128 projectors, 128
+    bands of which 64 occupied, degree 10, 3 cycles): the FP64 adjoint against central
+    differences of the FP64 forward at 32 seeded grid points and 16 entries of the D blocks,
+    and the complex64 adjoint against the FP64 one."""
+    prob = W.make_problem("differentiation")
+    M, m, C, nocc = prob.nband, prob.degree, prob.cycles, 64
+    ctx = pwlib.Context.from_problem(prob)
+    omega = abs(float(np.linalg.det(prob.lattice)))
+    n = float(np.prod(prob.box))
+    y0 = dev(W.psi0(prob.seed, ctx.npw, M))
+    v0 = dev(W.lanczos_v0(prob.seed, ctx.npw)[None])
+    yn = y0[:nocc] / torch.linalg.vector_norm(y0[:nocc], dim=1, keepdim=True)
+    field = torch.from_numpy(W.smooth_field(prob.seed, prob.lattice, prob.box)).cuda()
+    rho_t = (AG.density(yn, 1.0 / omega, ctx) * (1.0 + 0.05 * field)).detach()
+    h64 = pwlib.Diff(ctx, M, m, C, ckpt=2, precision=pwlib.PW_FP64)
+    bounds = h64.forward(y0.clone(), v0=v0)[1]
+
+    def grads(handle):
+        V = torch.from_numpy(prob.vloc.copy()).cuda().requires_grad_(True)
+        D = torch.from_numpy(prob.D.copy()).cuda().requires_grad_(True)
+        eig, psi = AG.chebfi_rr(V, D, handle, y0, bounds=bounds, split=nocc)
+        rho = AG.density(psi[:nocc], 1.0 / omega, ctx)
+        L = eig[:nocc].sum() + (omega / n) * ((rho - rho_t) ** 2).sum()
+        L.backward()
+        return V.grad.cpu().numpy(), D.grad.cpu().numpy()
+
+    gV, gD = grads(h64)
+
+    def loss(V, D):
+        ctx.set_vloc(V)
+        ctx.set_D(D)
+        psi = y0.clone()
+        eig, _ = h64.forward(psi, bounds=bounds)
+        rho = ctx.density_grad(psi[:nocc], [1.0 / omega] * nocc)
+        return eig[:nocc].sum() + (omega / n) * float(((rho - rho_t) ** 2).sum())
+
+    # Central-difference steps: a step h in V(r_j) at one grid point moves H by only
+    # h / (n1 n2 n3) = h / 262144, so with h = 1e-5 the change of L (~1e-9) is within a few
+    # thousand roundings of L itself (measured FD error 2.8e-6 there); h_V = 1e-3 keeps the
+    # operator step (4e-9) well below D's (1e-5) while the truncation error, of order
+    # (h/n)^2, stays negligible.
+    h, hv = 1e-5, 1e-3
+    rng = np.random.default_rng(prob.seed + 23)
+    fd, ad = [], []
+    for _ in range(32):
+        p = tuple(int(rng.integers(0, prob.box[a])) for a in range(3))
+        Vp, Vm = prob.vloc.copy(), prob.vloc.copy()
+        Vp[p] += hv
+        Vm[p] -= hv
+        fd.append((loss(Vp, prob.D) - loss(Vm, prob.D)) / (2 * hv))
+        ad.append(gV[p])
+    err_v = maxrel(np.array(ad), np.array(fd))
+    fd, ad = [], []
+    blk = 4 * len(prob.sigmas)
+    for _ in range(16):
+        at = int(rng.integers(0, prob.natom))
+        a, b = (at * blk + int(x) for x in rng.integers(0, blk, 2))
+        Dp, Dm = prob.D.copy(), prob.D.copy()
+        for (i, j) in {(a, b), (b, a)}:
+            Dp[i, j] += h
+            Dm[i, j] -= h
+        fd.append((loss(prob.vloc, Dp) - loss(prob.vloc, Dm)) / (2 * h))
+        ad.append(gD[a, b] + (gD[b, a] if a != b else 0.0))
+    err_d = maxrel(np.array(ad), np.array(fd))
+    ctx.set_vloc(prob.vloc)
+    ctx.set_D(prob.D)
+    h32 = pwlib.Diff(ctx, M, m, C, ckpt=2, precision=pwlib.PW_MIXED)
+    gV32, gD32 = grads(h32)
+    e32v, e32d = maxrel(gV32, gV), maxrel(gD32, gD)
+    print(f"full size: FD dV {err_v:.2e}, FD dD {err_d:.2e}; c64 vs FP64 dV {e32v:.2e}, dD {e32d:.2e}")
+    assert err_v < 1e-6 and err_d < 1e-6
+    assert e32v < 1e-5 and e32d < 1e-5
