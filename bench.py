@@ -234,6 +234,7 @@ def run_ours(args):
     Y0_32 = Y0.to(torch.complex64)
     rqmin, a, b = ctx.spectrum_bounds(Y0, 10, v0)
     tune_ms = ctx.autotune(M, pwlib.PW_MIXED)
+    fft_cfg = ctx.fft_config(pwlib.PW_MIXED)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
     Y32 = torch.empty_like(Y0_32)
     Y64 = torch.empty_like(Y0)
@@ -369,6 +370,10 @@ def run_ours(args):
               "config": workload_config(prob, npw, nproj),
               "precision": "filter: complex64 FFTs + BF16-split tcgen05 projector GEMMs (3 pieces, FP32 accumulation); RR: FP64",
               "filter_ms": 1e3 * t_filter / args.steps, "wall_s": wall, "autotune_local_ms": tune_ms,
+              "fft_config": {"batch_bytes": fft_cfg[0],
+                             "xline_kernel": ["line groups", "one thread per line", "warp groups",
+                                              "warp groups, table twiddles"][fft_cfg[1] % 4],
+                             "plane_kernels": ["line groups", "one thread per line"][fft_cfg[1] // 4]},
               "fp64": fp64, "eig_err_vs_fp64": eig_err,
               "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": bytes_psi,
                       "d2h_bytes_per_step": bytes_psi + 8 * M,

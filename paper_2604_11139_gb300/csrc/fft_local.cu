@@ -20,6 +20,9 @@
 // so no transposition or bit-reversal pass exists.
 #include <math.h>
 
+#include <type_traits>
+#include <utility>
+
 #include "pw_internal.cuh"
 
 namespace pw {
@@ -1139,6 +1142,615 @@ static cudaError_t plane_lg(int which, const cplx<T>* psi, int64_t ldpsi, cplx<T
   return cudaErrorNotSupported;
 }
 
+// ---- one thread per line ----------------------------------------------------------
+// Each thread transforms whole lines: its line lives in shared memory as a column
+// (element e of the thread's line at buf[e * blockDim.x + threadIdx.x], or a padded plane
+// row or column), so every shared access of a warp hits 32 consecutive words and no
+// barrier separates the stages.  The butterfly index of every stage is a compile-time
+// constant, so the twiddles are immediate constants: no twiddle table is read.
+
+// exp(-2 pi i n / d) at compile time: exact reduction of n/d to an octant, then Taylor
+// series of sin and cos on [0, pi/4] (13 terms: truncation below 1e-24).
+struct CxW { double re, im; };
+__host__ __device__ constexpr double cx_sinp(double x) {
+  double t = x, s = x;
+  for (int k = 1; k <= 13; ++k) { t *= -(x * x) / ((2.0 * k) * (2.0 * k + 1.0)); s += t; }
+  return s;
+}
+__host__ __device__ constexpr double cx_cosp(double x) {
+  double t = 1.0, s = 1.0;
+  for (int k = 1; k <= 13; ++k) { t *= -(x * x) / ((2.0 * k - 1.0) * (2.0 * k)); s += t; }
+  return s;
+}
+__host__ __device__ constexpr CxW cx_w(long n, long d) {
+  n %= d;
+  if (n < 0) n += d;
+  constexpr double q = 0.78539816339744830961566084581987572;  // pi / 4
+  const long o = (8 * n) / d;                                  // octant of 2 pi n / d
+  const double phi = q * ((double)(8 * n - o * d) / (double)d);          // theta - o pi/4
+  const double psi = q * ((double)((o + 1) * d - 8 * n) / (double)d);    // (o+1) pi/4 - theta
+  double c = 0, s = 0;  // cos theta, sin theta
+  switch (o) {
+    case 0: c = cx_cosp(phi); s = cx_sinp(phi); break;
+    case 1: c = cx_sinp(psi); s = cx_cosp(psi); break;
+    case 2: c = -cx_sinp(phi); s = cx_cosp(phi); break;
+    case 3: c = -cx_cosp(psi); s = cx_sinp(psi); break;
+    case 4: c = -cx_cosp(phi); s = -cx_sinp(phi); break;
+    case 5: c = -cx_sinp(psi); s = -cx_cosp(psi); break;
+    case 6: c = cx_sinp(phi); s = -cx_cosp(phi); break;
+    default: c = cx_cosp(psi); s = -cx_sinp(psi); break;
+  }
+  return CxW{c, -s};
+}
+
+// x * exp(S 2 pi i NUM / DEN)
+template <typename C, int S, long NUM, long DEN> __device__ __forceinline__ C twmul(C x) {
+  constexpr long n = ((NUM % DEN) + DEN) % DEN;
+  if constexpr (n == 0) {
+    return x;
+  } else if constexpr ((4 * n) % DEN == 0) {
+    constexpr int k = (int)(4 * n / DEN);  // (S i)^k
+    if constexpr (k == 1) return cmuli<S>(x);
+    else if constexpr (k == 2) return mk<C>(-x.x, -x.y);
+    else return cmuli<-S>(x);
+  } else {
+    using R = decltype(C{}.x);
+    constexpr CxW w = cx_w(n, DEN);  // exp(-2 pi i n / DEN)
+    constexpr R wr = (R)w.re, wi = (R)(S < 0 ? w.im : -w.im);
+    return mk<C>(x.x * wr - x.y * wi, x.x * wi + x.y * wr);
+  }
+}
+
+template <typename F, int... I> __device__ __forceinline__ void sfor_seq(F&& f, std::integer_sequence<int, I...>) {
+  (f(std::integral_constant<int, I>{}), ...);
+}
+// f(std::integral_constant<int, i>) for i = 0 .. N-1, unrolled at compile time
+template <int N, typename F> __device__ __forceinline__ void sfor(F&& f) {
+  sfor_seq(f, std::make_integer_sequence<int, N>{});
+}
+
+// Keeps the compiler from hoisting the next butterfly's loads above this one's stores:
+// bounds the live registers of the fully unrolled stages (otherwise every load of a
+// stage is scheduled first and the kernel spills).
+__device__ __forceinline__ void sched_fence() { asm volatile("" ::: "memory"); }
+
+// x[m] *= exp(S 2 pi i J m / N) for m = 1 .. R-1
+template <typename C, int S, int N, int J, int R> __device__ __forceinline__ void tw_stage(C* x) {
+  sfor<R>([&](auto mc) {
+    constexpr int M = decltype(mc)::value;
+    x[M] = twmul<C, S, (long)J * M, N>(x[M]);
+  });
+}
+
+constexpr int kTplX = 64;  // threads (= x-lines) per CTA of the x-line pass
+
+// x-line pass, one thread per (y,z) line: inverse x (DIF, first stage reads the sphere
+// planes), times V, forward x (DIT, last stage writes the sphere planes).
+template <typename T, int N1>
+__global__ void __launch_bounds__(kTplX) k_xline_tpl(cplx<T>* __restrict__ hb, int64_t hb_bs,
+                                                     const T* __restrict__ vperm, SphereDev sp, FftPlan plan) {
+  using C = cplx<T>;
+  constexpr CPlan P = make_cplan(N1);
+  static_assert(P.nst == 2, "two-stage plan expected");
+  constexpr int R1 = P.radix[0], R2 = P.radix[1];
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* S = reinterpret_cast<C*>(smem_raw) + threadIdx.x;  // element e at S[e * kTplX]
+  const int nyz = plan.n[1] * plan.n[2];
+  const int yz = blockIdx.x * kTplX + threadIdx.x, b = blockIdx.y;
+  const bool live = yz < nyz;
+  const int h0 = sp.plane_h[0], np = sp.nplane;
+  C* hbl = hb + (int64_t)b * hb_bs + (live ? yz : 0);
+  // stage 1 of the inverse transform (radix R1, stride R2)
+  sfor<R2>([&](auto jc) {
+    constexpr int J = decltype(jc)::value;
+    C x[R1];
+#pragma unroll
+    for (int a = 0; a < R1; ++a) {
+      const int p = pmod(J + R2 * a - h0, N1);
+      x[a] = (live && p < np) ? hbl[(int64_t)p * nyz] : czero<C>();
+    }
+    dftR<C, +1, R1>(x);
+    tw_stage<C, +1, N1, J, R1>(x);
+#pragma unroll
+    for (int m = 0; m < R1; ++m) S[(J + R2 * m) * kTplX] = x[m];
+    sched_fence();
+  });
+  // stage 2 inverse (radix R2, contiguous blocks), V at the digit-reversed positions,
+  // stage 2 forward
+  const T* vb = vperm + (live ? yz : 0);
+#pragma unroll
+  for (int blk = 0; blk < R1; ++blk) {
+    C y[R2];
+#pragma unroll
+    for (int m = 0; m < R2; ++m) y[m] = S[(blk * R2 + m) * kTplX];
+    dftR<C, +1, R2>(y);
+#pragma unroll
+    for (int m = 0; m < R2; ++m) y[m] = cscale(y[m], live ? vb[(int64_t)(blk * R2 + m) * nyz] : (T)0);
+    dftR<C, -1, R2>(y);
+#pragma unroll
+    for (int m = 0; m < R2; ++m) S[(blk * R2 + m) * kTplX] = y[m];
+    sched_fence();
+  }
+  // stage 1 of the forward transform (DIT: twiddles, then radix R1): the sphere planes.
+  // h0 is passed through an opaque copy so that the plane indices of stage 1 are not kept
+  // live across stage 2 (they would take ~100 registers).
+  int h0b;
+  asm volatile("mov.b32 %0, %1;" : "=r"(h0b) : "r"(h0));
+  sfor<R2>([&](auto jc) {
+    constexpr int J = decltype(jc)::value;
+    C x[R1];
+#pragma unroll
+    for (int m = 0; m < R1; ++m) x[m] = S[(J + R2 * m) * kTplX];
+    tw_stage<C, -1, N1, J, R1>(x);
+    dftR<C, -1, R1>(x);
+#pragma unroll
+    for (int a = 0; a < R1; ++a) {
+      const int p = pmod(J + R2 * a - h0b, N1);
+      if (live && p < np) hbl[(int64_t)p * nyz] = x[a];
+    }
+    sched_fence();
+  });
+}
+
+// x-line pass with a group of TW warps per 32 lines: lane = line, warp t of the group takes
+// the butterflies (and blocks) with index = t mod TW.  The warp index is uniform, so the
+// butterfly indices, and with them the twiddles, are still compile-time constants, while
+// each thread holds only 1/TW of a line: more warps per SM than one thread per line.
+template <typename C, int S, int N1, int R1, int R2, int T0, int TW>
+__device__ __forceinline__ void xw_stage1_inv(C* L, const C* hbl, int nyz, int h0, int np, bool live) {
+  sfor<R2 / TW>([&](auto ic) {
+    constexpr int J = T0 + TW * decltype(ic)::value;
+    C x[R1];
+#pragma unroll
+    for (int a = 0; a < R1; ++a) {
+      const int p = pmod(J + R2 * a - h0, N1);
+      x[a] = (live && p < np) ? hbl[(int64_t)p * nyz] : czero<C>();
+    }
+    dftR<C, +1, R1>(x);
+    tw_stage<C, +1, N1, J, R1>(x);
+#pragma unroll
+    for (int m = 0; m < R1; ++m) L[(J + R2 * m) * 32] = x[m];
+    sched_fence();
+  });
+}
+template <typename C, int S, int N1, int R1, int R2, int T0, int TW>
+__device__ __forceinline__ void xw_stage1_fwd(const C* L, C* hbl, int nyz, int h0, int np, bool live) {
+  sfor<R2 / TW>([&](auto ic) {
+    constexpr int J = T0 + TW * decltype(ic)::value;
+    C x[R1];
+#pragma unroll
+    for (int m = 0; m < R1; ++m) x[m] = L[(J + R2 * m) * 32];
+    tw_stage<C, -1, N1, J, R1>(x);
+    dftR<C, -1, R1>(x);
+#pragma unroll
+    for (int a = 0; a < R1; ++a) {
+      const int p = pmod(J + R2 * a - h0, N1);
+      if (live && p < np) hbl[(int64_t)p * nyz] = x[a];
+    }
+    sched_fence();
+  });
+}
+
+// The same with run-time butterfly indices (one code path for all warps of the group,
+// which keeps the kernel small for the larger radices) and twiddles read from the stage
+// table with warp-uniform indices.
+template <typename C, int S, int R1, int R2>
+__device__ __forceinline__ void xw_bf_inv(C* L, const C* hbl, const C* __restrict__ tw1, int J, int nyz, int h0,
+                                          int np, int n1, bool live) {
+  C x[R1];
+#pragma unroll
+  for (int a = 0; a < R1; ++a) {
+    const int p = pmod(J + R2 * a - h0, n1);
+    x[a] = (live && p < np) ? hbl[(int64_t)p * nyz] : czero<C>();
+  }
+  dftR<C, +1, R1>(x);
+  if (J) {
+#pragma unroll
+    for (int m = 1; m < R1; ++m) x[m] = cmul(x[m], cconj(__ldg(&tw1[J * (R1 - 1) + m - 1])));
+  }
+#pragma unroll
+  for (int m = 0; m < R1; ++m) L[(J + R2 * m) * 32] = x[m];
+}
+template <typename C, int S, int R1, int R2>
+__device__ __forceinline__ void xw_bf_fwd(const C* L, C* hbl, const C* __restrict__ tw1, int J, int nyz, int h0,
+                                          int np, int n1, bool live) {
+  C x[R1];
+#pragma unroll
+  for (int m = 0; m < R1; ++m) x[m] = L[(J + R2 * m) * 32];
+  if (J) {
+#pragma unroll
+    for (int m = 1; m < R1; ++m) x[m] = cmul(x[m], __ldg(&tw1[J * (R1 - 1) + m - 1]));
+  }
+  dftR<C, -1, R1>(x);
+#pragma unroll
+  for (int a = 0; a < R1; ++a) {
+    const int p = pmod(J + R2 * a - h0, n1);
+    if (live && p < np) hbl[(int64_t)p * nyz] = x[a];
+  }
+}
+
+template <typename T, int N1, int TW>
+__global__ void __launch_bounds__(32 * TW) k_xline_twr(cplx<T>* __restrict__ hb, int64_t hb_bs,
+                                                      const T* __restrict__ vperm, SphereDev sp, FftPlan plan,
+                                                      const cplx<T>* __restrict__ tw) {
+  using C = cplx<T>;
+  constexpr CPlan P = make_cplan(N1);
+  static_assert(P.nst == 2, "two-stage plan expected");
+  constexpr int R1 = P.radix[0], R2 = P.radix[1];
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int lane = threadIdx.x & 31, t = threadIdx.x >> 5;
+  C* L = reinterpret_cast<C*>(smem_raw) + lane;
+  const int nyz = plan.n[1] * plan.n[2];
+  const int yz = blockIdx.x * 32 + lane, b = blockIdx.y;
+  const bool live = yz < nyz;
+  const int h0 = sp.plane_h[0], np = sp.nplane;
+  const C* tw1 = tw + plan.d[0].tw_off[0];
+  C* hbl = hb + (int64_t)b * hb_bs + (live ? yz : 0);
+#pragma unroll 1
+  for (int J = t; J < R2; J += TW) xw_bf_inv<C, +1, R1, R2>(L, hbl, tw1, J, nyz, h0, np, N1, live);
+  __syncthreads();
+  const T* vb = vperm + (live ? yz : 0);
+#pragma unroll 1
+  for (int blk = t; blk < R1; blk += TW) {
+    C y[R2];
+#pragma unroll
+    for (int m = 0; m < R2; ++m) y[m] = L[(blk * R2 + m) * 32];
+    dftR<C, +1, R2>(y);
+#pragma unroll
+    for (int m = 0; m < R2; ++m) y[m] = cscale(y[m], live ? vb[(int64_t)(blk * R2 + m) * nyz] : (T)0);
+    dftR<C, -1, R2>(y);
+#pragma unroll
+    for (int m = 0; m < R2; ++m) L[(blk * R2 + m) * 32] = y[m];
+  }
+  __syncthreads();
+#pragma unroll 1
+  for (int J = t; J < R2; J += TW) xw_bf_fwd<C, -1, R1, R2>(L, hbl, tw1, J, nyz, h0, np, N1, live);
+}
+
+template <typename T, int N1, int TW>
+__global__ void __launch_bounds__(32 * TW) k_xline_tw(cplx<T>* __restrict__ hb, int64_t hb_bs,
+                                                     const T* __restrict__ vperm, SphereDev sp, FftPlan plan) {
+  using C = cplx<T>;
+  constexpr CPlan P = make_cplan(N1);
+  static_assert(P.nst == 2, "two-stage plan expected");
+  constexpr int R1 = P.radix[0], R2 = P.radix[1];
+  static_assert(R1 % TW == 0 && R2 % TW == 0, "butterflies must split evenly over the warps");
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int lane = threadIdx.x & 31, t = threadIdx.x >> 5;
+  C* L = reinterpret_cast<C*>(smem_raw) + lane;  // element e of this lane's line at L[e * 32]
+  const int nyz = plan.n[1] * plan.n[2];
+  const int yz = blockIdx.x * 32 + lane, b = blockIdx.y;
+  const bool live = yz < nyz;
+  const int h0 = sp.plane_h[0], np = sp.nplane;
+  C* hbl = hb + (int64_t)b * hb_bs + (live ? yz : 0);
+  sfor<TW>([&](auto tc) {
+    if (t == decltype(tc)::value) xw_stage1_inv<C, +1, N1, R1, R2, decltype(tc)::value, TW>(L, hbl, nyz, h0, np, live);
+  });
+  __syncthreads();
+  const T* vb = vperm + (live ? yz : 0);
+#pragma unroll 1
+  for (int blk = t; blk < R1; blk += TW) {
+    C y[R2];
+#pragma unroll
+    for (int m = 0; m < R2; ++m) y[m] = L[(blk * R2 + m) * 32];
+    dftR<C, +1, R2>(y);
+#pragma unroll
+    for (int m = 0; m < R2; ++m) y[m] = cscale(y[m], live ? vb[(int64_t)(blk * R2 + m) * nyz] : (T)0);
+    dftR<C, -1, R2>(y);
+#pragma unroll
+    for (int m = 0; m < R2; ++m) L[(blk * R2 + m) * 32] = y[m];
+  }
+  __syncthreads();
+  int h0b;
+  asm volatile("mov.b32 %0, %1;" : "=r"(h0b) : "r"(h0));
+  sfor<TW>([&](auto tc) {
+    if (t == decltype(tc)::value) xw_stage1_fwd<C, -1, N1, R1, R2, decltype(tc)::value, TW>(L, hbl, nyz, h0b, np, live);
+  });
+}
+
+template <typename T, int N1, int TW>
+static cudaError_t launch_xline_tw(cplx<T>* hb, int64_t hb_bs, const T* vperm, const SphereDev& sp,
+                                   const FftPlan& plan, int nb, cudaStream_t st) {
+  const size_t sm = sizeof(cplx<T>) * (size_t)N1 * 32;
+  cudaError_t e = cudaFuncSetAttribute(k_xline_tw<T, N1, TW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e) return e;
+  if ((e = cudaFuncSetAttribute(k_xline_tw<T, N1, TW>, cudaFuncAttributePreferredSharedMemoryCarveout, 100))) return e;
+  const int nyz = plan.n[1] * plan.n[2];
+  k_xline_tw<T, N1, TW><<<dim3((nyz + 31) / 32, nb), 32 * TW, sm, st>>>(hb, hb_bs, vperm, sp, plan); count_launch();
+  return cudaGetLastError();
+}
+
+template <typename T, int N1, int TW>
+static cudaError_t launch_xline_twr(cplx<T>* hb, int64_t hb_bs, const T* vperm, const SphereDev& sp,
+                                    const FftPlan& plan, const cplx<T>* tw, int nb, cudaStream_t st) {
+  const size_t sm = sizeof(cplx<T>) * (size_t)N1 * 32;
+  cudaError_t e = cudaFuncSetAttribute(k_xline_twr<T, N1, TW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e) return e;
+  if ((e = cudaFuncSetAttribute(k_xline_twr<T, N1, TW>, cudaFuncAttributePreferredSharedMemoryCarveout, 100))) return e;
+  const int nyz = plan.n[1] * plan.n[2];
+  k_xline_twr<T, N1, TW><<<dim3((nyz + 31) / 32, nb), 32 * TW, sm, st>>>(hb, hb_bs, vperm, sp, plan, tw); count_launch();
+  return cudaGetLastError();
+}
+
+// groups of warps per 32 x-lines, run-time butterfly indices (any two-stage plan)
+template <typename T>
+static cudaError_t xline_twr(cplx<T>* hb, int64_t hb_bs, const T* vperm, const SphereDev& sp, const FftPlan& plan,
+                             const cplx<T>* tw, int nb, cudaStream_t st) {
+  switch (plan.n[0]) {
+    case 24: return launch_xline_twr<T, 24, 4>(hb, hb_bs, vperm, sp, plan, tw, nb, st);
+    case 64: return launch_xline_twr<T, 64, 4>(hb, hb_bs, vperm, sp, plan, tw, nb, st);
+    case 72: return launch_xline_twr<T, 72, 4>(hb, hb_bs, vperm, sp, plan, tw, nb, st);
+    case 90: return launch_xline_twr<T, 90, 4>(hb, hb_bs, vperm, sp, plan, tw, nb, st);
+    case 96: return launch_xline_twr<T, 96, 4>(hb, hb_bs, vperm, sp, plan, tw, nb, st);
+    case 120: return launch_xline_twr<T, 120, 4>(hb, hb_bs, vperm, sp, plan, tw, nb, st);
+    default: return cudaErrorNotSupported;
+  }
+}
+
+// groups of warps per line where the butterfly counts allow (otherwise not supported)
+template <typename T>
+static cudaError_t xline_tw(cplx<T>* hb, int64_t hb_bs, const T* vperm, const SphereDev& sp, const FftPlan& plan,
+                            int nb, cudaStream_t st) {
+  switch (plan.n[0]) {
+    case 24: return launch_xline_tw<T, 24, 2>(hb, hb_bs, vperm, sp, plan, nb, st);
+    case 64: return launch_xline_tw<T, 64, 4>(hb, hb_bs, vperm, sp, plan, nb, st);
+    case 96: return launch_xline_tw<T, 96, 4>(hb, hb_bs, vperm, sp, plan, nb, st);
+    case 120: return launch_xline_tw<T, 120, 2>(hb, hb_bs, vperm, sp, plan, nb, st);
+    default: return cudaErrorNotSupported;
+  }
+}
+
+// Plane passes, one thread per line.  The CTA holds its x-plane as F[N2][N3 + 1] (odd
+// pitch: row and column accesses of a warp are conflict-free); the z-lines of the rows
+// holding coefficients and the y-lines of all N3 columns are transformed in place.
+template <int N2, int N3> struct PlaneT {
+  static constexpr CPlan P2 = make_cplan(N2), P3 = make_cplan(N3);
+  static constexpr int FP = N3 + 1;
+  static constexpr bool ok = (P2.nst == 2 && P3.nst == 2);
+  static constexpr int THREADS = ((N3 + 31) / 32) * 32;
+};
+
+template <typename T, int N2, int N3>
+__global__ void __launch_bounds__(PlaneT<N2, N3>::THREADS) k_plane_inv_tpl(const cplx<T>* __restrict__ psi,
+                                                                            int64_t ldpsi, cplx<T>* __restrict__ hb,
+                                                                            int64_t hb_bs, SphereDev sp) {
+  using C = cplx<T>;
+  using PT = PlaneT<N2, N3>;
+  constexpr int FP = PT::FP;
+  constexpr int Y1 = PT::P2.radix[0], Y2 = PT::P2.radix[1];
+  constexpr int Z1 = PT::P3.radix[0], Z2 = PT::P3.radix[1];
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* F = reinterpret_cast<C*>(smem_raw);
+  int* ymap = reinterpret_cast<int*>(F + N2 * FP);  // y -> sphere row of the plane, or -1
+  const int p = blockIdx.x, b = blockIdx.y;
+  const int r0 = sp.plane_row0[p], nr = sp.plane_row0[p + 1] - r0;
+  const C* src = psi + (int64_t)b * ldpsi;
+  for (int i = threadIdx.x; i < N2; i += blockDim.x) ymap[i] = -1;
+  __syncthreads();
+  for (int i = threadIdx.x; i < nr; i += blockDim.x) ymap[pmod(sp.row_k[r0 + i], N2)] = i;
+  // z-lines: one thread per sphere row, in place on its plane row
+  for (int row = threadIdx.x; row < nr; row += blockDim.x) {
+    const int g0 = sp.row_g0[r0 + row], cnt = sp.row_cnt[r0 + row], l0 = sp.row_l0[r0 + row];
+    C* line = F + pmod(sp.row_k[r0 + row], N2) * FP;
+    sfor<Z2>([&](auto jc) {
+      constexpr int J = decltype(jc)::value;
+      C x[Z1];
+#pragma unroll
+      for (int a = 0; a < Z1; ++a) {
+        const int idx = pmod(J + Z2 * a - l0, N3);
+        x[a] = idx < cnt ? src[g0 + idx] : czero<C>();
+      }
+      dftR<C, +1, Z1>(x);
+      tw_stage<C, +1, N3, J, Z1>(x);
+#pragma unroll
+      for (int m = 0; m < Z1; ++m) line[J + Z2 * m] = x[m];
+      sched_fence();
+    });
+#pragma unroll
+    for (int blk = 0; blk < Z1; ++blk) {
+      C y[Z2];
+#pragma unroll
+      for (int m = 0; m < Z2; ++m) y[m] = line[blk * Z2 + m];
+      dftR<C, +1, Z2>(y);
+#pragma unroll
+      for (int m = 0; m < Z2; ++m) line[blk * Z2 + m] = y[m];
+      sched_fence();
+    }
+  }
+  __syncthreads();
+  // y-lines: one thread per column, in place; rows without coefficients read as zero
+  C* dst = hb + (int64_t)b * hb_bs + (int64_t)p * N2 * N3;
+  for (int c = threadIdx.x; c < N3; c += blockDim.x) {
+    C* col = F + c;
+    sfor<Y2>([&](auto jc) {
+      constexpr int J = decltype(jc)::value;
+      C x[Y1];
+#pragma unroll
+      for (int a = 0; a < Y1; ++a) x[a] = ymap[J + Y2 * a] >= 0 ? col[(J + Y2 * a) * FP] : czero<C>();
+      dftR<C, +1, Y1>(x);
+      tw_stage<C, +1, N2, J, Y1>(x);
+#pragma unroll
+      for (int m = 0; m < Y1; ++m) col[(J + Y2 * m) * FP] = x[m];
+      sched_fence();
+    });
+#pragma unroll
+    for (int blk = 0; blk < Y1; ++blk) {
+      C y[Y2];
+#pragma unroll
+      for (int m = 0; m < Y2; ++m) y[m] = col[(blk * Y2 + m) * FP];
+      dftR<C, +1, Y2>(y);
+#pragma unroll
+      for (int m = 0; m < Y2; ++m) dst[(int64_t)(blk * Y2 + m) * N3 + c] = y[m];
+      sched_fence();
+    }
+  }
+}
+
+template <typename T, int N2, int N3>
+__global__ void __launch_bounds__(PlaneT<N2, N3>::THREADS) k_plane_fwd_tpl(const cplx<T>* __restrict__ hb,
+                                                                            int64_t hb_bs, SphereDev sp,
+                                                                            const T* __restrict__ kin,
+                                                                            const cplx<T>* __restrict__ psi,
+                                                                            int64_t ldpsi, cplx<T>* __restrict__ out,
+                                                                            int64_t ldout) {
+  using C = cplx<T>;
+  using PT = PlaneT<N2, N3>;
+  constexpr int FP = PT::FP;
+  constexpr int Y1 = PT::P2.radix[0], Y2 = PT::P2.radix[1];
+  constexpr int Z1 = PT::P3.radix[0], Z2 = PT::P3.radix[1];
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* F = reinterpret_cast<C*>(smem_raw);
+  int* ymap = reinterpret_cast<int*>(F + N2 * FP);
+  const int p = blockIdx.x, b = blockIdx.y;
+  const int r0 = sp.plane_row0[p], nr = sp.plane_row0[p + 1] - r0;
+  const C* srcp = hb + (int64_t)b * hb_bs + (int64_t)p * N2 * N3;
+  for (int i = threadIdx.x; i < N2; i += blockDim.x) ymap[i] = -1;
+  __syncthreads();
+  for (int i = threadIdx.x; i < nr; i += blockDim.x) ymap[pmod(sp.row_k[r0 + i], N2)] = i;
+  __syncthreads();
+  // y-lines (forward DIT: radix Y2 blocks read from the half-box plane, then radix Y1
+  // with twiddles); only the rows holding coefficients are stored
+  for (int c = threadIdx.x; c < N3; c += blockDim.x) {
+    C* col = F + c;
+#pragma unroll
+    for (int blk = 0; blk < Y1; ++blk) {
+      C y[Y2];
+#pragma unroll
+      for (int m = 0; m < Y2; ++m) y[m] = srcp[(int64_t)(blk * Y2 + m) * N3 + c];
+      dftR<C, -1, Y2>(y);
+#pragma unroll
+      for (int m = 0; m < Y2; ++m) col[(blk * Y2 + m) * FP] = y[m];
+      sched_fence();
+    }
+    sfor<Y2>([&](auto jc) {
+      constexpr int J = decltype(jc)::value;
+      C x[Y1];
+#pragma unroll
+      for (int m = 0; m < Y1; ++m) x[m] = col[(J + Y2 * m) * FP];
+      tw_stage<C, -1, N2, J, Y1>(x);
+      dftR<C, -1, Y1>(x);
+#pragma unroll
+      for (int a = 0; a < Y1; ++a)
+        if (ymap[J + Y2 * a] >= 0) col[(J + Y2 * a) * FP] = x[a];
+      sched_fence();
+    });
+  }
+  __syncthreads();
+  // z-lines of the rows holding coefficients: gather with the kinetic term
+  const C* yv = psi + (int64_t)b * ldpsi;
+  C* o = out + (int64_t)b * ldout;
+  for (int row = threadIdx.x; row < nr; row += blockDim.x) {
+    const int g0 = sp.row_g0[r0 + row], cnt = sp.row_cnt[r0 + row], l0 = sp.row_l0[r0 + row];
+    C* line = F + pmod(sp.row_k[r0 + row], N2) * FP;
+#pragma unroll
+    for (int blk = 0; blk < Z1; ++blk) {
+      C y[Z2];
+#pragma unroll
+      for (int m = 0; m < Z2; ++m) y[m] = line[blk * Z2 + m];
+      dftR<C, -1, Z2>(y);
+#pragma unroll
+      for (int m = 0; m < Z2; ++m) line[blk * Z2 + m] = y[m];
+      sched_fence();
+    }
+    sfor<Z2>([&](auto jc) {
+      constexpr int J = decltype(jc)::value;
+      C x[Z1];
+#pragma unroll
+      for (int m = 0; m < Z1; ++m) x[m] = line[J + Z2 * m];
+      tw_stage<C, -1, N3, J, Z1>(x);
+      dftR<C, -1, Z1>(x);
+#pragma unroll
+      for (int a = 0; a < Z1; ++a) {
+        const int idx = pmod(J + Z2 * a - l0, N3);
+        if (idx < cnt) {
+          const int g = g0 + idx;
+          const C yy = yv[g];
+          const T k = kin[g];
+          o[g] = mk<C>(k * yy.x + x[a].x, k * yy.y + x[a].y);
+        }
+      }
+      sched_fence();
+    });
+  }
+}
+
+template <typename T, int N1>
+static cudaError_t launch_xline_tpl(cplx<T>* hb, int64_t hb_bs, const T* vperm, const SphereDev& sp,
+                                    const FftPlan& plan, int nb, cudaStream_t st) {
+  const size_t sm = sizeof(cplx<T>) * (size_t)N1 * kTplX;
+  if (sm > 227 * 1024) return cudaErrorNotSupported;
+  cudaError_t e = cudaFuncSetAttribute(k_xline_tpl<T, N1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e) return e;
+  if ((e = cudaFuncSetAttribute(k_xline_tpl<T, N1>, cudaFuncAttributePreferredSharedMemoryCarveout, 100))) return e;
+  const int nyz = plan.n[1] * plan.n[2];
+  k_xline_tpl<T, N1><<<dim3((nyz + kTplX - 1) / kTplX, nb), kTplX, sm, st>>>(hb, hb_bs, vperm, sp, plan); count_launch();
+  return cudaGetLastError();
+}
+
+template <typename T>
+static cudaError_t xline_tpl(cplx<T>* hb, int64_t hb_bs, const T* vperm, const SphereDev& sp, const FftPlan& plan,
+                             int nb, cudaStream_t st) {
+  switch (plan.n[0]) {
+    case 24: return launch_xline_tpl<T, 24>(hb, hb_bs, vperm, sp, plan, nb, st);
+    case 64: return launch_xline_tpl<T, 64>(hb, hb_bs, vperm, sp, plan, nb, st);
+    case 72: return launch_xline_tpl<T, 72>(hb, hb_bs, vperm, sp, plan, nb, st);
+    case 90: return launch_xline_tpl<T, 90>(hb, hb_bs, vperm, sp, plan, nb, st);
+    case 96: return launch_xline_tpl<T, 96>(hb, hb_bs, vperm, sp, plan, nb, st);
+    case 120: return launch_xline_tpl<T, 120>(hb, hb_bs, vperm, sp, plan, nb, st);
+    default: return cudaErrorNotSupported;
+  }
+}
+
+template <typename T, int N2, int N3>
+static size_t plane_tpl_smem() {
+  return sizeof(cplx<T>) * (size_t)N2 * PlaneT<N2, N3>::FP + sizeof(int) * N2;
+}
+
+template <typename T, int N2, int N3>
+static cudaError_t plane_tpl_pair(int which, const cplx<T>* psi, int64_t ldpsi, cplx<T>* hb, int64_t hb_bs,
+                                  const SphereDev& sp, const T* kin, cplx<T>* out, int64_t ldout, int nb,
+                                  cudaStream_t st) {
+  using PT = PlaneT<N2, N3>;
+  if constexpr (!PT::ok) {
+    return cudaErrorNotSupported;
+  } else {
+    const size_t sm = plane_tpl_smem<T, N2, N3>();
+    if (sm > 227 * 1024 || sp.max_rows > PT::THREADS * 4) return cudaErrorNotSupported;
+    cudaError_t e;
+    if (which == 0) {
+      if ((e = cudaFuncSetAttribute(k_plane_inv_tpl<T, N2, N3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm)))
+        return e;
+      if ((e = cudaFuncSetAttribute(k_plane_inv_tpl<T, N2, N3>, cudaFuncAttributePreferredSharedMemoryCarveout, 100)))
+        return e;
+      k_plane_inv_tpl<T, N2, N3><<<dim3(sp.nplane, nb), PT::THREADS, sm, st>>>(psi, ldpsi, hb, hb_bs, sp); count_launch();
+    } else {
+      if ((e = cudaFuncSetAttribute(k_plane_fwd_tpl<T, N2, N3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm)))
+        return e;
+      if ((e = cudaFuncSetAttribute(k_plane_fwd_tpl<T, N2, N3>, cudaFuncAttributePreferredSharedMemoryCarveout, 100)))
+        return e;
+      k_plane_fwd_tpl<T, N2, N3><<<dim3(sp.nplane, nb), PT::THREADS, sm, st>>>(hb, hb_bs, sp, kin, psi, ldpsi, out,
+                                                                             ldout); count_launch();
+    }
+    return cudaGetLastError();
+  }
+}
+
+template <typename T>
+static cudaError_t plane_tpl(int which, const cplx<T>* psi, int64_t ldpsi, cplx<T>* hb, int64_t hb_bs,
+                             const SphereDev& sp, const FftPlan& plan, const T* kin, cplx<T>* out, int64_t ldout,
+                             int nb, cudaStream_t st) {
+  const int n2 = plan.n[1], n3 = plan.n[2];
+#define PW_TPL_CASE(A, B) \
+  if (n2 == A && n3 == B) return plane_tpl_pair<T, A, B>(which, psi, ldpsi, hb, hb_bs, sp, kin, out, ldout, nb, st);
+  PW_TPL_CASE(24, 24)
+  PW_TPL_CASE(64, 64)
+  PW_TPL_CASE(72, 90)
+  PW_TPL_CASE(96, 96)
+  PW_TPL_CASE(120, 120)
+#undef PW_TPL_CASE
+  return cudaErrorNotSupported;
+}
+
 // ---- launchers ------------------------------------------------------------------
 cudaError_t fft_set_constants() {
   const int Rs[6] = {6, 9, 10, 12, 15, 16};
@@ -1179,10 +1791,25 @@ cudaError_t launch_local_apply(const FftPlan& plan, const cplx<T>* tw, const Sph
   if ((e = cudaFuncSetAttribute(k_xline<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm2))) return e;
   const int64_t hb_bs = (int64_t)sp.nplane * plan.n[1] * plan.n[2];
   const int nyz = plan.n[1] * plan.n[2];
+  // one-thread-per-line kernels: complex64 only (a complex128 line per thread needs twice
+  // the shared memory per CTA), when the context selected them
+  // kernel forms (complex64): x-line form = variant % 4 (0 line groups, 1 one thread per
+  // line, 2 warp groups with compile-time twiddles, 3 warp groups with table twiddles),
+  // plane form = variant / 4 (0 line groups, 1 one thread per line)
+  const int fv = (std::is_same<T, float>::value && prof) ? prof->fft_variant[0] : 0;
+  const int xf = fv % 4, pf = fv / 4;
+  const bool tpl = pf == 1;
+  const bool xtw = xf == 2, xtwr = xf == 3;
   for (int b0 = 0; b0 < nband; b0 += band_batch) {
     const int nb = min(band_batch, nband - b0);
     prof_begin(prof, PW_PROF_PLANE_INV);
-    e = plane_lg<T>(0, psi + b0 * ldpsi, ldpsi, hb, hb_bs, sp, plan, tw, kin, nullptr, 0, nb, st);
+    e = cudaErrorNotSupported;
+    if constexpr (std::is_same<T, float>::value)
+      if (tpl) e = plane_tpl<T>(0, psi + b0 * ldpsi, ldpsi, hb, hb_bs, sp, plan, kin, nullptr, 0, nb, st);
+    if (e == cudaErrorNotSupported) {
+      (void)cudaGetLastError();
+      e = plane_lg<T>(0, psi + b0 * ldpsi, ldpsi, hb, hb_bs, sp, plan, tw, kin, nullptr, 0, nb, st);
+    }
     if (e == cudaErrorNotSupported) {
       (void)cudaGetLastError();
       k_plane_inv<T><<<dim3(sp.nplane, nb), kThreads, sm1, st>>>(psi + b0 * ldpsi, ldpsi, hb, hb_bs, sp, plan, tw, cz); count_launch();
@@ -1191,7 +1818,19 @@ cudaError_t launch_local_apply(const FftPlan& plan, const cplx<T>* tw, const Sph
     }
     prof_end(prof, PW_PROF_PLANE_INV);
     prof_begin(prof, PW_PROF_XLINE);
-    e = xline_lg<T>(hb, hb_bs, vperm, sp, plan, tw, nb, st);
+    e = cudaErrorNotSupported;
+    if constexpr (std::is_same<T, float>::value) {
+      if (xtw) e = xline_tw<T>(hb, hb_bs, vperm, sp, plan, nb, st);
+      if (xtwr) e = xline_twr<T>(hb, hb_bs, vperm, sp, plan, tw, nb, st);
+      if (xf == 1) {
+        (void)cudaGetLastError();
+        e = xline_tpl<T>(hb, hb_bs, vperm, sp, plan, nb, st);
+      }
+    }
+    if (e == cudaErrorNotSupported) {
+      (void)cudaGetLastError();
+      e = xline_lg<T>(hb, hb_bs, vperm, sp, plan, tw, nb, st);
+    }
     if (e == cudaErrorNotSupported) {
       (void)cudaGetLastError();
       k_xline<T><<<dim3((nyz + lyz - 1) / lyz, nb), kThreads, sm2, st>>>(hb, hb_bs, vperm, sp, plan, tw, lyz); count_launch();
@@ -1200,7 +1839,13 @@ cudaError_t launch_local_apply(const FftPlan& plan, const cplx<T>* tw, const Sph
     }
     prof_end(prof, PW_PROF_XLINE);
     prof_begin(prof, PW_PROF_PLANE_FWD);
-    e = plane_lg<T>(1, psi + b0 * ldpsi, ldpsi, hb, hb_bs, sp, plan, tw, kin, out + b0 * ldout, ldout, nb, st);
+    e = cudaErrorNotSupported;
+    if constexpr (std::is_same<T, float>::value)
+      if (tpl) e = plane_tpl<T>(1, psi + b0 * ldpsi, ldpsi, hb, hb_bs, sp, plan, kin, out + b0 * ldout, ldout, nb, st);
+    if (e == cudaErrorNotSupported) {
+      (void)cudaGetLastError();
+      e = plane_lg<T>(1, psi + b0 * ldpsi, ldpsi, hb, hb_bs, sp, plan, tw, kin, out + b0 * ldout, ldout, nb, st);
+    }
     if (e == cudaErrorNotSupported) {
       (void)cudaGetLastError();
       k_plane_fwd<T><<<dim3(sp.nplane, nb), kThreads, sm1, st>>>(hb, hb_bs, sp, plan, tw, cz, kin,

@@ -1345,39 +1345,71 @@ PW_API int pw_autotune(pw_ctx* ctx, int nband, int precision, double* best_ms) {
   size_t max_hb = 0;
   for (size_t c : cand) max_hb = std::max(max_hb, std::min<size_t>(std::max<size_t>(c / std::max<size_t>(per, 1), 1), nband) * per);
   WS(hb, unsigned char, WS_HB, max_hb);
-  cudaEvent_t e0, e1;
-  CU_TRY(cudaEventCreate(&e0), "event");
-  CU_TRY(cudaEventCreate(&e1), "event");
+  // events and the profiling switch are restored on every exit path
+  struct Guard {
+    pw_ctx* c;
+    bool prof;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    ~Guard() {
+      if (e0) cudaEventDestroy(e0);
+      if (e1) cudaEventDestroy(e1);
+      c->prof_on = prof;
+    }
+  } g{ctx, ctx->prof_on};
+  ctx->prof_on = false;  // the launches get the context for its kernel-form field only
+  CU_TRY(cudaEventCreate(&g.e0), "event");
+  CU_TRY(cudaEventCreate(&g.e1), "event");
   double best = 1e30;
   size_t best_c = ctx->fft_batch_bytes[slot];
-  const int64_t hb_bs = (int64_t)ctx->sp.nplane * ctx->n[1] * ctx->n[2];
-  for (size_t c : cand) {
+  int best_v = ctx->fft_variant[slot];
+  auto consider = [&](size_t c, int v) -> int {
     const int bb = (int)std::max<size_t>(1, std::min<size_t>(c / std::max<size_t>(per, 1), nband));
-    if (c != cand[0] && bb * per > c && bb == 1) continue;
+    if (c != cand[0] && bb * per > c && bb == 1) return PW_OK;
+    ctx->fft_variant[slot] = v;
     float tot = 0.f;
     for (int rep = 0; rep < 4; ++rep) {
-      cudaEventRecord(e0, st);
+      CU_TRY(cudaEventRecord(g.e0, st), "autotune event");
       cudaError_t e;
       if (precision == PW_MIXED)
         e = launch_local_apply<float>(ctx->plan, ctx->tw32, ctx->sp, ctx->vperm32, ctx->kin32, (const float2*)xin,
-                                      ctx->npw, nband, (float2*)xout, ctx->npw, (float2*)hb, bb, st, nullptr);
+                                      ctx->npw, nband, (float2*)xout, ctx->npw, (float2*)hb, bb, st, ctx);
       else
         e = launch_local_apply<double>(ctx->plan, ctx->tw64, ctx->sp, ctx->vperm64, ctx->kin64, (const double2*)xin,
-                                       ctx->npw, nband, (double2*)xout, ctx->npw, (double2*)hb, bb, st, nullptr);
-      cudaEventRecord(e1, st);
-      if (e != cudaSuccess) { cudaEventDestroy(e0); cudaEventDestroy(e1); ctx->poisoned = true; return cuda_status(e, "autotune"); }
-      CU_TRY(cudaEventSynchronize(e1), "autotune sync");
+                                       ctx->npw, nband, (double2*)xout, ctx->npw, (double2*)hb, bb, st, ctx);
+      CU_TRY(e, "autotune");
+      CU_TRY(cudaEventRecord(g.e1, st), "autotune event");
+      CU_TRY(cudaEventSynchronize(g.e1), "autotune sync");
       float ms = 0.f;
-      cudaEventElapsedTime(&ms, e0, e1);
+      cudaEventElapsedTime(&ms, g.e0, g.e1);
       if (rep > 0) tot += ms;  // first repetition warms up
     }
-    (void)hb_bs;
-    if (tot / 3.0 < best) { best = tot / 3.0; best_c = c; }
-  }
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
+    if (tot / 3.0 < best) { best = tot / 3.0; best_c = c; best_v = v; }
+    return PW_OK;
+  };
+  // batch size with the current kernel forms, every kernel form at that size (complex64:
+  // x-line form + 4 * plane form, 8 combinations), the batch size again with the forms kept
+  const int nvar = precision == PW_MIXED ? 8 : 1;
+  for (size_t c : cand) PW_TRY(consider(c, best_v));
+  const size_t c1 = best_c;
+  for (int v = 0; v < nvar; ++v) PW_TRY(consider(c1, v));
+  const int v1 = best_v;
+  for (size_t c : cand) PW_TRY(consider(c, v1));
   ctx->fft_batch_bytes[slot] = best_c;
+  ctx->fft_variant[slot] = best_v;
   if (best_ms) *best_ms = best;
+  return PW_OK;
+}
+
+PW_API int pw_fft_config(pw_ctx* ctx, int precision, int64_t set_batch_bytes, int set_variant, int64_t* batch_bytes,
+                         int* variant) {
+  PW_TRY(check_ctx(ctx));
+  if (precision != PW_FP64 && precision != PW_MIXED) return set_error(PW_EINVAL, "unknown precision");
+  if (set_variant > 7) return set_error(PW_EINVAL, "unknown FFT kernel variant %d", set_variant);
+  const int slot = precision == PW_MIXED ? 0 : 1;
+  if (batch_bytes) *batch_bytes = (int64_t)ctx->fft_batch_bytes[slot];
+  if (variant) *variant = ctx->fft_variant[slot];
+  if (set_batch_bytes >= 0) ctx->fft_batch_bytes[slot] = (size_t)set_batch_bytes;
+  if (set_variant >= 0) ctx->fft_variant[slot] = set_variant;
   return PW_OK;
 }
 

@@ -91,10 +91,16 @@ def test_hamiltonian_apply_fp64(key):
         assert torch.count_nonzero(h[:, ctx.npw:]) == 0
 
 
-@pytest.mark.parametrize("key", ["cubic16_q", "ortho_k_ragged", "tiny_24_aliasing"])
-def test_hamiltonian_apply_mixed(key):
+@pytest.mark.parametrize("variant", [0, 1, 2, 3, 4, 7])
+@pytest.mark.parametrize("key", ["cubic16_q", "ortho_k_ragged", "tiny_24_aliasing", "box_64_tl8"])
+def test_hamiltonian_apply_mixed(key, variant):
+    """The complex64 FFT pass kernel forms (variant = x-line form + 4 * plane form: line
+    groups; one thread per line; warp groups for the x-lines with compile-time or table
+    twiddles), the non-zero forms used where the box lengths have two-stage radix plans
+    (the 24^3 and 64^3 cases)."""
     prob, ham, ctx = setup(key)
     with ctx:
+        ctx.fft_config(pwlib.PW_MIXED, variant=variant)
         psi = W.random_block(101, ctx.npw, prob.nband)
         t = to_dev(psi, torch.complex64)
         h = torch.zeros_like(t)
@@ -119,10 +125,12 @@ def test_filter_fp64(key):
             assert rel(t.cpu().numpy()[:, :ctx.npw], ref).max() < 1e-10, degree
 
 
-@pytest.mark.parametrize("key", ["cubic16_q", "tiny_24_aliasing"])
-def test_filter_mixed(key):
+@pytest.mark.parametrize("variant", [0, 1, 2, 3, 4, 7])
+@pytest.mark.parametrize("key", ["cubic16_q", "tiny_24_aliasing", "box_64_tl8"])
+def test_filter_mixed(key, variant):
     prob, ham, ctx = setup(key)
     with ctx:
+        ctx.fft_config(pwlib.PW_MIXED, variant=variant)
         psi = W.random_block(103, ctx.npw, prob.nband)
         a, b = 0.0, 2.0 * prob.ecut + 3.0
         t = to_dev(psi, torch.complex64)
@@ -264,11 +272,13 @@ def test_full_size_fp64_at_scale_sampled_bands():
         torch.cuda.synchronize()
         ref = ham.apply_h(psi)
         assert rel(h.cpu().numpy()[:, :ctx.npw], ref).max() < 1e-11
-        t32 = to_dev(psi, torch.complex64)
-        h32 = torch.zeros_like(t32)
-        ctx.hamiltonian_apply(t32, h32, precision=pwlib.PW_MIXED)
-        torch.cuda.synchronize()
-        assert rel(h32.cpu().numpy().astype(np.complex128), ref).max() < 1e-5
+        for variant in (0, 1, 2, 3, 4, 7):
+            ctx.fft_config(pwlib.PW_MIXED, variant=variant)
+            t32 = to_dev(psi, torch.complex64)
+            h32 = torch.zeros_like(t32)
+            ctx.hamiltonian_apply(t32, h32, precision=pwlib.PW_MIXED)
+            torch.cuda.synchronize()
+            assert rel(h32.cpu().numpy().astype(np.complex128), ref).max() < 1e-5
 
 
 FULL_SIZE = {
@@ -305,11 +315,13 @@ def test_full_size_other_boxes_sampled_bands(key):
         assert err < 1e-11
         if sp is not None:
             assert rel(sp.cpu().numpy()[:, :ctx.npw], ham.apply_s(psi)).max() < 1e-12
-        t32 = to_dev(psi, torch.complex64)
-        h32 = torch.zeros_like(t32)
-        ctx.hamiltonian_apply(t32, h32, precision=pwlib.PW_MIXED)
-        torch.cuda.synchronize()
-        assert rel(h32.cpu().numpy().astype(np.complex128), ref).max() < 1e-5
+        for variant in (0, 1, 2, 3, 4, 7):
+            ctx.fft_config(pwlib.PW_MIXED, variant=variant)
+            t32 = to_dev(psi, torch.complex64)
+            h32 = torch.zeros_like(t32)
+            ctx.hamiltonian_apply(t32, h32, precision=pwlib.PW_MIXED)
+            torch.cuda.synchronize()
+            assert rel(h32.cpu().numpy().astype(np.complex128), ref).max() < 1e-5
 
 
 def test_rayleigh_ritz_many_bands():
