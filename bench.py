@@ -373,7 +373,8 @@ def run_ours(args):
               "fft_config": {"batch_bytes": fft_cfg[0],
                              "xline_kernel": ["line groups", "one thread per line", "warp groups",
                                               "warp groups, table twiddles"][fft_cfg[1] % 4],
-                             "plane_kernels": ["line groups", "one thread per line"][fft_cfg[1] // 4]},
+                             "plane_kernels": ["line groups", "one thread per line",
+                                               "warp groups"][fft_cfg[1] // 4]},
               "fp64": fp64, "eig_err_vs_fp64": eig_err,
               "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": bytes_psi,
                       "d2h_bytes_per_step": bytes_psi + 8 * M,

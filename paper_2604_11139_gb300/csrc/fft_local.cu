@@ -1674,6 +1674,283 @@ __global__ void __launch_bounds__(PlaneT<N2, N3>::THREADS) k_plane_fwd_tpl(const
   }
 }
 
+// Plane passes with groups of TW warps per 32 lines (lane = line; the warps of a group take
+// the butterflies with index = warp mod TW; run-time indices, twiddles read from the
+// stage tables with warp-uniform indices).  The CTA holds the x-plane as F[N2][N3 + 1] and
+// has one group per 32 columns; the z-lines of the sphere rows go in chunks of 32 rows.
+template <int N2, int N3, int TW> struct PlaneW {
+  static constexpr CPlan P2 = make_cplan(N2), P3 = make_cplan(N3);
+  static constexpr int FP = N3 + 1;
+  static constexpr int NG = (N3 + 31) / 32;
+  static constexpr int THREADS = 32 * TW * NG;
+  static constexpr bool ok = (P2.nst == 2 && P3.nst == 2);
+};
+
+template <typename T, int N2, int N3, int TW>
+__global__ void __launch_bounds__(PlaneW<N2, N3, TW>::THREADS) k_plane_inv_wg(const cplx<T>* __restrict__ psi,
+                                                                               int64_t ldpsi, cplx<T>* __restrict__ hb,
+                                                                               int64_t hb_bs, SphereDev sp, FftPlan plan,
+                                                                               const cplx<T>* __restrict__ tw) {
+  using C = cplx<T>;
+  using PW = PlaneW<N2, N3, TW>;
+  constexpr int FP = PW::FP, NG = PW::NG;
+  constexpr int Y1 = PW::P2.radix[0], Y2 = PW::P2.radix[1];
+  constexpr int Z1 = PW::P3.radix[0], Z2 = PW::P3.radix[1];
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* F = reinterpret_cast<C*>(smem_raw);
+  int* ymap = reinterpret_cast<int*>(F + N2 * FP);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, g = w / TW, t = w % TW;
+  const int p = blockIdx.x, b = blockIdx.y;
+  const int r0 = sp.plane_row0[p], nr = sp.plane_row0[p + 1] - r0;
+  const C* src = psi + (int64_t)b * ldpsi;
+  const C* twy = tw + plan.d[1].tw_off[0];
+  const C* twz = tw + plan.d[2].tw_off[0];
+  for (int i = threadIdx.x; i < N2; i += blockDim.x) ymap[i] = -1;
+  __syncthreads();
+  for (int i = threadIdx.x; i < nr; i += blockDim.x) ymap[pmod(sp.row_k[r0 + i], N2)] = i;
+  // z-lines, chunks of 32 * NG rows (the chunk count is the same for every thread)
+  for (int c0 = 0; c0 < nr; c0 += 32 * NG) {
+    const int row = c0 + g * 32 + lane;
+    const bool live = row < nr;
+    int g0 = 0, cnt = 0, l0 = 0;
+    C* line = F;
+    if (live) {
+      g0 = sp.row_g0[r0 + row]; cnt = sp.row_cnt[r0 + row]; l0 = sp.row_l0[r0 + row];
+      line = F + pmod(sp.row_k[r0 + row], N2) * FP;
+    }
+    if (live) {
+#pragma unroll 1
+      for (int J = t; J < Z2; J += TW) {
+        C x[Z1];
+#pragma unroll
+        for (int a = 0; a < Z1; ++a) {
+          const int idx = pmod(J + Z2 * a - l0, N3);
+          x[a] = idx < cnt ? src[g0 + idx] : czero<C>();
+        }
+        dftR<C, +1, Z1>(x);
+        if (J) {
+#pragma unroll
+          for (int m = 1; m < Z1; ++m) x[m] = cmul(x[m], cconj(__ldg(&twz[J * (Z1 - 1) + m - 1])));
+        }
+#pragma unroll
+        for (int m = 0; m < Z1; ++m) line[J + Z2 * m] = x[m];
+      }
+    }
+    __syncthreads();
+    if (live) {
+#pragma unroll 1
+      for (int blk = t; blk < Z1; blk += TW) {
+        C y[Z2];
+#pragma unroll
+        for (int m = 0; m < Z2; ++m) y[m] = line[blk * Z2 + m];
+        dftR<C, +1, Z2>(y);
+#pragma unroll
+        for (int m = 0; m < Z2; ++m) line[blk * Z2 + m] = y[m];
+      }
+    }
+  }
+  __syncthreads();
+  // y-lines: column c = 32 g + lane; rows without coefficients read as zero
+  const int c = g * 32 + lane;
+  const bool livec = c < N3;
+  C* col = F + (livec ? c : 0);
+  if (livec) {
+#pragma unroll 1
+    for (int J = t; J < Y2; J += TW) {
+      C x[Y1];
+#pragma unroll
+      for (int a = 0; a < Y1; ++a) x[a] = ymap[J + Y2 * a] >= 0 ? col[(J + Y2 * a) * FP] : czero<C>();
+      dftR<C, +1, Y1>(x);
+      if (J) {
+#pragma unroll
+        for (int m = 1; m < Y1; ++m) x[m] = cmul(x[m], cconj(__ldg(&twy[J * (Y1 - 1) + m - 1])));
+      }
+#pragma unroll
+      for (int m = 0; m < Y1; ++m) col[(J + Y2 * m) * FP] = x[m];
+    }
+  }
+  __syncthreads();
+  C* dst = hb + (int64_t)b * hb_bs + (int64_t)p * N2 * N3;
+  if (livec) {
+#pragma unroll 1
+    for (int blk = t; blk < Y1; blk += TW) {
+      C y[Y2];
+#pragma unroll
+      for (int m = 0; m < Y2; ++m) y[m] = col[(blk * Y2 + m) * FP];
+      dftR<C, +1, Y2>(y);
+#pragma unroll
+      for (int m = 0; m < Y2; ++m) dst[(int64_t)(blk * Y2 + m) * N3 + c] = y[m];
+    }
+  }
+}
+
+template <typename T, int N2, int N3, int TW>
+__global__ void __launch_bounds__(PlaneW<N2, N3, TW>::THREADS) k_plane_fwd_wg(const cplx<T>* __restrict__ hb,
+                                                                               int64_t hb_bs, SphereDev sp, FftPlan plan,
+                                                                               const cplx<T>* __restrict__ tw,
+                                                                               const T* __restrict__ kin,
+                                                                               const cplx<T>* __restrict__ psi,
+                                                                               int64_t ldpsi, cplx<T>* __restrict__ out,
+                                                                               int64_t ldout) {
+  using C = cplx<T>;
+  using PW = PlaneW<N2, N3, TW>;
+  constexpr int FP = PW::FP, NG = PW::NG;
+  constexpr int Y1 = PW::P2.radix[0], Y2 = PW::P2.radix[1];
+  constexpr int Z1 = PW::P3.radix[0], Z2 = PW::P3.radix[1];
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* F = reinterpret_cast<C*>(smem_raw);
+  int* ymap = reinterpret_cast<int*>(F + N2 * FP);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, g = w / TW, t = w % TW;
+  const int p = blockIdx.x, b = blockIdx.y;
+  const int r0 = sp.plane_row0[p], nr = sp.plane_row0[p + 1] - r0;
+  const C* srcp = hb + (int64_t)b * hb_bs + (int64_t)p * N2 * N3;
+  const C* twy = tw + plan.d[1].tw_off[0];
+  const C* twz = tw + plan.d[2].tw_off[0];
+  for (int i = threadIdx.x; i < N2; i += blockDim.x) ymap[i] = -1;
+  __syncthreads();
+  for (int i = threadIdx.x; i < nr; i += blockDim.x) ymap[pmod(sp.row_k[r0 + i], N2)] = i;
+  // y-lines: radix Y2 blocks read from the half-box plane, then radix Y1 with twiddles;
+  // only the rows holding coefficients are stored
+  const int c = g * 32 + lane;
+  const bool livec = c < N3;
+  C* col = F + (livec ? c : 0);
+  if (livec) {
+#pragma unroll 1
+    for (int blk = t; blk < Y1; blk += TW) {
+      C y[Y2];
+#pragma unroll
+      for (int m = 0; m < Y2; ++m) y[m] = srcp[(int64_t)(blk * Y2 + m) * N3 + c];
+      dftR<C, -1, Y2>(y);
+#pragma unroll
+      for (int m = 0; m < Y2; ++m) col[(blk * Y2 + m) * FP] = y[m];
+    }
+  }
+  __syncthreads();
+  if (livec) {
+#pragma unroll 1
+    for (int J = t; J < Y2; J += TW) {
+      C x[Y1];
+#pragma unroll
+      for (int m = 0; m < Y1; ++m) x[m] = col[(J + Y2 * m) * FP];
+      if (J) {
+#pragma unroll
+        for (int m = 1; m < Y1; ++m) x[m] = cmul(x[m], __ldg(&twy[J * (Y1 - 1) + m - 1]));
+      }
+      dftR<C, -1, Y1>(x);
+#pragma unroll
+      for (int a = 0; a < Y1; ++a)
+        if (ymap[J + Y2 * a] >= 0) col[(J + Y2 * a) * FP] = x[a];
+    }
+  }
+  __syncthreads();
+  // z-lines of the rows holding coefficients, chunks of 32 * NG rows: gather with the
+  // kinetic term
+  const C* yv = psi + (int64_t)b * ldpsi;
+  C* o = out + (int64_t)b * ldout;
+  for (int c0 = 0; c0 < nr; c0 += 32 * NG) {
+    const int row = c0 + g * 32 + lane;
+    const bool live = row < nr;
+    int g0 = 0, cnt = 0, l0 = 0;
+    C* line = F;
+    if (live) {
+      g0 = sp.row_g0[r0 + row]; cnt = sp.row_cnt[r0 + row]; l0 = sp.row_l0[r0 + row];
+      line = F + pmod(sp.row_k[r0 + row], N2) * FP;
+    }
+    if (live) {
+#pragma unroll 1
+      for (int blk = t; blk < Z1; blk += TW) {
+        C y[Z2];
+#pragma unroll
+        for (int m = 0; m < Z2; ++m) y[m] = line[blk * Z2 + m];
+        dftR<C, -1, Z2>(y);
+#pragma unroll
+        for (int m = 0; m < Z2; ++m) line[blk * Z2 + m] = y[m];
+      }
+    }
+    __syncthreads();
+    if (live) {
+#pragma unroll 1
+      for (int J = t; J < Z2; J += TW) {
+        C x[Z1];
+#pragma unroll
+        for (int m = 0; m < Z1; ++m) x[m] = line[J + Z2 * m];
+        if (J) {
+#pragma unroll
+          for (int m = 1; m < Z1; ++m) x[m] = cmul(x[m], __ldg(&twz[J * (Z1 - 1) + m - 1]));
+        }
+        dftR<C, -1, Z1>(x);
+#pragma unroll
+        for (int a = 0; a < Z1; ++a) {
+          const int idx = pmod(J + Z2 * a - l0, N3);
+          if (idx < cnt) {
+            const int gg = g0 + idx;
+            const C yy = yv[gg];
+            const T k = kin[gg];
+            o[gg] = mk<C>(k * yy.x + x[a].x, k * yy.y + x[a].y);
+          }
+        }
+      }
+    }
+    __syncthreads();
+  }
+}
+
+template <typename T, int N2, int N3, int TW>
+static size_t plane_wg_smem() {
+  return sizeof(cplx<T>) * (size_t)N2 * PlaneW<N2, N3, TW>::FP + sizeof(int) * N2;
+}
+
+template <typename T, int N2, int N3, int TW>
+static cudaError_t plane_wg_pair(int which, const cplx<T>* psi, int64_t ldpsi, cplx<T>* hb, int64_t hb_bs,
+                                 const SphereDev& sp, const FftPlan& plan, const cplx<T>* tw, const T* kin,
+                                 cplx<T>* out, int64_t ldout, int nb, cudaStream_t st) {
+  using PW = PlaneW<N2, N3, TW>;
+  if constexpr (!PW::ok) {
+    return cudaErrorNotSupported;
+  } else {
+    const size_t sm = plane_wg_smem<T, N2, N3, TW>();
+    if (sm > 227 * 1024) return cudaErrorNotSupported;
+    cudaError_t e;
+    if (which == 0) {
+      if ((e = cudaFuncSetAttribute(k_plane_inv_wg<T, N2, N3, TW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)sm)))
+        return e;
+      if ((e = cudaFuncSetAttribute(k_plane_inv_wg<T, N2, N3, TW>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                    100)))
+        return e;
+      k_plane_inv_wg<T, N2, N3, TW><<<dim3(sp.nplane, nb), PW::THREADS, sm, st>>>(psi, ldpsi, hb, hb_bs, sp, plan,
+                                                                                 tw); count_launch();
+    } else {
+      if ((e = cudaFuncSetAttribute(k_plane_fwd_wg<T, N2, N3, TW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)sm)))
+        return e;
+      if ((e = cudaFuncSetAttribute(k_plane_fwd_wg<T, N2, N3, TW>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                    100)))
+        return e;
+      k_plane_fwd_wg<T, N2, N3, TW><<<dim3(sp.nplane, nb), PW::THREADS, sm, st>>>(hb, hb_bs, sp, plan, tw, kin, psi,
+                                                                                 ldpsi, out, ldout); count_launch();
+    }
+    return cudaGetLastError();
+  }
+}
+
+template <typename T>
+static cudaError_t plane_wg(int which, const cplx<T>* psi, int64_t ldpsi, cplx<T>* hb, int64_t hb_bs,
+                            const SphereDev& sp, const FftPlan& plan, const cplx<T>* tw, const T* kin, cplx<T>* out,
+                            int64_t ldout, int nb, cudaStream_t st) {
+  const int n2 = plan.n[1], n3 = plan.n[2];
+#define PW_WG_CASE(A, B, TWN)                                                                              \
+  if (n2 == A && n3 == B)                                                                                  \
+    return plane_wg_pair<T, A, B, TWN>(which, psi, ldpsi, hb, hb_bs, sp, plan, tw, kin, out, ldout, nb, st);
+  PW_WG_CASE(24, 24, 4)
+  PW_WG_CASE(64, 64, 4)
+  PW_WG_CASE(72, 90, 4)
+  PW_WG_CASE(96, 96, 4)
+  PW_WG_CASE(120, 120, 4)
+#undef PW_WG_CASE
+  return cudaErrorNotSupported;
+}
+
 template <typename T, int N1>
 static cudaError_t launch_xline_tpl(cplx<T>* hb, int64_t hb_bs, const T* vperm, const SphereDev& sp,
                                     const FftPlan& plan, int nb, cudaStream_t st) {
@@ -1795,17 +2072,19 @@ cudaError_t launch_local_apply(const FftPlan& plan, const cplx<T>* tw, const Sph
   // the shared memory per CTA), when the context selected them
   // kernel forms (complex64): x-line form = variant % 4 (0 line groups, 1 one thread per
   // line, 2 warp groups with compile-time twiddles, 3 warp groups with table twiddles),
-  // plane form = variant / 4 (0 line groups, 1 one thread per line)
+  // plane form = variant / 4 (0 line groups, 1 one thread per line, 2 warp groups)
   const int fv = (std::is_same<T, float>::value && prof) ? prof->fft_variant[0] : 0;
   const int xf = fv % 4, pf = fv / 4;
-  const bool tpl = pf == 1;
+  const bool tpl = pf == 1, pwg = pf == 2;
   const bool xtw = xf == 2, xtwr = xf == 3;
   for (int b0 = 0; b0 < nband; b0 += band_batch) {
     const int nb = min(band_batch, nband - b0);
     prof_begin(prof, PW_PROF_PLANE_INV);
     e = cudaErrorNotSupported;
-    if constexpr (std::is_same<T, float>::value)
+    if constexpr (std::is_same<T, float>::value) {
       if (tpl) e = plane_tpl<T>(0, psi + b0 * ldpsi, ldpsi, hb, hb_bs, sp, plan, kin, nullptr, 0, nb, st);
+      if (pwg) e = plane_wg<T>(0, psi + b0 * ldpsi, ldpsi, hb, hb_bs, sp, plan, tw, kin, nullptr, 0, nb, st);
+    }
     if (e == cudaErrorNotSupported) {
       (void)cudaGetLastError();
       e = plane_lg<T>(0, psi + b0 * ldpsi, ldpsi, hb, hb_bs, sp, plan, tw, kin, nullptr, 0, nb, st);
@@ -1840,8 +2119,11 @@ cudaError_t launch_local_apply(const FftPlan& plan, const cplx<T>* tw, const Sph
     prof_end(prof, PW_PROF_XLINE);
     prof_begin(prof, PW_PROF_PLANE_FWD);
     e = cudaErrorNotSupported;
-    if constexpr (std::is_same<T, float>::value)
+    if constexpr (std::is_same<T, float>::value) {
       if (tpl) e = plane_tpl<T>(1, psi + b0 * ldpsi, ldpsi, hb, hb_bs, sp, plan, kin, out + b0 * ldout, ldout, nb, st);
+      if (pwg)
+        e = plane_wg<T>(1, psi + b0 * ldpsi, ldpsi, hb, hb_bs, sp, plan, tw, kin, out + b0 * ldout, ldout, nb, st);
+    }
     if (e == cudaErrorNotSupported) {
       (void)cudaGetLastError();
       e = plane_lg<T>(1, psi + b0 * ldpsi, ldpsi, hb, hb_bs, sp, plan, tw, kin, out + b0 * ldout, ldout, nb, st);

@@ -262,7 +262,8 @@ struct pw_ctx {
   // forms: 0 line groups of 1-8 threads with shared-memory twiddles, 1 one thread per line
   // with compile-time twiddles, 2 groups of warps per 32 lines (lane = line) with
   // compile-time twiddles, 3 the same with run-time butterfly indices and table twiddles;
-  // plane forms: 0 line groups, 1 one thread per line.  Forms other than 0 cover two-stage
+  // plane forms: 0 line groups, 1 one thread per line, 2 groups of warps per 32 lines with
+  // table twiddles.  Forms other than 0 cover two-stage
   // plans in complex64 only (otherwise form 0 runs); set by pw_autotune
   int fft_variant[2] = {0, 0};
   int last_sweeps = 0;  // Jacobi sweeps of the last Rayleigh-Ritz step
