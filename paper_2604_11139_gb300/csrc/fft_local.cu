@@ -436,9 +436,11 @@ __global__ void __launch_bounds__(LineCfg<N1>::THREADS) k_xline_fused(cplx<T>* _
   const int nyz = plan.n[1] * plan.n[2];
   const int yz0 = blockIdx.x * LC::LPC, b = blockIdx.y;
   const int ln = min(LC::LPC, nyz - yz0);
-  // the sphere's x-planes are the contiguous Miller range h0 .. h0 + nplane - 1
-  const int h0 = sp.plane_h[0], np = sp.nplane;
-  auto pidx = [&](int x) { const int p = pmod(x - h0, N1); return p < np ? p : -1; };
+  // The x-line operation (inverse DFT, times V, forward DFT) is a convolution in x-frequency
+  // and so commutes with a shift of the frequencies: plane p (Miller index h0 + p) is placed
+  // at frequency p instead of h0 + p, and output p is again plane p.
+  const int np = sp.nplane;
+  auto pidx = [&](int x) { return x < np ? x : -1; };
   load_tw(twt, tw, plan.d[0]);
   __syncthreads();
   const C* tw1 = twt + (plan.d[0].tw_off[0] - plan.d[0].tw_base);
@@ -1238,7 +1240,7 @@ __global__ void __launch_bounds__(kTplX) k_xline_tpl(cplx<T>* __restrict__ hb, i
   const int nyz = plan.n[1] * plan.n[2];
   const int yz = blockIdx.x * kTplX + threadIdx.x, b = blockIdx.y;
   const bool live = yz < nyz;
-  const int h0 = sp.plane_h[0], np = sp.nplane;
+  const int np = sp.nplane;
   C* hbl = hb + (int64_t)b * hb_bs + (live ? yz : 0);
   // stage 1 of the inverse transform (radix R1, stride R2)
   sfor<R2>([&](auto jc) {
@@ -1246,7 +1248,7 @@ __global__ void __launch_bounds__(kTplX) k_xline_tpl(cplx<T>* __restrict__ hb, i
     C x[R1];
 #pragma unroll
     for (int a = 0; a < R1; ++a) {
-      const int p = pmod(J + R2 * a - h0, N1);
+      const int p = J + R2 * a;  // plane p at x-frequency p (shift invariance, see k_xline_fused)
       x[a] = (live && p < np) ? hbl[(int64_t)p * nyz] : czero<C>();
     }
     dftR<C, +1, R1>(x);
@@ -1271,11 +1273,7 @@ __global__ void __launch_bounds__(kTplX) k_xline_tpl(cplx<T>* __restrict__ hb, i
     for (int m = 0; m < R2; ++m) S[(blk * R2 + m) * kTplX] = y[m];
     sched_fence();
   }
-  // stage 1 of the forward transform (DIT: twiddles, then radix R1): the sphere planes.
-  // h0 is passed through an opaque copy so that the plane indices of stage 1 are not kept
-  // live across stage 2 (they would take ~100 registers).
-  int h0b;
-  asm volatile("mov.b32 %0, %1;" : "=r"(h0b) : "r"(h0));
+  // stage 1 of the forward transform (DIT: twiddles, then radix R1): the sphere planes
   sfor<R2>([&](auto jc) {
     constexpr int J = decltype(jc)::value;
     C x[R1];
@@ -1285,7 +1283,7 @@ __global__ void __launch_bounds__(kTplX) k_xline_tpl(cplx<T>* __restrict__ hb, i
     dftR<C, -1, R1>(x);
 #pragma unroll
     for (int a = 0; a < R1; ++a) {
-      const int p = pmod(J + R2 * a - h0b, N1);
+      const int p = J + R2 * a;
       if (live && p < np) hbl[(int64_t)p * nyz] = x[a];
     }
     sched_fence();
@@ -1303,7 +1301,7 @@ __device__ __forceinline__ void xw_stage1_inv(C* L, const C* hbl, int nyz, int h
     C x[R1];
 #pragma unroll
     for (int a = 0; a < R1; ++a) {
-      const int p = pmod(J + R2 * a - h0, N1);
+      const int p = J + R2 * a;  // plane p at x-frequency p (shift invariance, see k_xline_fused)
       x[a] = (live && p < np) ? hbl[(int64_t)p * nyz] : czero<C>();
     }
     dftR<C, +1, R1>(x);
@@ -1324,7 +1322,7 @@ __device__ __forceinline__ void xw_stage1_fwd(const C* L, C* hbl, int nyz, int h
     dftR<C, -1, R1>(x);
 #pragma unroll
     for (int a = 0; a < R1; ++a) {
-      const int p = pmod(J + R2 * a - h0, N1);
+      const int p = J + R2 * a;
       if (live && p < np) hbl[(int64_t)p * nyz] = x[a];
     }
     sched_fence();
@@ -1340,7 +1338,7 @@ __device__ __forceinline__ void xw_bf_inv(C* L, const C* hbl, const C* __restric
   C x[R1];
 #pragma unroll
   for (int a = 0; a < R1; ++a) {
-    const int p = pmod(J + R2 * a - h0, n1);
+    const int p = J + R2 * a;  // plane p at x-frequency p (shift invariance, see k_xline_fused)
     x[a] = (live && p < np) ? hbl[(int64_t)p * nyz] : czero<C>();
   }
   dftR<C, +1, R1>(x);
@@ -1364,13 +1362,13 @@ __device__ __forceinline__ void xw_bf_fwd(const C* L, C* hbl, const C* __restric
   dftR<C, -1, R1>(x);
 #pragma unroll
   for (int a = 0; a < R1; ++a) {
-    const int p = pmod(J + R2 * a - h0, n1);
+    const int p = J + R2 * a;
     if (live && p < np) hbl[(int64_t)p * nyz] = x[a];
   }
 }
 
 template <typename T, int N1, int TW>
-__global__ void __launch_bounds__(32 * TW) k_xline_twr(cplx<T>* __restrict__ hb, int64_t hb_bs,
+__global__ void __launch_bounds__(32 * TW, 32 / TW) k_xline_twr(cplx<T>* __restrict__ hb, int64_t hb_bs,
                                                       const T* __restrict__ vperm, SphereDev sp, FftPlan plan,
                                                       const cplx<T>* __restrict__ tw) {
   using C = cplx<T>;
@@ -1441,10 +1439,8 @@ __global__ void __launch_bounds__(32 * TW) k_xline_tw(cplx<T>* __restrict__ hb, 
     for (int m = 0; m < R2; ++m) L[(blk * R2 + m) * 32] = y[m];
   }
   __syncthreads();
-  int h0b;
-  asm volatile("mov.b32 %0, %1;" : "=r"(h0b) : "r"(h0));
   sfor<TW>([&](auto tc) {
-    if (t == decltype(tc)::value) xw_stage1_fwd<C, -1, N1, R1, R2, decltype(tc)::value, TW>(L, hbl, nyz, h0b, np, live);
+    if (t == decltype(tc)::value) xw_stage1_fwd<C, -1, N1, R1, R2, decltype(tc)::value, TW>(L, hbl, nyz, h0, np, live);
   });
 }
 
