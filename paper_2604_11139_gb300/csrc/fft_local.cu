@@ -18,6 +18,7 @@
 // (digit-reversed in, natural out); between them the data stays in the
 // digit-reversed (y,z) order and the potential grid is stored permuted to it,
 // so no transposition or bit-reversal pass exists.
+#include <cuda_bf16.h>
 #include <math.h>
 
 #include <type_traits>
@@ -1704,7 +1705,8 @@ __global__ void __launch_bounds__(PlaneW<N2, N3, TW>::THREADS) k_plane_inv_wg(co
   for (int i = threadIdx.x; i < N2; i += blockDim.x) ymap[i] = -1;
   __syncthreads();
   for (int i = threadIdx.x; i < nr; i += blockDim.x) ymap[pmod(sp.row_k[r0 + i], N2)] = i;
-  // z-lines, chunks of 32 * NG rows (the chunk count is the same for every thread)
+  // z-lines, chunks of 32 * NG rows (the chunk count is the same for every thread); the
+  // first stage reads the row's run of coefficients straight from the block
   for (int c0 = 0; c0 < nr; c0 += 32 * NG) {
     const int row = c0 + g * 32 + lane;
     const bool live = row < nr;
@@ -1780,14 +1782,14 @@ __global__ void __launch_bounds__(PlaneW<N2, N3, TW>::THREADS) k_plane_inv_wg(co
   }
 }
 
-template <typename T, int N2, int N3, int TW>
+template <typename T, int N2, int N3, int TW, bool REC>
 __global__ void __launch_bounds__(PlaneW<N2, N3, TW>::THREADS) k_plane_fwd_wg(const cplx<T>* __restrict__ hb,
                                                                                int64_t hb_bs, SphereDev sp, FftPlan plan,
                                                                                const cplx<T>* __restrict__ tw,
                                                                                const T* __restrict__ kin,
                                                                                const cplx<T>* __restrict__ psi,
                                                                                int64_t ldpsi, cplx<T>* __restrict__ out,
-                                                                               int64_t ldout) {
+                                                                               int64_t ldout, Pass3Rec rec) {
   using C = cplx<T>;
   using PW = PlaneW<N2, N3, TW>;
   constexpr int FP = PW::FP, NG = PW::NG;
@@ -1843,15 +1845,19 @@ __global__ void __launch_bounds__(PlaneW<N2, N3, TW>::THREADS) k_plane_fwd_wg(co
   // kinetic term
   const C* yv = psi + (int64_t)b * ldpsi;
   C* o = out + (int64_t)b * ldout;
+  T ra = 0, rs = 0;  // recurrence alpha and shift
+  if constexpr (REC) {
+    ra = (T)rec.alpha;
+    rs = (T)rec.shift;
+    if (rec.dev_ce) {
+      rs = (T)rec.dev_ce[0];
+      ra = (T)((rec.first ? 1.0 : 2.0) / rec.dev_ce[1]);
+    }
+  }
   for (int c0 = 0; c0 < nr; c0 += 32 * NG) {
     const int row = c0 + g * 32 + lane;
     const bool live = row < nr;
-    int g0 = 0, cnt = 0, l0 = 0;
-    C* line = F;
-    if (live) {
-      g0 = sp.row_g0[r0 + row]; cnt = sp.row_cnt[r0 + row]; l0 = sp.row_l0[r0 + row];
-      line = F + pmod(sp.row_k[r0 + row], N2) * FP;
-    }
+    C* line = live ? F + pmod(sp.row_k[r0 + row], N2) * FP : F;
     if (live) {
 #pragma unroll 1
       for (int blk = t; blk < Z1; blk += TW) {
@@ -1876,18 +1882,47 @@ __global__ void __launch_bounds__(PlaneW<N2, N3, TW>::THREADS) k_plane_fwd_wg(co
         }
         dftR<C, -1, Z1>(x);
 #pragma unroll
-        for (int a = 0; a < Z1; ++a) {
-          const int idx = pmod(J + Z2 * a - l0, N3);
-          if (idx < cnt) {
-            const int gg = g0 + idx;
-            const C yy = yv[gg];
-            const T k = kin[gg];
-            o[gg] = mk<C>(k * yy.x + x[a].x, k * yy.y + x[a].y);
+        for (int a = 0; a < Z1; ++a) line[J + Z2 * a] = x[a];
+      }
+    }
+    __syncthreads();
+  }
+  // gather the plane's coefficients, one warp per row (coalesced reads and writes), with the
+  // kinetic term (and the recurrence)
+  for (int row = w; row < nr; row += blockDim.x >> 5) {
+    const int g0 = sp.row_g0[r0 + row], cnt = sp.row_cnt[r0 + row], l0 = sp.row_l0[r0 + row];
+    const C* line = F + pmod(sp.row_k[r0 + row], N2) * FP;
+    for (int idx = lane; idx < cnt; idx += 32) {
+      const C v = line[pmod(l0 + idx, N3)];
+      const int gg = g0 + idx;
+      const C yy = yv[gg];
+      const T k = kin[gg];
+      if constexpr (!REC) {
+        o[gg] = mk<C>(k * yy.x + v.x, k * yy.y + v.y);
+      } else {
+        const C pz = ((const C*)rec.pz)[(int64_t)b * rec.ldpz + gg];
+        C r = mk<C>(ra * (k * yy.x + v.x + pz.x - rs * yy.x), ra * (k * yy.y + v.y + pz.y - rs * yy.y));
+        if (rec.ykm1) {
+          const C ym = ((const C*)rec.ykm1)[(int64_t)b * rec.ldykm1 + gg];
+          r.x -= (T)rec.beta * ym.x;
+          r.y -= (T)rec.beta * ym.y;
+        }
+        o[gg] = r;
+        if (rec.split) {
+          __nv_bfloat16* sb = (__nv_bfloat16*)rec.split + (int64_t)b * rec.split_ld + 2 * (int64_t)gg;
+          float re = (float)r.x, im = (float)r.y;
+          for (int pc = 0; pc < rec.pieces; ++pc) {
+            const __nv_bfloat16 hr = __float2bfloat16_rn(re), hi = __float2bfloat16_rn(im);
+            __nv_bfloat162 two;
+            two.x = hr;
+            two.y = hi;
+            *reinterpret_cast<__nv_bfloat162*>(sb + (int64_t)pc * rec.split_piece_stride) = two;
+            re -= __bfloat162float(hr);
+            im -= __bfloat162float(hi);
           }
         }
       }
     }
-    __syncthreads();
   }
 }
 
@@ -1899,7 +1934,7 @@ static size_t plane_wg_smem() {
 template <typename T, int N2, int N3, int TW>
 static cudaError_t plane_wg_pair(int which, const cplx<T>* psi, int64_t ldpsi, cplx<T>* hb, int64_t hb_bs,
                                  const SphereDev& sp, const FftPlan& plan, const cplx<T>* tw, const T* kin,
-                                 cplx<T>* out, int64_t ldout, int nb, cudaStream_t st) {
+                                 cplx<T>* out, int64_t ldout, int nb, cudaStream_t st, const Pass3Rec* rec) {
   using PW = PlaneW<N2, N3, TW>;
   if constexpr (!PW::ok) {
     return cudaErrorNotSupported;
@@ -1917,14 +1952,29 @@ static cudaError_t plane_wg_pair(int which, const cplx<T>* psi, int64_t ldpsi, c
       k_plane_inv_wg<T, N2, N3, TW><<<dim3(sp.nplane, nb), PW::THREADS, sm, st>>>(psi, ldpsi, hb, hb_bs, sp, plan,
                                                                                  tw); count_launch();
     } else {
-      if ((e = cudaFuncSetAttribute(k_plane_fwd_wg<T, N2, N3, TW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)sm)))
-        return e;
-      if ((e = cudaFuncSetAttribute(k_plane_fwd_wg<T, N2, N3, TW>, cudaFuncAttributePreferredSharedMemoryCarveout,
-                                    100)))
-        return e;
-      k_plane_fwd_wg<T, N2, N3, TW><<<dim3(sp.nplane, nb), PW::THREADS, sm, st>>>(hb, hb_bs, sp, plan, tw, kin, psi,
-                                                                                 ldpsi, out, ldout); count_launch();
+      if (rec) {
+        if constexpr (std::is_same<T, float>::value) {
+          if ((e = cudaFuncSetAttribute(k_plane_fwd_wg<T, N2, N3, TW, true>,
+                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm)))
+            return e;
+          if ((e = cudaFuncSetAttribute(k_plane_fwd_wg<T, N2, N3, TW, true>,
+                                        cudaFuncAttributePreferredSharedMemoryCarveout, 100)))
+            return e;
+          k_plane_fwd_wg<T, N2, N3, TW, true><<<dim3(sp.nplane, nb), PW::THREADS, sm, st>>>(
+              hb, hb_bs, sp, plan, tw, kin, psi, ldpsi, out, ldout, *rec); count_launch();
+        } else {
+          return cudaErrorNotSupported;
+        }
+      } else {
+        if ((e = cudaFuncSetAttribute(k_plane_fwd_wg<T, N2, N3, TW, false>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm)))
+          return e;
+        if ((e = cudaFuncSetAttribute(k_plane_fwd_wg<T, N2, N3, TW, false>,
+                                      cudaFuncAttributePreferredSharedMemoryCarveout, 100)))
+          return e;
+        k_plane_fwd_wg<T, N2, N3, TW, false><<<dim3(sp.nplane, nb), PW::THREADS, sm, st>>>(
+            hb, hb_bs, sp, plan, tw, kin, psi, ldpsi, out, ldout, Pass3Rec{}); count_launch();
+      }
     }
     return cudaGetLastError();
   }
@@ -1933,11 +1983,11 @@ static cudaError_t plane_wg_pair(int which, const cplx<T>* psi, int64_t ldpsi, c
 template <typename T>
 static cudaError_t plane_wg(int which, const cplx<T>* psi, int64_t ldpsi, cplx<T>* hb, int64_t hb_bs,
                             const SphereDev& sp, const FftPlan& plan, const cplx<T>* tw, const T* kin, cplx<T>* out,
-                            int64_t ldout, int nb, cudaStream_t st) {
+                            int64_t ldout, int nb, cudaStream_t st, const Pass3Rec* rec = nullptr) {
   const int n2 = plan.n[1], n3 = plan.n[2];
-#define PW_WG_CASE(A, B, TWN)                                                                              \
-  if (n2 == A && n3 == B)                                                                                  \
-    return plane_wg_pair<T, A, B, TWN>(which, psi, ldpsi, hb, hb_bs, sp, plan, tw, kin, out, ldout, nb, st);
+#define PW_WG_CASE(A, B, TWN)                                                                                  \
+  if (n2 == A && n3 == B)                                                                                      \
+    return plane_wg_pair<T, A, B, TWN>(which, psi, ldpsi, hb, hb_bs, sp, plan, tw, kin, out, ldout, nb, st, rec);
   PW_WG_CASE(24, 24, 4)
   PW_WG_CASE(64, 64, 4)
   PW_WG_CASE(72, 90, 4)
@@ -1945,6 +1995,12 @@ static cudaError_t plane_wg(int which, const cplx<T>* psi, int64_t ldpsi, cplx<T
   PW_WG_CASE(120, 120, 4)
 #undef PW_WG_CASE
   return cudaErrorNotSupported;
+}
+
+static bool plane_wg_covers(const FftPlan& plan) {
+  const int n2 = plan.n[1], n3 = plan.n[2];
+  return (n2 == 24 && n3 == 24) || (n2 == 64 && n3 == 64) || (n2 == 72 && n3 == 90) || (n2 == 96 && n3 == 96) ||
+         (n2 == 120 && n3 == 120);
 }
 
 template <typename T, int N1>
@@ -2131,6 +2187,58 @@ cudaError_t launch_local_apply(const FftPlan& plan, const cplx<T>* tw, const Sph
     } else if (e != cudaSuccess) {
       return e;
     }
+    prof_end(prof, PW_PROF_PLANE_FWD);
+  }
+  return cudaGetLastError();
+}
+
+bool local_apply_rec_supported(const FftPlan& plan, const ::pw_ctx* prof) {
+  return prof && prof->fft_variant[0] / 4 == 2 && plane_wg_covers(plan);
+}
+
+cudaError_t launch_local_apply_rec(const FftPlan& plan, const float2* tw, const SphereDev& sp, const float* vperm,
+                                   const float* kin, const float2* psi, int64_t ldpsi, int nband, float2* out,
+                                   int64_t ldout, float2* hb, int band_batch, cudaStream_t st, ::pw_ctx* prof,
+                                   const Pass3Rec& rec) {
+  using T = float;
+  if (!local_apply_rec_supported(plan, prof)) return cudaErrorNotSupported;
+  if (nband <= 0) return cudaSuccess;
+  const int xf = prof->fft_variant[0] % 4;
+  const int64_t hb_bs = (int64_t)sp.nplane * plan.n[1] * plan.n[2];
+  const int nyz = plan.n[1] * plan.n[2];
+  const int lyz = 32;
+  const size_t sm2 = sizeof(cplx<T>) * (size_t)plan.n[0] * lyz;
+  cudaError_t e;
+  for (int b0 = 0; b0 < nband; b0 += band_batch) {
+    const int nb = min(band_batch, nband - b0);
+    prof_begin(prof, PW_PROF_PLANE_INV);
+    if ((e = plane_wg<T>(0, psi + b0 * ldpsi, ldpsi, hb, hb_bs, sp, plan, tw, kin, nullptr, 0, nb, st))) return e;
+    prof_end(prof, PW_PROF_PLANE_INV);
+    prof_begin(prof, PW_PROF_XLINE);
+    e = cudaErrorNotSupported;
+    if (xf == 2) e = xline_tw<T>(hb, hb_bs, vperm, sp, plan, nb, st);
+    if (xf == 3) e = xline_twr<T>(hb, hb_bs, vperm, sp, plan, tw, nb, st);
+    if (xf == 1) e = xline_tpl<T>(hb, hb_bs, vperm, sp, plan, nb, st);
+    if (e == cudaErrorNotSupported) {
+      (void)cudaGetLastError();
+      e = xline_lg<T>(hb, hb_bs, vperm, sp, plan, tw, nb, st);
+    }
+    if (e == cudaErrorNotSupported) {
+      (void)cudaGetLastError();
+      if ((e = cudaFuncSetAttribute(k_xline<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm2))) return e;
+      k_xline<T><<<dim3((nyz + lyz - 1) / lyz, nb), kThreads, sm2, st>>>(hb, hb_bs, vperm, sp, plan, tw, lyz); count_launch();
+      e = cudaGetLastError();
+    }
+    if (e) return e;
+    prof_end(prof, PW_PROF_XLINE);
+    prof_begin(prof, PW_PROF_PLANE_FWD);
+    Pass3Rec r = rec;
+    r.pz = rec.pz + b0 * rec.ldpz;
+    if (rec.ykm1) r.ykm1 = rec.ykm1 + b0 * rec.ldykm1;
+    if (rec.split) r.split = (__nv_bfloat16*)rec.split + b0 * rec.split_ld;
+    if ((e = plane_wg<T>(1, psi + b0 * ldpsi, ldpsi, hb, hb_bs, sp, plan, tw, kin, out + b0 * ldout, ldout, nb, st,
+                         &r)))
+      return e;
     prof_end(prof, PW_PROF_PLANE_FWD);
   }
   return cudaGetLastError();

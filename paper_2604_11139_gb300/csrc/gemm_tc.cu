@@ -349,6 +349,11 @@ __global__ void __launch_bounds__(192, 1) k_tc_gemm(const __grid_constant__ CUte
 #pragma unroll
           for (int i = 0; i < 32; ++i)
             if (jc + i < N) o[(int64_t)i * epi.part_ld] = acc[i];
+        } else if (epi.mode == TC_EPI_STORE) {
+          float* __restrict__ o = epi.out + (int64_t)jc * epi.ldo + r;
+#pragma unroll
+          for (int i = 0; i < 32; ++i)
+            if (jc + i < N) o[(int64_t)i * epi.ldo] = epi.alpha * acc[i];
         } else if (epi.mode == TC_EPI_ACCUM) {
           float* __restrict__ o = epi.out + (int64_t)jc * epi.ldo + r;
           float wv[32];

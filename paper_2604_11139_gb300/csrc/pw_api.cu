@@ -436,6 +436,61 @@ int filter_impl(pw_ctx* ctx, cplx<T>* psi, int64_t ldpsi, int nband, int degree,
     ProfScope ps(ctx, PW_PROF_GEMM_PROJ);
     PW_TRY(tc_split(ctx, (const float2*)psi, ldpsi, npw, nband, ctx->kp1, WS_YSPLIT, &ys));
   }
+  // complex64 with S = I and the warp-group plane kernels: the nonlocal term first
+  // (projection, D, back-projection into PZ), then the FFT passes with the recurrence and
+  // the bf16 split of Y_{k+1} fused into pass 3 (fewer block reads than the recurrence in
+  // the back-projection epilogue)
+  if constexpr (kMixed) {
+    if (np > 0 && !ctx->has_q && local_apply_rec_supported(ctx->plan, ctx)) {
+      WS(PZ, C, WS_PZ, (size_t)npw * nband);
+      for (int k = 0; k < degree; ++k) {
+        C* cur = buf[k % 3];
+        C* prev = buf[(k + 2) % 3];
+        C* dst = buf[(k + 1) % 3];
+        const int64_t ldc = ld[k % 3], ldp = ld[(k + 2) % 3], ldd = ld[(k + 1) % 3];
+        {
+          ProfScope ps(ctx, PW_PROF_GEMM_PROJ);
+          PW_TRY(tc_project(ctx, ys, nband, (float2*)Cm));
+        }
+        __nv_bfloat16* zs;
+        {
+          ProfScope ps(ctx, PW_PROF_SMALL);
+          CU_TRY(launch_dblock<T>(np, nband, Prec<T>::D(ctx), ctx->blk0, ctx->blklen, Cm, np, Z, np, st), "filter D");
+          PW_TRY(tc_split(ctx, (const float2*)Z, np, np, nband, ctx->kp2, WS_ZSPLIT, &zs));
+        }
+        {
+          ProfScope ps(ctx, PW_PROF_GEMM_BACK);
+          tc::TcEpi te{};
+          te.mode = tc::TC_EPI_STORE;
+          te.out = (float*)PZ;
+          te.ldo = 2 * (int64_t)npw;
+          te.alpha = 1.f;
+          PW_TRY(tc_backproject(ctx, zs, nband, te));
+        }
+        Pass3Rec rec{};
+        rec.pz = (const float2*)PZ;
+        rec.ldpz = npw;
+        rec.ykm1 = (k == 0) ? nullptr : (const float2*)prev;
+        rec.ldykm1 = ldp;
+        rec.alpha = (float)(k == 0 ? 1.0 / e : 2.0 / e);
+        rec.beta = 1.f;
+        rec.shift = (float)cc;
+        rec.dev_ce = dev_ce;
+        rec.first = (k == 0);
+        rec.split = (k + 1 < degree) ? (void*)ys : nullptr;
+        rec.split_ld = ctx->kp1;
+        rec.split_piece_stride = (int64_t)nband * ctx->kp1;
+        rec.pieces = ctx->tc_pieces;
+        CU_TRY(launch_local_apply_rec(ctx->plan, ctx->tw32, ctx->sp, ctx->vperm32, ctx->kin32, (const float2*)cur, ldc,
+                                      nband, (float2*)dst, ldd, (float2*)hb, bb, st, ctx, rec), "filter local + recurrence");
+      }
+      if (degree % 3 != 0) {
+        CU_TRY(cudaMemcpy2DAsync(psi, sizeof(C) * ldpsi, buf[degree % 3], sizeof(C) * npw, sizeof(C) * npw, nband,
+                                 cudaMemcpyDeviceToDevice, st), "filter copy-out");
+      }
+      return PW_OK;
+    }
+  }
   for (int k = 0; k < degree; ++k) {
     C* cur = buf[k % 3];
     C* prev = buf[(k + 2) % 3];

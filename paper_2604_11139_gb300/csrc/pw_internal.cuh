@@ -177,6 +177,33 @@ cudaError_t launch_local_apply(const FftPlan& plan, const cplx<T>* tw, const Sph
                                int nband, cplx<T>* out, int64_t ldout, cplx<T>* hb, int band_batch,
                                cudaStream_t st, ::pw_ctx* prof);
 
+// Recurrence step fused into FFT pass 3 (complex64, S = I):
+//   y_{k+1} = alpha (kin y_k + (V y_k) + pz - shift y_k) - beta y_{k-1}
+// pz = P D P^dagger y_k from the back-projection GEMM (ld ldpz); ykm1 may be NULL; with
+// dev_ce, shift = c and alpha = (first ? 1 : 2) / e are read from the device.  split (may be
+// NULL) receives the bf16 pieces of y_{k+1}: piece p of band b, real row r (2g: Re, 2g+1: Im)
+// at split[p * split_piece_stride + b * split_ld + r].
+struct Pass3Rec {
+  const float2* pz;
+  int64_t ldpz;
+  const float2* ykm1;
+  int64_t ldykm1;
+  float alpha, beta, shift;
+  const double* dev_ce;
+  int first;
+  void* split;  // __nv_bfloat16*
+  int64_t split_ld, split_piece_stride;
+  int pieces;
+};
+// H-apply local part with the fused recurrence of Pass3Rec (out = y_{k+1}); requires the
+// warp-group plane kernels for this box (plane form 2 of the context's complex64 variant),
+// else returns cudaErrorNotSupported before launching anything.
+cudaError_t launch_local_apply_rec(const FftPlan& plan, const float2* tw, const SphereDev& sp, const float* vperm,
+                                   const float* kin, const float2* psi, int64_t ldpsi, int nband, float2* out,
+                                   int64_t ldout, float2* hb, int band_batch, cudaStream_t st, ::pw_ctx* prof,
+                                   const Pass3Rec& rec);
+bool local_apply_rec_supported(const FftPlan& plan, const ::pw_ctx* prof);
+
 // fills the constant twiddles of the composite in-register radices on the current device
 cudaError_t fft_set_constants();
 
@@ -275,7 +302,7 @@ enum WsSlot {
   WS_YSPLIT, WS_WSPLIT, WS_ZSPLIT, WS_TCPART, WS_TCERR,      // tensor-core mixed path
   WS_HY, WS_SY, WS_ROT, WS_Y32,                              // Rayleigh-Ritz / solve
   WS_GRAM, WS_GRAM2, WS_LINV, WS_TMP, WS_U, WS_JAC, WS_EIG,  // subspace matrices
-  WS_LZ, WS_RQ, WS_DEN, WS_SCAL, WS_VPOT, WS_NUM
+  WS_LZ, WS_RQ, WS_DEN, WS_SCAL, WS_VPOT, WS_PZ, WS_NUM
 };
 void* ws_get(pw_ctx* c, int slot, size_t bytes, int* status);
 // process-wide count of kernel launches issued by this library (diagnostics)

@@ -7,7 +7,7 @@
 namespace pw {
 namespace tc {
 
-enum TcEpiMode { TC_EPI_PARTIAL = 0, TC_EPI_ACCUM = 1, TC_EPI_CHEB = 2 };
+enum TcEpiMode { TC_EPI_PARTIAL = 0, TC_EPI_ACCUM = 1, TC_EPI_CHEB = 2, TC_EPI_STORE = 3 };
 
 // Output element (row r, column j) of the real view lives at base[j * ld + r].
 struct TcEpi {
@@ -15,7 +15,8 @@ struct TcEpi {
   // TC_EPI_PARTIAL: part[z * part_split_stride + j * part_ld + r] = acc (split z = blockIdx.z)
   float* part;
   int64_t part_ld, part_split_stride;
-  // TC_EPI_ACCUM: out += alpha acc ; TC_EPI_CHEB: out = alpha (out + acc - shift yk) - beta ykm1
+  // TC_EPI_ACCUM: out += alpha acc ; TC_EPI_STORE: out = alpha acc ;
+  // TC_EPI_CHEB: out = alpha (out + acc - shift yk) - beta ykm1
   float* out;
   int64_t ldo;
   const float* yk;

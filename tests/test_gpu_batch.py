@@ -17,19 +17,26 @@ from paper_2604_11139_gb300 import pwlib  # noqa: E402
 KPTS = np.array([[0.125, 0.125, 0.25], [0.375, -0.125, 0.25], [-0.375, 0.375, -0.25]])
 
 
-def problem():
-    return W.make_problem("batched_kpoints", box=(24, 24, 30), ecut=3.0, natom=3, nband=6)
+def problem(box=(24, 24, 30)):
+    return W.make_problem("batched_kpoints", box=box, ecut=3.0, natom=3, nband=6)
 
 
-def contexts(prob, ecuts):
-    return [pwlib.Context.from_problem(prob, kpt=k, ecut=e) for k, e in zip(KPTS, ecuts)]
+def contexts(prob, ecuts, variant=None):
+    ctxs = [pwlib.Context.from_problem(prob, kpt=k, ecut=e) for k, e in zip(KPTS, ecuts)]
+    if variant is not None:
+        for c in ctxs:
+            c.fft_config(pwlib.PW_MIXED, variant=variant)
+    return ctxs
 
 
-@pytest.mark.parametrize("precision", [pwlib.PW_FP64, pwlib.PW_MIXED])
-def test_batch_filter_equals_per_k_filter(precision):
-    prob = problem()
+# variant 11 on a 24^3 box: warp-group FFT kernels with the recurrence fused into pass 3
+@pytest.mark.parametrize("precision,variant,box", [(pwlib.PW_FP64, None, (24, 24, 30)),
+                                                   (pwlib.PW_MIXED, None, (24, 24, 30)),
+                                                   (pwlib.PW_MIXED, 11, (24, 24, 24))])
+def test_batch_filter_equals_per_k_filter(precision, variant, box):
+    prob = problem(box)
     ecuts = W.ecut_jitter(prob.seed, len(KPTS), prob.ecut)
-    ctxs = contexts(prob, ecuts)
+    ctxs = contexts(prob, ecuts, variant)
     assert len({c.npw for c in ctxs}) == len(ctxs)   # ragged spheres
     dt = torch.complex128 if precision == pwlib.PW_FP64 else torch.complex64
     with pwlib.Batch(ctxs) as bt:
