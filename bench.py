@@ -52,6 +52,8 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--workload", default=WORKLOAD)
+    ap.add_argument("--tc-pieces", type=int, default=2,
+                    help="bf16 pieces of the mixed GEMM operands: 2 (3 products) or 3 (6 products)")
     ap.add_argument("--bands", type=int, default=None,
                     help="override the workload's band count (small profiling cases only)")
     return ap.parse_args()
@@ -233,6 +235,8 @@ def run_ours(args):
     Y0 = torch.from_numpy(psi0).cuda()                       # complex128, resident
     Y0_32 = Y0.to(torch.complex64)
     rqmin, a, b = ctx.spectrum_bounds(Y0, 10, v0)
+    if args.tc_pieces:
+        ctx.tc_config(args.tc_pieces)
     tune_ms = ctx.autotune(M, pwlib.PW_MIXED)
     fft_cfg = ctx.fft_config(pwlib.PW_MIXED)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
@@ -368,8 +372,10 @@ def run_ours(args):
               "warmup": args.warmup, "ms_per_step": 1e3 * t_step / args.steps, "higher_is_better": True,
               "scaling": "weak", "vs_baseline": None, "dtype": "c64", "data": "synthetic",
               "config": workload_config(prob, npw, nproj),
-              "precision": "filter: complex64 FFTs + BF16-split tcgen05 projector GEMMs (3 pieces, FP32 accumulation); RR: FP64",
+              "precision": f"filter: complex64 FFTs + BF16-split tcgen05 projector GEMMs ({ctx.tc_config()} pieces per "
+                           f"operand, {3 if ctx.tc_config() == 2 else 6} products, FP32 accumulation); RR: FP64",
               "filter_ms": 1e3 * t_filter / args.steps, "wall_s": wall, "autotune_local_ms": tune_ms,
+              "tc_pieces": ctx.tc_config(),
               "fft_config": {"batch_bytes": fft_cfg[0],
                              "xline_kernel": ["line groups", "one thread per line", "warp groups",
                                               "warp groups, table twiddles"][fft_cfg[1] % 4],
@@ -410,6 +416,7 @@ def run_batched(args):
     a = [bd[1] for bd in bounds]
     b = [bd[2] for bd in bounds]
     for c in ctxs:
+        c.tc_config(args.tc_pieces)
         c.autotune(M, pwlib.PW_MIXED)
     y32 = [y.to(torch.complex64) for y in y0]
     work = [y.clone() for y in y32]
@@ -472,7 +479,7 @@ def run_batched(args):
                      "nk": nk, "npw_min": min(npws), "npw_max": max(npws), "nband": M, "degree": m,
                      "l2": "flushed between steps (256 MB write)"},
           "fp64": {"value": sub * M * m / t64, "unit": UNIT, "k_points": sub, "filter_ms": 1e3 * t64},
-          "eig_err_vs_fp64": err, "gpu_launches": int(launches + nodes * args.steps),
+          "tc_pieces": args.tc_pieces, "eig_err_vs_fp64": err, "gpu_launches": int(launches + nodes * args.steps),
           "graph_kernel_nodes": int(nodes), "clocks": clk})
     for c in ctxs:
         c.close()

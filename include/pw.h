@@ -269,6 +269,12 @@ PW_API int pw_autotune(pw_ctx* ctx, int nband, int precision, double* best_ms);
 PW_API int pw_fft_config(pw_ctx* ctx, int precision, int64_t set_batch_bytes, int set_variant,
                          int64_t* batch_bytes, int* variant);
 
+/* Reads (*pieces, may be NULL) and then, for set_pieces >= 0, sets the number of bf16
+ * pieces per operand of the mixed-precision projector GEMMs: 3 (six products, ~2^-24
+ * relative per product, the default) or 2 (three products, ~2^-16).  The tensor-core
+ * operands of P are rebuilt on the next mixed-precision call. */
+PW_API int pw_tc_config(pw_ctx* ctx, int set_pieces, int* pieces);
+
 PW_API int pw_profile_enable(pw_ctx* ctx, int on);
 PW_API int pw_profile_read(pw_ctx* ctx, double* ms, int64_t* launches);
 PW_API uint64_t pw_kernel_launches(void);

@@ -1468,6 +1468,16 @@ PW_API int pw_fft_config(pw_ctx* ctx, int precision, int64_t set_batch_bytes, in
   return PW_OK;
 }
 
+PW_API int pw_tc_config(pw_ctx* ctx, int set_pieces, int* pieces) {
+  PW_TRY(check_ctx(ctx));
+  if (pieces) *pieces = ctx->tc_pieces;
+  if (set_pieces >= 0) {
+    if (set_pieces != 2 && set_pieces != 3) return set_error(PW_EINVAL, "bf16 pieces must be 2 or 3");
+    ctx->tc_pieces = set_pieces;  // the operands are rebuilt on the next mixed call
+  }
+  return PW_OK;
+}
+
 PW_API int pw_profile_enable(pw_ctx* ctx, int on) {
   PW_TRY(check_ctx(ctx));
   ctx->prof_on = (on != 0);

@@ -30,7 +30,7 @@ EXPORTS = ("pw_ctx_create", "pw_ctx_destroy", "pw_ctx_set_stream", "pw_ctx_info"
            "pw_kernel_launches", "pw_hamiltonian_apply_noalloc", "pw_autotune", "pw_batch_create",
            "pw_batch_destroy", "pw_batch_filter", "pw_batch_chebfi_solve", "pw_ctx_set_vloc", "pw_ctx_set_D",
            "pw_local_apply", "pw_diff_create", "pw_diff_destroy", "pw_diff_tape_bytes", "pw_diff_forward",
-           "pw_diff_backward", "pw_fft_config", "pw_strerror", "pw_last_error")
+           "pw_diff_backward", "pw_fft_config", "pw_tc_config", "pw_strerror", "pw_last_error")
 
 PROF_CLASSES = ("plane_inv", "xline", "plane_fwd", "gemm_proj", "gemm_back", "small", "rr")
 
@@ -79,6 +79,7 @@ def load(path: Optional[str] = None):
     lib.pw_hamiltonian_apply_noalloc.argtypes = [vp, vp, i64, ci, vp, i64]
     lib.pw_autotune.argtypes = [vp, ci, ci, pd]
     lib.pw_fft_config.argtypes = [vp, ci, i64, ci, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ci)]
+    lib.pw_tc_config.argtypes = [vp, ci, ctypes.POINTER(ci)]
     pvp = ctypes.POINTER(vp)
     pi64 = ctypes.POINTER(ctypes.c_int64)
     lib.pw_batch_create.argtypes = [pvp, ci, vp, pvp]
@@ -230,6 +231,12 @@ class Context:
         out_b = bb.value if batch_bytes is None else int(batch_bytes)
         out_v = v.value if variant is None else int(variant)
         return out_b, out_v
+
+    def tc_config(self, pieces=None):
+        """bf16 pieces per operand of the mixed projector GEMMs (2 or 3); sets it if given."""
+        v = ctypes.c_int(0)
+        _check(load().pw_tc_config(self._h, -1 if pieces is None else int(pieces), ctypes.byref(v)))
+        return v.value if pieces is None else int(pieces)
 
     def profile(self, on=True):
         _check(load().pw_profile_enable(self._h, 1 if on else 0))

@@ -188,9 +188,13 @@ def test_chebfi_solve_fp64_matches_oracle(key):
         np.testing.assert_allclose(eig, lam, atol=1e-10, rtol=0)
 
 
-def test_chebfi_solve_mixed_close_to_fp64():
+@pytest.mark.parametrize("pieces", [3, 2])
+def test_chebfi_solve_mixed_close_to_fp64(pieces):
+    """Mixed-precision ChebFi within 1e-6 Ha of FP64, with 3 and with 2 bf16 pieces per
+    GEMM operand."""
     prob, ham, ctx = setup("tiny_24_aliasing")
     with ctx:
+        ctx.tc_config(pieces)
         psi0 = W.psi0(prob.seed, ctx.npw, prob.nband)
         v0 = to_dev(W.lanczos_v0(prob.seed, ctx.npw)[None])
         e64, _, _ = ctx.chebfi_solve(to_dev(psi0), prob.degree, prob.cycles, v0)
