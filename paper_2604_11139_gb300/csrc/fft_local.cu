@@ -1369,7 +1369,7 @@ __device__ __forceinline__ void xw_bf_fwd(const C* L, C* hbl, const C* __restric
 }
 
 template <typename T, int N1, int TW>
-__global__ void __launch_bounds__(32 * TW, 32 / TW) k_xline_twr(cplx<T>* __restrict__ hb, int64_t hb_bs,
+__global__ void __launch_bounds__(32 * TW, 24 / TW) k_xline_twr(cplx<T>* __restrict__ hb, int64_t hb_bs,
                                                       const T* __restrict__ vperm, SphereDev sp, FftPlan plan,
                                                       const cplx<T>* __restrict__ tw) {
   using C = cplx<T>;
