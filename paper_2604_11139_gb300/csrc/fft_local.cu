@@ -21,6 +21,7 @@
 #include <cuda_bf16.h>
 #include <math.h>
 
+#include <algorithm>
 #include <type_traits>
 #include <utility>
 
@@ -2244,6 +2245,130 @@ cudaError_t launch_local_apply_rec(const FftPlan& plan, const float2* tw, const 
   return cudaGetLastError();
 }
 
+// Density x-lines with groups of TW warps per 32 lines (lane = line), two-stage plans: each
+// CTA takes 32 (y,z) lines and a share of the bands (blockIdx.y), transforms a (and b) per
+// band, accumulates w_b Re[conj(a) b] per point in registers and adds its sums to the
+// permuted grid atomically.  The planes sit at x-frequency p (a common shift of a and b
+// multiplies both by the same phase, which the product cancels).
+template <typename T, int N1, int TW>
+__global__ void __launch_bounds__(32 * TW) k_xdens_wg(const cplx<T>* __restrict__ hba, const cplx<T>* __restrict__ hbb,
+                                                     int64_t hb_bs, int nb, int bper, const T* __restrict__ w,
+                                                     SphereDev sp, FftPlan plan, const cplx<T>* __restrict__ tw,
+                                                     double* __restrict__ out_perm) {
+  using C = cplx<T>;
+  constexpr CPlan P = make_cplan(N1);
+  static_assert(P.nst == 2, "two-stage plan expected");
+  constexpr int R1 = P.radix[0], R2 = P.radix[1];
+  constexpr int NBK = (R1 + TW - 1) / TW;  // stage-2 blocks per warp (at most)
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int lane = threadIdx.x & 31, t = threadIdx.x >> 5;
+  C* La = reinterpret_cast<C*>(smem_raw) + lane;
+  C* Lb = La + N1 * 32;
+  const int nyz = plan.n[1] * plan.n[2];
+  const int yz = blockIdx.x * 32 + lane;
+  const bool live = yz < nyz;
+  const int np = sp.nplane;
+  const bool two = hbb != nullptr;
+  const C* tw1 = tw + plan.d[0].tw_off[0];
+  double acc[NBK][R2];
+#pragma unroll
+  for (int i = 0; i < NBK; ++i)
+#pragma unroll
+    for (int m = 0; m < R2; ++m) acc[i][m] = 0.0;
+  const int b_lo = blockIdx.y * bper, b_hi = min(nb, b_lo + bper);
+  for (int b = b_lo; b < b_hi; ++b) {
+    const C* ha = hba + (int64_t)b * hb_bs + (live ? yz : 0);
+    const C* hbp = two ? hbb + (int64_t)b * hb_bs + (live ? yz : 0) : nullptr;
+#pragma unroll 1
+    for (int J = t; J < R2; J += TW) {
+      for (int which = 0; which < (two ? 2 : 1); ++which) {
+        const C* src = which ? hbp : ha;
+        C* L = which ? Lb : La;
+        C x[R1];
+#pragma unroll
+        for (int a = 0; a < R1; ++a) {
+          const int p = J + R2 * a;
+          x[a] = (live && p < np) ? src[(int64_t)p * nyz] : czero<C>();
+        }
+        dftR<C, +1, R1>(x);
+        if (J) {
+#pragma unroll
+          for (int m = 1; m < R1; ++m) x[m] = cmul(x[m], cconj(__ldg(&tw1[J * (R1 - 1) + m - 1])));
+        }
+#pragma unroll
+        for (int m = 0; m < R1; ++m) L[(J + R2 * m) * 32] = x[m];
+      }
+    }
+    __syncthreads();
+    const double wb = (double)w[b];
+#pragma unroll
+    for (int i = 0; i < NBK; ++i) {
+      const int blk = t + TW * i;
+      if (blk < R1) {
+        C ya[R2], yb[R2];
+#pragma unroll
+        for (int m = 0; m < R2; ++m) ya[m] = La[(blk * R2 + m) * 32];
+        dftR<C, +1, R2>(ya);
+        if (two) {
+#pragma unroll
+          for (int m = 0; m < R2; ++m) yb[m] = Lb[(blk * R2 + m) * 32];
+          dftR<C, +1, R2>(yb);
+        }
+#pragma unroll
+        for (int m = 0; m < R2; ++m) {
+          const C bv = two ? yb[m] : ya[m];
+          acc[i][m] += wb * ((double)ya[m].x * (double)bv.x + (double)ya[m].y * (double)bv.y);
+        }
+      }
+    }
+    __syncthreads();
+  }
+  if (live && b_hi > b_lo) {
+#pragma unroll
+    for (int i = 0; i < NBK; ++i) {
+      const int blk = t + TW * i;
+      if (blk < R1) {
+#pragma unroll
+        for (int m = 0; m < R2; ++m) atomicAdd(&out_perm[(int64_t)(blk * R2 + m) * nyz + yz], acc[i][m]);
+      }
+    }
+  }
+}
+
+template <typename T, int N1>
+static cudaError_t launch_xdens_wg(const cplx<T>* hba, const cplx<T>* hbb, int64_t hb_bs, int nb, const T* w,
+                                   const SphereDev& sp, const FftPlan& plan, const cplx<T>* tw, double* out_perm,
+                                   cudaStream_t st) {
+  constexpr int TW = 4;
+  const size_t sm = sizeof(cplx<T>) * (size_t)N1 * 32 * (hbb ? 2 : 1);
+  cudaError_t e = cudaFuncSetAttribute(k_xdens_wg<T, N1, TW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e) return e;
+  if ((e = cudaFuncSetAttribute(k_xdens_wg<T, N1, TW>, cudaFuncAttributePreferredSharedMemoryCarveout, 100))) return e;
+  const int nyz = plan.n[1] * plan.n[2];
+  const int gx = (nyz + 31) / 32;
+  // enough CTAs for a few waves of the 152 SMs: split the bands
+  int splits = std::max(1, std::min(nb, (152 * 6 + gx - 1) / gx));
+  const int bper = (nb + splits - 1) / splits;
+  splits = (nb + bper - 1) / bper;
+  k_xdens_wg<T, N1, TW><<<dim3(gx, splits), 32 * TW, sm, st>>>(hba, hbb, hb_bs, nb, bper, w, sp, plan, tw, out_perm); count_launch();
+  return cudaGetLastError();
+}
+
+template <typename T>
+static cudaError_t xdens_wg(const cplx<T>* hba, const cplx<T>* hbb, int64_t hb_bs, int nb, const T* w,
+                            const SphereDev& sp, const FftPlan& plan, const cplx<T>* tw, double* out_perm,
+                            cudaStream_t st) {
+  switch (plan.n[0]) {
+    case 24: return launch_xdens_wg<T, 24>(hba, hbb, hb_bs, nb, w, sp, plan, tw, out_perm, st);
+    case 64: return launch_xdens_wg<T, 64>(hba, hbb, hb_bs, nb, w, sp, plan, tw, out_perm, st);
+    case 72: return launch_xdens_wg<T, 72>(hba, hbb, hb_bs, nb, w, sp, plan, tw, out_perm, st);
+    case 90: return launch_xdens_wg<T, 90>(hba, hbb, hb_bs, nb, w, sp, plan, tw, out_perm, st);
+    case 96: return launch_xdens_wg<T, 96>(hba, hbb, hb_bs, nb, w, sp, plan, tw, out_perm, st);
+    case 120: return launch_xdens_wg<T, 120>(hba, hbb, hb_bs, nb, w, sp, plan, tw, out_perm, st);
+    default: return cudaErrorNotSupported;
+  }
+}
+
 template <typename T>
 cudaError_t launch_density(const FftPlan& plan, const cplx<T>* tw, const SphereDev& sp,
                            const cplx<T>* a, const cplx<T>* b, int64_t ld, int nband, const T* w_dev,
@@ -2262,10 +2387,26 @@ cudaError_t launch_density(const FftPlan& plan, const cplx<T>* tw, const SphereD
   cplx<T>* hbb = b ? hb + hb_bs * band_batch : nullptr;
   for (int b0 = 0; b0 < nband; b0 += band_batch) {
     const int nb = min(band_batch, nband - b0);
-    k_plane_inv<T><<<dim3(sp.nplane, nb), kThreads, sm1, st>>>(a + b0 * ld, ld, hb, hb_bs, sp, plan, tw, cz); count_launch();
-    if (b) { k_plane_inv<T><<<dim3(sp.nplane, nb), kThreads, sm1, st>>>(b + b0 * ld, ld, hbb, hb_bs, sp, plan, tw, cz); count_launch(); }
-    k_xline_density<T><<<(nyz + lyz - 1) / lyz, kThreads, sm2, st>>>(hb, hbb, hb_bs, nb, w_dev + b0, sp, plan,
-                                                                     tw, lyz, out_perm); count_launch();
+    // pass 1 for a (and b): warp-group plane kernels where they cover the box
+    for (int which = 0; which < (b ? 2 : 1); ++which) {
+      const cplx<T>* src = (which ? b : a) + b0 * ld;
+      cplx<T>* dst = which ? hbb : hb;
+      e = plane_wg<T>(0, src, ld, dst, hb_bs, sp, plan, tw, nullptr, nullptr, 0, nb, st);
+      if (e == cudaErrorNotSupported) {
+        (void)cudaGetLastError();
+        k_plane_inv<T><<<dim3(sp.nplane, nb), kThreads, sm1, st>>>(src, ld, dst, hb_bs, sp, plan, tw, cz); count_launch();
+        e = cudaGetLastError();
+      }
+      if (e) return e;
+    }
+    e = xdens_wg<T>(hb, hbb, hb_bs, nb, w_dev + b0, sp, plan, tw, out_perm, st);
+    if (e == cudaErrorNotSupported) {
+      (void)cudaGetLastError();
+      k_xline_density<T><<<(nyz + lyz - 1) / lyz, kThreads, sm2, st>>>(hb, hbb, hb_bs, nb, w_dev + b0, sp, plan,
+                                                                       tw, lyz, out_perm); count_launch();
+      e = cudaGetLastError();
+    }
+    if (e) return e;
   }
   return cudaGetLastError();
 }

@@ -13,7 +13,7 @@ cudaError_t la_zero_upper(double2* A, int64_t lda, int n, cudaStream_t st);
 cudaError_t la_trinv_lower(const double2* L, int64_t lda, int n, double2* X, int64_t ldx, double2* tmp,
                            cudaStream_t st);
 // eigenpairs of Hermitian A (n x n, lda n; destroyed): eig ascending (device), U (n x n);
-// ws: 3 n*n complex; norms_dev: 2 doubles.  Synchronises the stream once per sweep.
+// ws: 3 n*n + n + 2 complex; norms_dev: 2 doubles.  Synchronises the stream once per sweep.
 int la_jacobi_eigh(double2* A, int n, double2* U, double* eig, double2* ws, double* norms_dev,
                    cudaStream_t st, int max_sweeps, double tol, int* sweeps_out);
 cudaError_t la_coldot(const double2* A, int64_t lda, const double2* B, int64_t ldb, int npw, int m,

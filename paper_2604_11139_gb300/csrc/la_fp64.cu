@@ -213,8 +213,19 @@ __device__ __forceinline__ Rot jac_rot(const double2* A, int n, int p, int q) {
   return r;
 }
 
+// the rotation of every pair of round t, computed once (FP64 square roots and divisions
+// are the expensive part of a round)
+__global__ void k_jacobi_rot(const double2* __restrict__ A, int n, int np, int t, Rot* __restrict__ rot) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= np / 2) return;
+  int p, q;
+  rr_pair(t, i, np, p, q);
+  rot[i] = jac_rot(A, n, p, q);
+}
+
 __global__ void k_jacobi_round(const double2* __restrict__ Ao, double2* __restrict__ An,
-                               const double2* __restrict__ Vo, double2* __restrict__ Vn, int n, int np, int t) {
+                               const double2* __restrict__ Vo, double2* __restrict__ Vn, int n, int np, int t,
+                               const Rot* __restrict__ rot) {
   const int npair = np / 2;
   const int64_t nblk = (int64_t)npair * npair;
   const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -223,7 +234,7 @@ __global__ void k_jacobi_round(const double2* __restrict__ Ao, double2* __restri
     int pI, qI, pJ, qJ;
     rr_pair(t, I, np, pI, qI);
     rr_pair(t, Jx, np, pJ, qJ);
-    const Rot ri = jac_rot(Ao, n, pI, qI), rj = jac_rot(Ao, n, pJ, qJ);
+    const Rot ri = rot[I], rj = rot[Jx];
     const bool vpI = pI < n, vqI = qI < n, vpJ = pJ < n, vqJ = qJ < n;
     const double2 z = make_double2(0, 0);
     const double2 b00 = (vpI && vpJ) ? Ao[pI + (int64_t)pJ * n] : z;
@@ -251,7 +262,7 @@ __global__ void k_jacobi_round(const double2* __restrict__ Ao, double2* __restri
     const int r = (int)(k % n), Jx = (int)(k / n);
     int pJ, qJ;
     rr_pair(t, Jx, np, pJ, qJ);
-    const Rot rj = jac_rot(Ao, n, pJ, qJ);
+    const Rot rj = rot[Jx];
     const bool vp = pJ < n, vq = qJ < n;
     const double2 z = make_double2(0, 0);
     const double2 vpv = vp ? Vo[r + (int64_t)pJ * n] : z;
@@ -310,10 +321,11 @@ __global__ void k_sort_eig(const double2* A, const double2* V, int n, double* ei
 
 int la_jacobi_eigh(double2* A, int n, double2* U, double* eig, double2* ws, double* norms_dev,
                    cudaStream_t st, int max_sweeps, double tol, int* sweeps_out) {
-  // ws: 3 n*n complex (A copy, V, V copy)
+  // ws: 3 n*n + n + 2 complex (A copy, V, V copy, the rotations of a round)
   double2* A2 = ws;
   double2* V = ws + (int64_t)n * n;
   double2* V2 = ws + 2 * (int64_t)n * n;
+  Rot* rot = reinterpret_cast<Rot*>(ws + 3 * (int64_t)n * n);
   const int64_t nn = (int64_t)n * n;
   k_eye<<<(unsigned)((nn + 255) / 256), 256, 0, st>>>(V, n); count_launch();
   cudaMemcpyAsync(A2, A, sizeof(double2) * nn, cudaMemcpyDeviceToDevice, st);
@@ -329,7 +341,8 @@ int la_jacobi_eigh(double2* A, int n, double2* U, double* eig, double2* ws, doub
   double prev_off = INFINITY;
   while (!conv && sweep < max_sweeps) {
     for (int t = 0; t < np - 1; ++t) {
-      k_jacobi_round<<<nblk, 256, 0, st>>>(Acur, Anext, Vcur, Vnext, n, np, t); count_launch();
+      k_jacobi_rot<<<(npair + 127) / 128, 128, 0, st>>>(Acur, n, np, t, rot); count_launch();
+      k_jacobi_round<<<nblk, 256, 0, st>>>(Acur, Anext, Vcur, Vnext, n, np, t, rot); count_launch();
       double2* x = Acur; Acur = Anext; Anext = x;
       x = Vcur; Vcur = Vnext; Vnext = x;
     }

@@ -711,7 +711,7 @@ int rr_impl(pw_ctx* ctx, double2* Y, int64_t ldy, int m, double2* hpsi_out, doub
   WS(Linv, double2, WS_LINV, (size_t)m * m);
   WS(tmp, double2, WS_TMP, (size_t)m * m);
   WS(U, double2, WS_U, (size_t)m * m);
-  WS(jac, double2, WS_JAC, (size_t)3 * m * m);
+  WS(jac, double2, WS_JAC, (size_t)3 * m * m + m + 2);
   WS(eig, double, WS_EIG, (size_t)2 * m + 4);
   WS(scal, int, WS_SCAL, 16);
   double* norms = eig + 2 * m;

@@ -202,7 +202,7 @@ def test_chebfi_solve_mixed_close_to_fp64(pieces):
         assert np.abs(emx - e64).max() < 1e-6
 
 
-@pytest.mark.parametrize("key", ["ortho_k_ragged", "box_2_3_5"])
+@pytest.mark.parametrize("key", ["ortho_k_ragged", "box_2_3_5", "tiny_24_aliasing", "box_64_tl8"])
 def test_density_grad(key):
     prob, ham, ctx = setup(key)
     with ctx:
