@@ -134,7 +134,8 @@ PW_API int pw_rayleigh_ritz(pw_ctx* ctx, void* psi, int64_t ldpsi, int nband,
  * [filter (precision) -> Rayleigh-Ritz (FP64)], the cut of each later cycle
  * being the largest Ritz value.  psi: complex128 device block, overwritten with
  * the Ritz vectors.  eig, resid: host arrays of nband (resid may be NULL).
- * bounds (host, may be NULL) receives {upper, first cut}. */
+ * bounds (host, may be NULL) receives {upper, first cut}.  With PW_MIXED and Q == NULL
+ * the Rayleigh quotients of the first cut come from the complex64 H-apply. */
 PW_API int pw_chebfi_solve(pw_ctx* ctx, void* psi, int64_t ldpsi, int nband, int degree,
                            int cycles, int lanczos_steps, const void* v0, int precision,
                            double* eig, double* resid, double* bounds);

@@ -1342,7 +1342,33 @@ PW_API int pw_chebfi_solve(pw_ctx* ctx, void* psi_v, int64_t ldpsi, int nband, i
   if (precision != PW_FP64 && precision != PW_MIXED) return set_error(PW_EINVAL, "unknown precision");
   double2* psi = (double2*)psi_v;
   double rqmin = 0, a = 0, upper = 0;
-  PW_TRY(bounds_impl(ctx, psi, ldpsi, nband, lanczos_steps, (const double2*)v0, &rqmin, &a, &upper));
+  if (precision == PW_MIXED && !ctx->has_q) {
+    // the cut a is a filter parameter, not a result: the Rayleigh quotients of the starting
+    // block come from the complex64 H-apply (the FP64 apply of a block costs as much as a
+    // filter's worth of mixed steps); the Lanczos bound stays FP64
+    PW_TRY(bounds_impl(ctx, psi, ldpsi, 0, lanczos_steps, (const double2*)v0, nullptr, nullptr, &upper));
+    const int npw = ctx->npw;
+    const cudaStream_t st = ctx->stream;
+    WS(y32, float2, WS_Y1, (size_t)npw * nband);
+    WS(h32, float2, WS_Y2, (size_t)npw * nband);
+    WS(HY, double2, WS_HY, (size_t)npw * nband);
+    WS(rq, double2, WS_RQ, (size_t)3 * nband + 8);
+    CU_TRY(la_to_c64(psi, ldpsi, y32, npw, npw, nband, st), "to c64");
+    PW_TRY(apply_impl<float>(ctx, y32, npw, nband, h32, nullptr, npw));
+    CU_TRY(la_to_c128(h32, npw, HY, npw, npw, nband, st), "to c128");
+    CU_TRY(la_coldot(psi, ldpsi, HY, npw, npw, nband, rq, st), "rq num");
+    CU_TRY(la_coldot(psi, ldpsi, psi, ldpsi, npw, nband, rq + nband, st), "rq den");
+    double* mm = (double*)(rq + 2 * nband);
+    double* rqv = (double*)(rq + 2 * nband + 1);
+    CU_TRY(la_rq_minmax(rq, rq + nband, nband, rqv, mm, st), "rq minmax");
+    double h[2];
+    CU_TRY(cudaMemcpyAsync(h, mm, 2 * sizeof(double), cudaMemcpyDeviceToHost, st), "rq copy");
+    CU_TRY(cudaStreamSynchronize(st), "rq sync");
+    rqmin = h[0];
+    a = h[1];
+  } else {
+    PW_TRY(bounds_impl(ctx, psi, ldpsi, nband, lanczos_steps, (const double2*)v0, &rqmin, &a, &upper));
+  }
   if (bounds) { bounds[0] = upper; bounds[1] = a; }
   for (int c = 0; c < cycles; ++c) {
     if (precision == PW_FP64) {
