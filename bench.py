@@ -160,6 +160,22 @@ def cpu_oracle_rate(prob, seconds, max_bands=256):
                       f"of the {prob.name} workload, {dt:.1f} s"}
 
 
+def max_over_ranks(values, dist, device):
+    """Element-wise maximum of per-rank timings across the ranks (identity without a group)."""
+    if dist is None:
+        return [float(v) for v in values]
+    import torch
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(x) for x in t.tolist()]
+
+
+def weak_value(world, units_per_rank, seconds):
+    """Whole-job throughput of `world` independent replicas, each processing `units_per_rank`
+    units in `seconds` (the maximum over the ranks)."""
+    return world * units_per_rank / seconds
+
+
 def nvtx_push(name):
     try:
         import torch
@@ -284,14 +300,8 @@ def run_ours(args):
     clk = clocks.stop()
     filt_ms = [e0.elapsed_time(e1) for e0, e1, e2 in evs]
     step_ms = [e0.elapsed_time(e2) for e0, e1, e2 in evs]
-    t_filter = sum(filt_ms) / 1e3
-    if dist is not None:
-        t = torch.tensor([t_filter, sum(step_ms) / 1e3], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_filter, t_step = float(t[0]), float(t[1])
-    else:
-        t_step = sum(step_ms) / 1e3
-    value = world * M * m * args.steps / t_filter
+    t_filter, t_step = max_over_ranks([sum(filt_ms) / 1e3, sum(step_ms) / 1e3], dist, "cuda")
+    value = weak_value(world, M * m * args.steps, t_filter)
 
     # FP64 GPU path on the same inputs (denominator of the mixed-vs-FP64 ratio)
     fp64 = None
@@ -328,7 +338,10 @@ def run_ours(args):
         torch.cuda.synchronize()
         if s > 0:
             e2e_t.append(time.perf_counter() - t0)
-    e2e_val = world * M * m / statistics.mean(e2e_t) if e2e_t else None
+    e2e_val = None
+    if e2e_t:
+        (t_e2e,) = max_over_ranks([statistics.mean(e2e_t)], dist, "cuda")
+        e2e_val = weak_value(world, M * m, t_e2e)
     bytes_psi = psi0.nbytes
 
     # roofline of the dominant kernel class of the filter, and of every class
