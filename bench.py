@@ -358,7 +358,7 @@ def run_ours(args):
     pieces = ctx.tc_config()
     # pass 3 carries the recurrence (reads P Z and Y_{k-1}, writes the bf16 pieces of Y_{k+1})
     # when the warp-group plane kernels run without Q
-    fused = (fft_cfg[1] // 4 == 2) and prob.Q is None
+    fused = (fft_cfg[1] // 8 == 2) and prob.Q is None
     alg = {"plane_inv": ("hbm", nb_avg * (npw + half) * c8),
            "xline": ("hbm", nb_avg * 2 * half * c8 + box[0] * box[1] * box[2] * 4),
            "plane_fwd": ("hbm", nb_avg * ((half + (4 if fused else 2) * npw) * c8 + (4 * pieces * npw if fused else 0))),
@@ -402,9 +402,10 @@ def run_ours(args):
               "tc_pieces": ctx.tc_config(),
               "fft_config": {"batch_bytes": fft_cfg[0],
                              "xline_kernel": ["line groups", "one thread per line", "warp groups",
-                                              "warp groups, table twiddles"][fft_cfg[1] % 4],
+                                              "warp groups, table twiddles",
+                                              "warp groups, table twiddles, bands per CTA"][fft_cfg[1] % 8],
                              "plane_kernels": ["line groups", "one thread per line",
-                                               "warp groups"][fft_cfg[1] // 4]},
+                                               "warp groups"][fft_cfg[1] // 8]},
               "fp64": fp64, "eig_err_vs_fp64": eig_err,
               "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": bytes_psi,
                       "d2h_bytes_per_step": bytes_psi + 8 * M,

@@ -253,18 +253,18 @@ enum pw_prof_class {
 };
 /* Autotuner: times the local-potential FFT passes on nband bands for several band
  * batch sizes (the batch's half-box planes from 16 MB to 2 GB) and, for PW_MIXED, the
- * forms of the pass kernels, variant = x-line form + 4 * plane form.  x-line forms:
+ * forms of the pass kernels, variant = x-line form + 8 * plane form.  x-line forms:
  * 0 line groups of 1-8 threads with shared-memory twiddles, 1 one thread per line with
  * compile-time twiddles, 2 groups of warps per 32 lines with compile-time twiddles,
- * 3 the same with run-time butterfly indices and table twiddles; plane forms: 0 line
- * groups, 1 one thread per line, 2 groups of warps per 32 lines with table twiddles.
- * Forms other than 0 cover box lengths with two-stage
- * radix plans.  Keeps the fastest for `precision` in the context.  Synchronises the
- * stream; *best_ms (may be NULL) receives the best time of one apply. */
+ * 3 the same with run-time butterfly indices and table twiddles, 4 as 3 with several bands
+ * per CTA; plane forms: 0 line groups, 1 one thread per line, 2 groups of warps per 32
+ * lines with table twiddles.  Forms other than 0 cover box lengths with two-stage radix
+ * plans.  Keeps the fastest for `precision` in the context.  Synchronises the stream;
+ * *best_ms (may be NULL) receives the best time of one apply. */
 PW_API int pw_autotune(pw_ctx* ctx, int nband, int precision, double* best_ms);
 /* Reads (*batch_bytes, *variant; either pointer may be NULL) and then, for arguments
  * >= 0, sets the FFT configuration of `precision`: bytes of half-box planes per band
- * batch (>= 1 band is always used) and the pass-kernel forms (0 ... 11 as for
+ * batch (>= 1 band is always used) and the pass-kernel forms (as for
  * pw_autotune; non-zero forms apply to PW_MIXED only and fall back to 0 for box
  * lengths they do not cover).  Pass -1 to leave a field unchanged. */
 PW_API int pw_fft_config(pw_ctx* ctx, int precision, int64_t set_batch_bytes, int set_variant,

@@ -1407,6 +1407,64 @@ __global__ void __launch_bounds__(32 * TW, 24 / TW) k_xline_twr(cplx<T>* __restr
   for (int J = t; J < R2; J += TW) xw_bf_fwd<C, -1, R1, R2>(L, hbl, tw1, J, nyz, h0, np, N1, live);
 }
 
+// The same with several bands per CTA: the V values of the CTA's lines stay in registers.
+template <typename T, int N1, int TW>
+__global__ void __launch_bounds__(32 * TW, 24 / TW) k_xline_twm(cplx<T>* __restrict__ hb, int64_t hb_bs, int nb,
+                                                      int bper, const T* __restrict__ vperm, SphereDev sp,
+                                                      FftPlan plan, const cplx<T>* __restrict__ tw) {
+  using C = cplx<T>;
+  constexpr CPlan P = make_cplan(N1);
+  static_assert(P.nst == 2, "two-stage plan expected");
+  constexpr int R1 = P.radix[0], R2 = P.radix[1];
+  constexpr int NBK = (R1 + TW - 1) / TW;  // stage-2 blocks per warp (at most)
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int lane = threadIdx.x & 31, t = threadIdx.x >> 5;
+  C* L = reinterpret_cast<C*>(smem_raw) + lane;
+  const int nyz = plan.n[1] * plan.n[2];
+  const int yz = blockIdx.x * 32 + lane;
+  const bool live = yz < nyz;
+  const int h0 = sp.plane_h[0], np = sp.nplane;
+  const C* tw1 = tw + plan.d[0].tw_off[0];
+  // this thread's V values, read once for all the CTA's bands
+  T vr[NBK][R2];
+  {
+    const T* vb = vperm + (live ? yz : 0);
+#pragma unroll
+    for (int i = 0; i < NBK; ++i) {
+      const int blk = t + TW * i;
+#pragma unroll
+      for (int m = 0; m < R2; ++m) vr[i][m] = (live && blk < R1) ? vb[(int64_t)(blk * R2 + m) * nyz] : (T)0;
+    }
+  }
+  const int b_lo = blockIdx.y * bper, b_hi = min(nb, b_lo + bper);
+#pragma unroll 1
+  for (int b = b_lo; b < b_hi; ++b) {
+    C* hbl = hb + (int64_t)b * hb_bs + (live ? yz : 0);
+#pragma unroll 1
+    for (int J = t; J < R2; J += TW) xw_bf_inv<C, +1, R1, R2>(L, hbl, tw1, J, nyz, h0, np, N1, live);
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < NBK; ++i) {
+      const int blk = t + TW * i;
+      if (blk < R1) {
+        C y[R2];
+#pragma unroll
+        for (int m = 0; m < R2; ++m) y[m] = L[(blk * R2 + m) * 32];
+        dftR<C, +1, R2>(y);
+#pragma unroll
+        for (int m = 0; m < R2; ++m) y[m] = cscale(y[m], vr[i][m]);
+        dftR<C, -1, R2>(y);
+#pragma unroll
+        for (int m = 0; m < R2; ++m) L[(blk * R2 + m) * 32] = y[m];
+      }
+    }
+    __syncthreads();
+#pragma unroll 1
+    for (int J = t; J < R2; J += TW) xw_bf_fwd<C, -1, R1, R2>(L, hbl, tw1, J, nyz, h0, np, N1, live);
+    __syncthreads();  // the next band's first stage overwrites the lines
+  }
+}
+
 template <typename T, int N1, int TW>
 __global__ void __launch_bounds__(32 * TW) k_xline_tw(cplx<T>* __restrict__ hb, int64_t hb_bs,
                                                      const T* __restrict__ vperm, SphereDev sp, FftPlan plan) {
@@ -1460,27 +1518,39 @@ static cudaError_t launch_xline_tw(cplx<T>* hb, int64_t hb_bs, const T* vperm, c
 
 template <typename T, int N1, int TW>
 static cudaError_t launch_xline_twr(cplx<T>* hb, int64_t hb_bs, const T* vperm, const SphereDev& sp,
-                                    const FftPlan& plan, const cplx<T>* tw, int nb, cudaStream_t st) {
+                                    const FftPlan& plan, const cplx<T>* tw, int nb, bool multi, cudaStream_t st) {
   const size_t sm = sizeof(cplx<T>) * (size_t)N1 * 32;
-  cudaError_t e = cudaFuncSetAttribute(k_xline_twr<T, N1, TW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  if (e) return e;
-  if ((e = cudaFuncSetAttribute(k_xline_twr<T, N1, TW>, cudaFuncAttributePreferredSharedMemoryCarveout, 100))) return e;
   const int nyz = plan.n[1] * plan.n[2];
-  k_xline_twr<T, N1, TW><<<dim3((nyz + 31) / 32, nb), 32 * TW, sm, st>>>(hb, hb_bs, vperm, sp, plan, tw); count_launch();
+  const int gx = (nyz + 31) / 32;
+  cudaError_t e;
+  if (!multi) {
+    if ((e = cudaFuncSetAttribute(k_xline_twr<T, N1, TW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm)))
+      return e;
+    if ((e = cudaFuncSetAttribute(k_xline_twr<T, N1, TW>, cudaFuncAttributePreferredSharedMemoryCarveout, 100)))
+      return e;
+    k_xline_twr<T, N1, TW><<<dim3(gx, nb), 32 * TW, sm, st>>>(hb, hb_bs, vperm, sp, plan, tw); count_launch();
+    return cudaGetLastError();
+  }
+  if ((e = cudaFuncSetAttribute(k_xline_twm<T, N1, TW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm))) return e;
+  if ((e = cudaFuncSetAttribute(k_xline_twm<T, N1, TW>, cudaFuncAttributePreferredSharedMemoryCarveout, 100))) return e;
+  // several bands per CTA (the V values stay in registers), about six waves of CTAs
+  const int bper = std::max(1, (int)(((int64_t)nb * gx + 152 * 36 - 1) / (152 * 36)));
+  const int splits = (nb + bper - 1) / bper;
+  k_xline_twm<T, N1, TW><<<dim3(gx, splits), 32 * TW, sm, st>>>(hb, hb_bs, nb, bper, vperm, sp, plan, tw); count_launch();
   return cudaGetLastError();
 }
 
 // groups of warps per 32 x-lines, run-time butterfly indices (any two-stage plan)
 template <typename T>
 static cudaError_t xline_twr(cplx<T>* hb, int64_t hb_bs, const T* vperm, const SphereDev& sp, const FftPlan& plan,
-                             const cplx<T>* tw, int nb, cudaStream_t st) {
+                             const cplx<T>* tw, int nb, bool multi, cudaStream_t st) {
   switch (plan.n[0]) {
-    case 24: return launch_xline_twr<T, 24, 4>(hb, hb_bs, vperm, sp, plan, tw, nb, st);
-    case 64: return launch_xline_twr<T, 64, 4>(hb, hb_bs, vperm, sp, plan, tw, nb, st);
-    case 72: return launch_xline_twr<T, 72, 4>(hb, hb_bs, vperm, sp, plan, tw, nb, st);
-    case 90: return launch_xline_twr<T, 90, 4>(hb, hb_bs, vperm, sp, plan, tw, nb, st);
-    case 96: return launch_xline_twr<T, 96, 4>(hb, hb_bs, vperm, sp, plan, tw, nb, st);
-    case 120: return launch_xline_twr<T, 120, 4>(hb, hb_bs, vperm, sp, plan, tw, nb, st);
+    case 24: return launch_xline_twr<T, 24, 4>(hb, hb_bs, vperm, sp, plan, tw, nb, multi, st);
+    case 64: return launch_xline_twr<T, 64, 4>(hb, hb_bs, vperm, sp, plan, tw, nb, multi, st);
+    case 72: return launch_xline_twr<T, 72, 4>(hb, hb_bs, vperm, sp, plan, tw, nb, multi, st);
+    case 90: return launch_xline_twr<T, 90, 4>(hb, hb_bs, vperm, sp, plan, tw, nb, multi, st);
+    case 96: return launch_xline_twr<T, 96, 4>(hb, hb_bs, vperm, sp, plan, tw, nb, multi, st);
+    case 120: return launch_xline_twr<T, 120, 4>(hb, hb_bs, vperm, sp, plan, tw, nb, multi, st);
     default: return cudaErrorNotSupported;
   }
 }
@@ -2123,13 +2193,14 @@ cudaError_t launch_local_apply(const FftPlan& plan, const cplx<T>* tw, const Sph
   const int nyz = plan.n[1] * plan.n[2];
   // one-thread-per-line kernels: complex64 only (a complex128 line per thread needs twice
   // the shared memory per CTA), when the context selected them
-  // kernel forms (complex64): x-line form = variant % 4 (0 line groups, 1 one thread per
-  // line, 2 warp groups with compile-time twiddles, 3 warp groups with table twiddles),
-  // plane form = variant / 4 (0 line groups, 1 one thread per line, 2 warp groups)
+  // kernel forms (complex64): x-line form = variant % 8 (0 line groups, 1 one thread per
+  // line, 2 warp groups with compile-time twiddles, 3 warp groups with table twiddles, 4 the
+  // same with several bands per CTA), plane form = variant / 8 (0 line groups, 1 one thread
+  // per line, 2 warp groups)
   const int fv = (std::is_same<T, float>::value && prof) ? prof->fft_variant[0] : 0;
-  const int xf = fv % 4, pf = fv / 4;
+  const int xf = fv % 8, pf = fv / 8;
   const bool tpl = pf == 1, pwg = pf == 2;
-  const bool xtw = xf == 2, xtwr = xf == 3;
+  const bool xtw = xf == 2, xtwr = xf == 3 || xf == 4;
   for (int b0 = 0; b0 < nband; b0 += band_batch) {
     const int nb = min(band_batch, nband - b0);
     prof_begin(prof, PW_PROF_PLANE_INV);
@@ -2153,7 +2224,7 @@ cudaError_t launch_local_apply(const FftPlan& plan, const cplx<T>* tw, const Sph
     e = cudaErrorNotSupported;
     if constexpr (std::is_same<T, float>::value) {
       if (xtw) e = xline_tw<T>(hb, hb_bs, vperm, sp, plan, nb, st);
-      if (xtwr) e = xline_twr<T>(hb, hb_bs, vperm, sp, plan, tw, nb, st);
+      if (xtwr) e = xline_twr<T>(hb, hb_bs, vperm, sp, plan, tw, nb, xf == 4, st);
       if (xf == 1) {
         (void)cudaGetLastError();
         e = xline_tpl<T>(hb, hb_bs, vperm, sp, plan, nb, st);
@@ -2194,7 +2265,7 @@ cudaError_t launch_local_apply(const FftPlan& plan, const cplx<T>* tw, const Sph
 }
 
 bool local_apply_rec_supported(const FftPlan& plan, const ::pw_ctx* prof) {
-  return prof && prof->fft_variant[0] / 4 == 2 && plane_wg_covers(plan);
+  return prof && prof->fft_variant[0] / 8 == 2 && plane_wg_covers(plan);
 }
 
 cudaError_t launch_local_apply_rec(const FftPlan& plan, const float2* tw, const SphereDev& sp, const float* vperm,
@@ -2204,7 +2275,7 @@ cudaError_t launch_local_apply_rec(const FftPlan& plan, const float2* tw, const 
   using T = float;
   if (!local_apply_rec_supported(plan, prof)) return cudaErrorNotSupported;
   if (nband <= 0) return cudaSuccess;
-  const int xf = prof->fft_variant[0] % 4;
+  const int xf = prof->fft_variant[0] % 8;
   const int64_t hb_bs = (int64_t)sp.nplane * plan.n[1] * plan.n[2];
   const int nyz = plan.n[1] * plan.n[2];
   const int lyz = 32;
@@ -2218,7 +2289,7 @@ cudaError_t launch_local_apply_rec(const FftPlan& plan, const float2* tw, const 
     prof_begin(prof, PW_PROF_XLINE);
     e = cudaErrorNotSupported;
     if (xf == 2) e = xline_tw<T>(hb, hb_bs, vperm, sp, plan, nb, st);
-    if (xf == 3) e = xline_twr<T>(hb, hb_bs, vperm, sp, plan, tw, nb, st);
+    if (xf == 3 || xf == 4) e = xline_twr<T>(hb, hb_bs, vperm, sp, plan, tw, nb, xf == 4, st);
     if (xf == 1) e = xline_tpl<T>(hb, hb_bs, vperm, sp, plan, nb, st);
     if (e == cudaErrorNotSupported) {
       (void)cudaGetLastError();

@@ -1468,11 +1468,13 @@ PW_API int pw_autotune(pw_ctx* ctx, int nband, int precision, double* best_ms) {
     return PW_OK;
   };
   // batch size with the current kernel forms, every kernel form at that size (complex64:
-  // x-line form + 4 * plane form, 12 combinations), the batch size again with the forms kept
-  const int nvar = precision == PW_MIXED ? 12 : 1;
+  // x-line form (0-4) + 8 * plane form (0-2)), the batch size again with the forms kept
   for (size_t c : cand) PW_TRY(consider(c, best_v));
   const size_t c1 = best_c;
-  for (int v = 0; v < nvar; ++v) PW_TRY(consider(c1, v));
+  if (precision == PW_MIXED) {
+    for (int pf = 0; pf < 3; ++pf)
+      for (int xf = 0; xf < 5; ++xf) PW_TRY(consider(c1, xf + 8 * pf));
+  }
   const int v1 = best_v;
   for (size_t c : cand) PW_TRY(consider(c, v1));
   ctx->fft_batch_bytes[slot] = best_c;
@@ -1485,7 +1487,7 @@ PW_API int pw_fft_config(pw_ctx* ctx, int precision, int64_t set_batch_bytes, in
                          int* variant) {
   PW_TRY(check_ctx(ctx));
   if (precision != PW_FP64 && precision != PW_MIXED) return set_error(PW_EINVAL, "unknown precision");
-  if (set_variant > 11) return set_error(PW_EINVAL, "unknown FFT kernel variant %d", set_variant);
+  if (set_variant > 20 || set_variant % 8 > 4) return set_error(PW_EINVAL, "unknown FFT kernel variant %d", set_variant);
   const int slot = precision == PW_MIXED ? 0 : 1;
   if (batch_bytes) *batch_bytes = (int64_t)ctx->fft_batch_bytes[slot];
   if (variant) *variant = ctx->fft_variant[slot];

@@ -285,13 +285,13 @@ struct pw_ctx {
   uint64_t ws_gen = 0;  // bumped whenever a workspace is (re)allocated (captured graphs check it)
   // tuning: bytes of half-box planes per FFT band batch (complex64, complex128); set by pw_autotune
   size_t fft_batch_bytes[2] = {(size_t)48 << 20, (size_t)256 << 20};
-  // FFT pass kernel forms per precision, variant = xline form + 4 * plane form.  x-line
+  // FFT pass kernel forms per precision, variant = xline form + 8 * plane form.  x-line
   // forms: 0 line groups of 1-8 threads with shared-memory twiddles, 1 one thread per line
   // with compile-time twiddles, 2 groups of warps per 32 lines (lane = line) with
-  // compile-time twiddles, 3 the same with run-time butterfly indices and table twiddles;
-  // plane forms: 0 line groups, 1 one thread per line, 2 groups of warps per 32 lines with
-  // table twiddles.  Forms other than 0 cover two-stage
-  // plans in complex64 only (otherwise form 0 runs); set by pw_autotune
+  // compile-time twiddles, 3 the same with run-time butterfly indices and table twiddles,
+  // 4 as 3 with several bands per CTA (V kept in registers); plane forms: 0 line groups,
+  // 1 one thread per line, 2 groups of warps per 32 lines with table twiddles.  Forms other
+  // than 0 cover two-stage plans in complex64 only (otherwise form 0 runs); set by pw_autotune
   int fft_variant[2] = {0, 0};
   int last_sweeps = 0;  // Jacobi sweeps of the last Rayleigh-Ritz step
 };
