@@ -54,6 +54,10 @@ def parse():
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--tc-pieces", type=int, default=2,
                     help="bf16 pieces of the mixed GEMM operands: 2 (3 products) or 3 (6 products)")
+    ap.add_argument("--fft-variant", type=int, default=None,
+                    help="pin the FFT kernel forms (x-line form + 8 * plane form) instead of autotuning")
+    ap.add_argument("--fft-batch-mb", type=int, default=None,
+                    help="pin the FFT band batch (MB of half-box planes per launch) instead of autotuning")
     ap.add_argument("--bands", type=int, default=None,
                     help="override the workload's band count (small profiling cases only)")
     return ap.parse_args()
@@ -255,7 +259,12 @@ def run_ours(args):
     rqmin, a, b = ctx.spectrum_bounds(Y0, 10, v0)
     if args.tc_pieces:
         ctx.tc_config(args.tc_pieces)
-    tune_ms = ctx.autotune(M, pwlib.PW_MIXED)
+    if args.fft_variant is None and args.fft_batch_mb is None:
+        tune_ms = ctx.autotune(M, pwlib.PW_MIXED)
+    else:   # pinned (profiling runs: the autotuner's timings are meaningless under ncu)
+        tune_ms = None
+        ctx.fft_config(pwlib.PW_MIXED, batch_bytes=None if args.fft_batch_mb is None else args.fft_batch_mb << 20,
+                       variant=args.fft_variant)
     fft_cfg = ctx.fft_config(pwlib.PW_MIXED)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
     Y32 = torch.empty_like(Y0_32)
