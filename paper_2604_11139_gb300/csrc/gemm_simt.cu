@@ -30,16 +30,28 @@ __device__ __forceinline__ void epi_apply(const Epi<T>& e, int m, int n, cplx<T>
 
 constexpr int BM = 64, BN = 64, BK = 16;
 
+// row and column of the lth tile on or below the diagonal (row-major order of the lower triangle)
+__device__ __forceinline__ void lower_tile(int l, int& bi, int& bj) {
+  int r = 0;
+  while ((r + 1) * (r + 2) / 2 <= l) ++r;
+  bi = r;
+  bj = l - r * (r + 1) / 2;
+}
+
 template <typename T, int TA, int TB>
 __global__ void __launch_bounds__(256) k_cgemm(int M, int N, int K, const cplx<T>* __restrict__ A, int64_t lda,
                                                const cplx<T>* __restrict__ B, int64_t ldb, Epi<T> epi,
-                                               int kchunk, cplx<T>* __restrict__ ws) {
+                                               int kchunk, cplx<T>* __restrict__ ws, int tri) {
   using C = cplx<T>;
   __shared__ C As[BK][BM + 1];
   __shared__ C Bs[BK][BN + 1];
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
-  const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
-  const int kb = blockIdx.z * kchunk, ke = min(K, kb + kchunk);
+  int bi = blockIdx.x, bj = blockIdx.y;
+  if (tri == GEMM_LOWER_OUT) lower_tile(blockIdx.x, bi, bj);
+  const int m0 = bi * BM, n0 = bj * BN;
+  const int kb = blockIdx.z * kchunk;
+  int ke = min(K, kb + kchunk);
+  if (tri == GEMM_B_UPPER) ke = min(ke, n0 + BN);  // op(B)[k][n] = 0 for k > n
   C acc[4][4];
 #pragma unroll
   for (int i = 0; i < 4; ++i)
@@ -107,21 +119,101 @@ __global__ void __launch_bounds__(256) k_cgemm(int M, int N, int K, const cplx<T
 }
 
 template <typename T>
-__global__ void k_splitk_reduce(int M, int N, int nsplit, const cplx<T>* __restrict__ ws, Epi<T> epi) {
+__global__ void k_splitk_reduce(int M, int N, int nsplit, const cplx<T>* __restrict__ ws, Epi<T> epi, int tri) {
   using C = cplx<T>;
   const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (idx >= (int64_t)M * N) return;
+  const int m = (int)(idx % M), n = (int)(idx / M);
+  if (tri == GEMM_LOWER_OUT && m / BM < n / BN) return;  // tile above the diagonal: never computed
   C s = czero<C>();
   for (int z = 0; z < nsplit; ++z) s = cadd(s, ws[z * (int64_t)M * N + idx]);
-  const int m = (int)(idx % M), n = (int)(idx / M);
   epi_apply<T>(epi, m, n, s);
+}
+
+// Matrix-vector forms (N <= GEMV_MAXN columns of op(B), B as stored): a 64-wide output tile would
+// spend 64 / N times the arithmetic, so these read A once at memory speed instead.
+constexpr int GEMV_MAXN = 4;
+
+// out[m][j] = sum_k conj(A[k][m]) B[k][j]: one CTA per m, the K loop strided over its threads
+template <typename T>
+__global__ void __launch_bounds__(256) k_cgemv_t(int M, int N, int K, const cplx<T>* __restrict__ A, int64_t lda,
+                                                 const cplx<T>* __restrict__ B, int64_t ldb, Epi<T> epi) {
+  using C = cplx<T>;
+  __shared__ C red[8][GEMV_MAXN];
+  const int m = blockIdx.x;
+  C acc[GEMV_MAXN];
+#pragma unroll
+  for (int j = 0; j < GEMV_MAXN; ++j) acc[j] = czero<C>();
+  const C* a = A + (int64_t)m * lda;
+  for (int k = threadIdx.x; k < K; k += 256) {
+    const C x = a[k];
+#pragma unroll
+    for (int j = 0; j < GEMV_MAXN; ++j)
+      if (j < N) {
+        const C b = B[k + (int64_t)j * ldb];
+        acc[j].x = fma(x.x, b.x, acc[j].x);
+        acc[j].x = fma(x.y, b.y, acc[j].x);
+        acc[j].y = fma(x.x, b.y, acc[j].y);
+        acc[j].y = fma(-x.y, b.x, acc[j].y);
+      }
+  }
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+  for (int j = 0; j < GEMV_MAXN; ++j) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      acc[j].x += __shfl_xor_sync(0xffffffffu, acc[j].x, o);
+      acc[j].y += __shfl_xor_sync(0xffffffffu, acc[j].y, o);
+    }
+    if (lane == 0) red[w][j] = acc[j];
+  }
+  __syncthreads();
+  if (threadIdx.x < N) {
+    const int j = threadIdx.x;
+    C s = czero<C>();
+    for (int q = 0; q < 8; ++q) s = cadd(s, red[q][j]);
+    epi_apply<T>(epi, m, j, s);
+  }
+}
+
+// out[i][j] = sum_k A[i][k] B[k][j]: one thread per row i, B's few columns broadcast
+template <typename T>
+__global__ void __launch_bounds__(256) k_cgemv_n(int M, int N, int K, const cplx<T>* __restrict__ A, int64_t lda,
+                                                 const cplx<T>* __restrict__ B, int64_t ldb, Epi<T> epi) {
+  using C = cplx<T>;
+  const int i = blockIdx.x * 256 + threadIdx.x;
+  if (i >= M) return;
+  C acc[GEMV_MAXN];
+#pragma unroll
+  for (int j = 0; j < GEMV_MAXN; ++j) acc[j] = czero<C>();
+  for (int k = 0; k < K; ++k) {
+    const C x = A[i + (int64_t)k * lda];
+#pragma unroll
+    for (int j = 0; j < GEMV_MAXN; ++j)
+      if (j < N) {
+        const C b = B[k + (int64_t)j * ldb];
+        acc[j].x = fma(x.x, b.x, acc[j].x);
+        acc[j].x = fma(-x.y, b.y, acc[j].x);
+        acc[j].y = fma(x.x, b.y, acc[j].y);
+        acc[j].y = fma(x.y, b.x, acc[j].y);
+      }
+  }
+  for (int j = 0; j < N; ++j) epi_apply<T>(epi, i, j, acc[j]);
 }
 
 template <typename T>
 cudaError_t launch_cgemm(int ta, int tb, int M, int N, int K, const cplx<T>* A, int64_t lda,
                          const cplx<T>* B, int64_t ldb, const Epi<T>& epi, int nsplit, cplx<T>* ws,
-                         cudaStream_t st) {
+                         cudaStream_t st, int tri) {
   if (M <= 0 || N <= 0) return cudaSuccess;
+  if (tri == GEMM_LOWER_OUT && M != N) return cudaErrorInvalidValue;
+  if (tri == GEMM_B_UPPER && N > K) return cudaErrorInvalidValue;
+  if (N <= GEMV_MAXN && tb == 0 && tri == GEMM_FULL && K > 0) {
+    if (ta == 1) k_cgemv_t<T><<<M, 256, 0, st>>>(M, N, K, A, lda, B, ldb, epi);
+    else k_cgemv_n<T><<<(M + 255) / 256, 256, 0, st>>>(M, N, K, A, lda, B, ldb, epi);
+    count_launch();
+    return cudaGetLastError();
+  }
   if (K <= 0) nsplit = 1;
   if (nsplit < 1) nsplit = 1;
   int kchunk = (K + nsplit - 1) / nsplit;
@@ -129,15 +221,17 @@ cudaError_t launch_cgemm(int ta, int tb, int M, int N, int K, const cplx<T>* A, 
   if (kchunk <= 0) kchunk = BK;
   nsplit = (K + kchunk - 1) / kchunk;
   if (nsplit < 1) nsplit = 1;
-  dim3 grid((M + BM - 1) / BM, (N + BN - 1) / BN, nsplit);
-  if (ta == 0 && tb == 0) k_cgemm<T, 0, 0><<<grid, 256, 0, st>>>(M, N, K, A, lda, B, ldb, epi, kchunk, ws);
-  else if (ta == 1 && tb == 0) k_cgemm<T, 1, 0><<<grid, 256, 0, st>>>(M, N, K, A, lda, B, ldb, epi, kchunk, ws);
-  else if (ta == 0 && tb == 1) k_cgemm<T, 0, 1><<<grid, 256, 0, st>>>(M, N, K, A, lda, B, ldb, epi, kchunk, ws);
-  else k_cgemm<T, 1, 1><<<grid, 256, 0, st>>>(M, N, K, A, lda, B, ldb, epi, kchunk, ws);
+  const int tm = (M + BM - 1) / BM, tn = (N + BN - 1) / BN;
+  dim3 grid(tm, tn, nsplit);
+  if (tri == GEMM_LOWER_OUT) grid = dim3(tm * (tm + 1) / 2, 1, nsplit);
+  if (ta == 0 && tb == 0) k_cgemm<T, 0, 0><<<grid, 256, 0, st>>>(M, N, K, A, lda, B, ldb, epi, kchunk, ws, tri);
+  else if (ta == 1 && tb == 0) k_cgemm<T, 1, 0><<<grid, 256, 0, st>>>(M, N, K, A, lda, B, ldb, epi, kchunk, ws, tri);
+  else if (ta == 0 && tb == 1) k_cgemm<T, 0, 1><<<grid, 256, 0, st>>>(M, N, K, A, lda, B, ldb, epi, kchunk, ws, tri);
+  else k_cgemm<T, 1, 1><<<grid, 256, 0, st>>>(M, N, K, A, lda, B, ldb, epi, kchunk, ws, tri);
   count_launch();
   if (nsplit > 1) {
     const int64_t tot = (int64_t)M * N;
-    k_splitk_reduce<T><<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(M, N, nsplit, ws, epi); count_launch();
+    k_splitk_reduce<T><<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(M, N, nsplit, ws, epi, tri); count_launch();
   }
   return cudaGetLastError();
 }
@@ -172,9 +266,9 @@ cudaError_t launch_dblock(int nproj, int nband, const T* D, const int* blk0, con
 }
 
 template cudaError_t launch_cgemm<double>(int, int, int, int, int, const double2*, int64_t, const double2*,
-                                          int64_t, const Epi<double>&, int, double2*, cudaStream_t);
+                                          int64_t, const Epi<double>&, int, double2*, cudaStream_t, int);
 template cudaError_t launch_cgemm<float>(int, int, int, int, int, const float2*, int64_t, const float2*,
-                                         int64_t, const Epi<float>&, int, float2*, cudaStream_t);
+                                         int64_t, const Epi<float>&, int, float2*, cudaStream_t, int);
 template cudaError_t launch_dblock<double>(int, int, const double*, const int*, const int*, const double2*,
                                            int64_t, double2*, int64_t, cudaStream_t);
 template cudaError_t launch_dblock<float>(int, int, const float*, const int*, const int*, const float2*,

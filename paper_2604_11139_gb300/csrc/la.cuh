@@ -6,6 +6,8 @@ namespace pw {
 typedef int (*ApplyFn)(void* ctx, const double2* v, double2* w);
 
 cudaError_t la_herm_sym(double2* A, int64_t lda, int n, cudaStream_t st);
+// A[j][i] = conj(A[i][j]) for i > j, real diagonal (the lower triangle is kept)
+cudaError_t la_herm_from_lower(double2* A, int64_t lda, int n, cudaStream_t st);
 // lower Cholesky in place; *flag set to 1 (device) if a pivot is not positive
 cudaError_t la_cholesky(double2* A, int64_t lda, int n, int* flag, cudaStream_t st);
 cudaError_t la_zero_upper(double2* A, int64_t lda, int n, cudaStream_t st);

@@ -29,6 +29,21 @@ cudaError_t la_herm_sym(double2* A, int64_t lda, int n, cudaStream_t st) {
   return cudaGetLastError();
 }
 
+// upper triangle from the lower one (a Gram matrix of which only the lower tiles were computed)
+__global__ void k_herm_from_lower(double2* A, int64_t lda, int n) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  if (i >= n || j >= n || i < j) return;
+  if (i == j) { A[i + i * lda].y = 0.0; return; }
+  A[j + i * lda] = cconj(A[i + j * lda]);
+}
+
+cudaError_t la_herm_from_lower(double2* A, int64_t lda, int n, cudaStream_t st) {
+  dim3 b(16, 16), g((n + 15) / 16, (n + 15) / 16);
+  k_herm_from_lower<<<g, b, 0, st>>>(A, lda, n); count_launch();
+  return cudaGetLastError();
+}
+
 // ---- blocked Cholesky A = L L^dagger (lower, in place; strict upper part zeroed) ---
 constexpr int NB = 32;
 
@@ -214,10 +229,11 @@ __device__ __forceinline__ Rot jac_rot(const double2* A, int n, int p, int q) {
 }
 
 // the rotation of every pair of round t, computed once (FP64 square roots and divisions
-// are the expensive part of a round)
+// are the expensive part of a round).  One pair per CTA of one warp: FP64 issues at a small
+// fraction of the FP32 rate, so the pairs are spread over the SMs rather than queued on one.
 __global__ void k_jacobi_rot(const double2* __restrict__ A, int n, int np, int t, Rot* __restrict__ rot) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= np / 2) return;
+  const int i = blockIdx.x;
+  if (i >= np / 2 || threadIdx.x != 0) return;
   int p, q;
   rr_pair(t, i, np, p, q);
   rot[i] = jac_rot(A, n, p, q);
@@ -341,7 +357,7 @@ int la_jacobi_eigh(double2* A, int n, double2* U, double* eig, double2* ws, doub
   double prev_off = INFINITY;
   while (!conv && sweep < max_sweeps) {
     for (int t = 0; t < np - 1; ++t) {
-      k_jacobi_rot<<<(npair + 127) / 128, 128, 0, st>>>(Acur, n, np, t, rot); count_launch();
+      k_jacobi_rot<<<npair, 32, 0, st>>>(Acur, n, np, t, rot); count_launch();
       k_jacobi_round<<<nblk, 256, 0, st>>>(Acur, Anext, Vcur, Vnext, n, np, t, rot); count_launch();
       double2* x = Acur; Acur = Anext; Anext = x;
       x = Vcur; Vcur = Vnext; Vnext = x;

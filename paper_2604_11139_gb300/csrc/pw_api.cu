@@ -200,12 +200,14 @@ int upload(pw_ctx* ctx, X** dst, const X* src, size_t n) {
   return PW_OK;
 }
 
-int nsplit_for(int m, int n, int k) {
-  const int tiles = ((m + 63) / 64) * ((n + 63) / 64);
-  int s = (2 * 152 + tiles - 1) / tiles;
+// K splits for `tiles` output tiles: the SIMT GEMM holds 2 CTAs per SM (128 registers x 256
+// threads), so tiles x splits stays within one wave of 2 x 152 CTAs
+int nsplit_tiles(int tiles, int k) {
+  int s = (2 * 152) / tiles;
   s = std::min(s, std::max(1, k / 512));
   return std::max(1, std::min(s, 64));
 }
+int nsplit_for(int m, int n, int k) { return nsplit_tiles(((m + 63) / 64) * ((n + 63) / 64), k); }
 
 template <typename T> struct Prec;
 template <> struct Prec<double> {
@@ -673,15 +675,24 @@ int recur_step(pw_ctx* ctx, const cplx<T>* cur, int64_t ldc, const cplx<T>* prev
 // ---------------------------------------------------------------------------
 // S-Ortho (Alg. 9) and Rayleigh-Ritz (Alg. 5), FP64
 // ---------------------------------------------------------------------------
+// G = Y^H B for a Hermitian result (B = S Y or H Y): only the tiles on and below the diagonal are
+// computed; the upper triangle is the conjugate of the lower one
+int gram_herm(pw_ctx* ctx, const double2* Y, int64_t ldy, const double2* B, int64_t ldb, int m, double2* G) {
+  const cudaStream_t st = ctx->stream;
+  const int tl = (m + 63) / 64;
+  const int ns = nsplit_tiles(tl * (tl + 1) / 2, ctx->npw);
+  WS(spl, double2, WS_SPLIT, (size_t)ns * m * m);
+  CU_TRY(launch_cgemm<double>(1, 0, m, m, ctx->npw, Y, ldy, B, ldb, epi<double>(EPI_STORE, G, m), ns, spl, st,
+                              GEMM_LOWER_OUT), "gram");
+  CU_TRY(la_herm_from_lower(G, m, m, st), "gram Hermitian");
+  return PW_OK;
+}
+
 // G = Y^H SY (herm.), L = chol(G), Linv = L^-1.  flag set on failure.
 int gram_chol(pw_ctx* ctx, const double2* Y, int64_t ldy, const double2* SY, int64_t lds, int m, double2* G,
               double2* Linv, double2* tmp, int* flag) {
   const cudaStream_t st = ctx->stream;
-  const int ns = nsplit_for(m, m, ctx->npw);
-  WS(spl, double2, WS_SPLIT, (size_t)ns * m * m);
-  CU_TRY(launch_cgemm<double>(1, 0, m, m, ctx->npw, Y, ldy, SY, lds, epi<double>(EPI_STORE, G, m), ns, spl, st),
-         "gram");
-  CU_TRY(la_herm_sym(G, m, m, st), "gram sym");
+  PW_TRY(gram_herm(ctx, Y, ldy, SY, lds, m, G));
   CU_TRY(la_cholesky(G, m, m, flag, st), "cholesky");
   CU_TRY(la_trinv_lower(G, m, m, Linv, m, tmp, st), "triangular inverse");
   return PW_OK;
@@ -697,6 +708,11 @@ int check_flag(pw_ctx* ctx, int* flag_dev, const char* what) {
 
 // q_out (ld npw): the S-orthonormal block Q before the rotation; x_out (m x m): the rotation X
 // (Psi = Q X); eig_dev_out (device, m): the Ritz values.  Each may be NULL.
+//
+// S-Ortho (Alg. 9) is Cholesky-QR in the S metric.  One pass leaves the block S-orthonormal to
+// within about cond(Y)^2 * eps; the second pass is the Cholesky factor of the Rayleigh-Ritz overlap
+// S_Psi itself (Alg. 5 reduces H_Psi with it), so the block is not rotated twice before H is applied:
+// Psi = Y1 X with X = L^{-dagger} U, and Q = Y1 L^{-dagger} is formed only when it is asked for.
 int rr_impl(pw_ctx* ctx, double2* Y, int64_t ldy, int m, double2* hpsi_out, double* eig_h, double* resid_h,
             double2* q_out = nullptr, double2* x_out = nullptr, double* eig_dev_out = nullptr) {
   PW_TRY(check_tc_flag(ctx));
@@ -717,8 +733,8 @@ int rr_impl(pw_ctx* ctx, double2* Y, int64_t ldy, int m, double2* hpsi_out, doub
   double* norms = eig + 2 * m;
   double* resid = eig + m;
   CU_TRY(cudaMemsetAsync(scal, 0, 16 * sizeof(int), st), "flag reset");
-  // two passes of Cholesky-QR in the S metric
-  for (int rep = 0; rep < 2; ++rep) {
+  // first Cholesky-QR pass in the S metric: Y <- Y L^{-dagger}
+  {
     const double2* SY = Y;
     int64_t lds = ldy;
     if (ctx->has_q) {
@@ -727,26 +743,19 @@ int rr_impl(pw_ctx* ctx, double2* Y, int64_t ldy, int m, double2* hpsi_out, doub
       lds = npw;
     }
     PW_TRY(gram_chol(ctx, Y, ldy, SY, lds, m, G, Linv, tmp, scal));
-    // Y <- Y L^{-dagger}
-    CU_TRY(launch_cgemm<double>(0, 1, npw, m, m, Y, ldy, Linv, m, epi<double>(EPI_STORE, ROT, npw), 1, nullptr, st),
-           "s-ortho rotate");
+    CU_TRY(launch_cgemm<double>(0, 1, npw, m, m, Y, ldy, Linv, m, epi<double>(EPI_STORE, ROT, npw), 1, nullptr, st,
+                                GEMM_B_UPPER), "s-ortho rotate");
     CU_TRY(cudaMemcpy2DAsync(Y, sizeof(double2) * ldy, ROT, sizeof(double2) * npw, sizeof(double2) * npw, m,
                              cudaMemcpyDeviceToDevice, st), "s-ortho copy");
   }
   PW_TRY(check_flag(ctx, scal, "S-Ortho Cholesky"));
-  if (q_out)
-    CU_TRY(cudaMemcpy2DAsync(q_out, sizeof(double2) * npw, Y, sizeof(double2) * ldy, sizeof(double2) * npw, m,
-                             cudaMemcpyDeviceToDevice, st), "copy Q");
   // H Psi, S Psi
   PW_TRY(apply_impl<double>(ctx, Y, ldy, m, HY, ctx->has_q ? SYb : nullptr, npw));
   const double2* SY = ctx->has_q ? SYb : Y;
   const int64_t lds = ctx->has_q ? npw : ldy;
-  const int ns = nsplit_for(m, m, npw);
-  WS(spl, double2, WS_SPLIT, (size_t)ns * m * m);
   // H_Psi = Psi^dagger (H Psi) -> G2
-  CU_TRY(launch_cgemm<double>(1, 0, m, m, npw, Y, ldy, HY, npw, epi<double>(EPI_STORE, G2, m), ns, spl, st), "H gram");
-  CU_TRY(la_herm_sym(G2, m, m, st), "H gram sym");
-  // S_Psi -> G, Cholesky, Linv
+  PW_TRY(gram_herm(ctx, Y, ldy, HY, npw, m, G2));
+  // S_Psi -> G, Cholesky (the second S-Ortho pass), Linv
   PW_TRY(gram_chol(ctx, Y, ldy, SY, lds, m, G, Linv, tmp, scal));
   // Cm = Linv H_Psi Linv^dagger
   CU_TRY(launch_cgemm<double>(0, 1, m, m, m, G2, m, Linv, m, epi<double>(EPI_STORE, tmp, m), 1, nullptr, st), "reduce 1");
@@ -758,7 +767,10 @@ int rr_impl(pw_ctx* ctx, double2* Y, int64_t ldy, int m, double2* hpsi_out, doub
   ctx->last_sweeps = sweeps;
   // X = Linv^dagger U  -> tmp
   CU_TRY(launch_cgemm<double>(1, 0, m, m, m, Linv, m, U, m, epi<double>(EPI_STORE, tmp, m), 1, nullptr, st), "back-transform");
-  if (x_out) CU_TRY(cudaMemcpyAsync(x_out, tmp, sizeof(double2) * m * m, cudaMemcpyDeviceToDevice, st), "copy X");
+  if (q_out)
+    CU_TRY(launch_cgemm<double>(0, 1, npw, m, m, Y, ldy, Linv, m, epi<double>(EPI_STORE, q_out, npw), 1, nullptr, st,
+                                GEMM_B_UPPER), "Q");
+  if (x_out) CU_TRY(cudaMemcpyAsync(x_out, U, sizeof(double2) * m * m, cudaMemcpyDeviceToDevice, st), "copy X");
   if (eig_dev_out)
     CU_TRY(cudaMemcpyAsync(eig_dev_out, eig, sizeof(double) * m, cudaMemcpyDeviceToDevice, st), "copy eig");
   // rotate Y, HY, SY

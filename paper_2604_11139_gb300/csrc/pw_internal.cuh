@@ -212,12 +212,19 @@ cudaError_t launch_density(const FftPlan& plan, const cplx<T>* tw, const SphereD
                            const cplx<T>* a, const cplx<T>* b, int64_t ld, int nband, const T* w_dev,
                            double* out_perm, cplx<T>* hb, int band_batch, cudaStream_t st);
 
+// Structure a GEMM may skip work for:
+//  GEMM_LOWER_OUT: M == N and only the 64 x 64 output tiles on or below the diagonal are computed
+//    and stored (a Hermitian Gram matrix; the tiles above the diagonal are left as they were);
+//  GEMM_B_UPPER: op(B)[k][n] == 0 for k > n (B = L^dagger with L lower triangular), so the K range
+//    of an output tile stops at its last column (N <= K).
+enum { GEMM_FULL = 0, GEMM_LOWER_OUT = 1, GEMM_B_UPPER = 2 };
+
 // op(A) is M x K, op(B) is K x N; ta/tb: 0 = as stored (column-major), 1 = conjugate transpose.
 // nsplit > 1 splits K and reduces through `ws` (nsplit*M*N complex) before the epilogue.
 template <typename T>
 cudaError_t launch_cgemm(int ta, int tb, int M, int N, int K, const cplx<T>* A, int64_t lda,
                          const cplx<T>* B, int64_t ldb, const Epi<T>& epi, int nsplit, cplx<T>* ws,
-                         cudaStream_t st);
+                         cudaStream_t st, int tri = GEMM_FULL);
 
 // real block-diagonal (or dense) D times complex C: Z = D C (nproj x nband)
 template <typename T>

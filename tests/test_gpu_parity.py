@@ -328,6 +328,47 @@ def test_full_size_other_boxes_sampled_bands(key):
             assert rel(h32.cpu().numpy().astype(np.complex128), ref).max() < 1e-5
 
 
+@pytest.mark.parametrize("key", ["cubic16_q", "ortho_k_ragged"])
+def test_few_bands_matrix_vector_forms(key):
+    """1-4 bands take the matrix-vector forms of the projector products (P^dagger psi reads P
+    once per column, P Z one row per thread, the recurrence epilogue included); 5 bands the
+    tiled GEMM."""
+    prob, ham, ctx = setup(key)
+    with ctx:
+        a, b = -0.5, 2.0 * prob.ecut + 3.0
+        for nb in (1, 2, 3, 4, 5):
+            psi = W.random_block(110 + nb, ctx.npw, nb)
+            t = to_dev(psi, ld=ctx.npw + 2)
+            h = torch.zeros_like(t)
+            ctx.hamiltonian_apply(t, h)
+            torch.cuda.synchronize()
+            assert rel(h.cpu().numpy()[:, :ctx.npw], ham.apply_h(psi)).max() < 1e-11, nb
+            ctx.chebyshev_filter(t, 3, a, b)
+            torch.cuda.synchronize()
+            ref = O.chebyshev_filter(ham.apply_a, psi, 3, a, b)
+            assert rel(t.cpu().numpy()[:, :ctx.npw], ref).max() < 1e-10, nb
+
+
+def test_rayleigh_ritz_ill_conditioned_block():
+    """Columns scaled over four decades and mixed (condition number ~1e4, as after a filter):
+    the Ritz values of the span do not depend on the basis, and the single Cholesky-QR pass
+    before the Rayleigh-Ritz reduction keeps them at the FP64 level."""
+    prob, ham, ctx = setup("tiny_24_aliasing")
+    with ctx:
+        psi = W.random_block(120, ctx.npw, prob.nband)
+        mix = np.linalg.qr(W.random_block(121, prob.nband, prob.nband))[0]
+        Y = (psi.T @ np.diag(np.geomspace(1.0, 1e-4, prob.nband)) @ mix).T
+        t = to_dev(Y)
+        eig, _ = ctx.rayleigh_ritz(t)
+        y = psi
+        for _ in range(2):
+            y, _ = O.s_ortho(y, ham.apply_s(y))
+        lam, *_ = O.rayleigh_ritz(y, ham.apply_h(y), ham.apply_s(y))
+        np.testing.assert_allclose(eig, lam, atol=1e-9, rtol=0)
+        R = t.cpu().numpy()
+        np.testing.assert_allclose(R.conj() @ R.T, np.eye(prob.nband), atol=1e-11)
+
+
 def test_rayleigh_ritz_many_bands():
     """Jacobi eigensolver on a 200 x 200 reduced problem (odd pairing rounds, many sweeps)."""
     prob = W.make_problem("tiny_gamma_fp64", nband=200)
