@@ -29,15 +29,45 @@
 
 namespace pw {
 
+// ---- butterfly arithmetic ---------------------------------------------------------
+// complex64 butterflies use the paired FP32 instructions of sm_100-class SMs (one add,
+// multiply or fused multiply-add for both halves of a float2, each half rounded to nearest
+// as the scalar instruction would); complex128 keeps the scalar forms.
+__device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
+__device__ __forceinline__ double2 bf_add(double2 a, double2 b) { return cadd(a, b); }
+__device__ __forceinline__ float2 bf_add(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ double2 bf_sub(double2 a, double2 b) { return csub(a, b); }
+__device__ __forceinline__ float2 bf_sub(float2 a, float2 b) { return __ffma2_rn(b, f2(-1.f, -1.f), a); }
+__device__ __forceinline__ double2 bf_scale(double2 a, double s) { return cscale(a, s); }
+__device__ __forceinline__ float2 bf_scale(float2 a, float s) { return __fmul2_rn(a, f2(s, s)); }
+// a + s b
+__device__ __forceinline__ double2 bf_axpy(double2 a, double s, double2 b) {
+  return make_double2(fma(s, b.x, a.x), fma(s, b.y, a.y));
+}
+__device__ __forceinline__ float2 bf_axpy(float2 a, float s, float2 b) { return __ffma2_rn(b, f2(s, s), a); }
+// a + (S i) s b  and  a - (S i) s b
+template <int S> __device__ __forceinline__ double2 bf_add_muli(double2 a, double2 b, double s = 1.0) {
+  return make_double2(fma(-S * s, b.y, a.x), fma(S * s, b.x, a.y));
+}
+template <int S> __device__ __forceinline__ float2 bf_add_muli(float2 a, float2 b, float s = 1.f) {
+  return __ffma2_rn(f2(b.y, b.x), f2(-S * s, S * s), a);
+}
+template <int S> __device__ __forceinline__ double2 bf_sub_muli(double2 a, double2 b, double s = 1.0) {
+  return make_double2(fma(S * s, b.y, a.x), fma(-S * s, b.x, a.y));
+}
+template <int S> __device__ __forceinline__ float2 bf_sub_muli(float2 a, float2 b, float s = 1.f) {
+  return __ffma2_rn(f2(b.y, b.x), f2(S * s, -S * s), a);
+}
+
 // ---- small DFTs: y_m = sum_k x_k exp(S 2 pi i k m / R) -------------------------
 template <typename C, int S> __device__ __forceinline__ void dft2(C& a, C& b) {
-  C t = a; a = cadd(t, b); b = csub(t, b);
+  C t = a; a = bf_add(t, b); b = bf_sub(t, b);
 }
 template <typename C, int S> __device__ __forceinline__ void dft4(C* x) {
-  C s02 = cadd(x[0], x[2]), d02 = csub(x[0], x[2]);
-  C s13 = cadd(x[1], x[3]), d13 = cmuli<S>(csub(x[1], x[3]));
-  x[0] = cadd(s02, s13); x[2] = csub(s02, s13);
-  x[1] = cadd(d02, d13); x[3] = csub(d02, d13);
+  C s02 = bf_add(x[0], x[2]), d02 = bf_sub(x[0], x[2]);
+  C s13 = bf_add(x[1], x[3]), d13 = bf_sub(x[1], x[3]);
+  x[0] = bf_add(s02, s13); x[2] = bf_sub(s02, s13);
+  x[1] = bf_add_muli<S>(d02, d13); x[3] = bf_sub_muli<S>(d02, d13);
 }
 template <typename C, int S> __device__ __forceinline__ void dft8(C* x) {
   using R = decltype(C{}.x);
@@ -45,22 +75,23 @@ template <typename C, int S> __device__ __forceinline__ void dft8(C* x) {
   C e[4] = {x[0], x[2], x[4], x[6]};
   C o[4] = {x[1], x[3], x[5], x[7]};
   dft4<C, S>(e); dft4<C, S>(o);
-  // o[m] *= w8^m, w8 = exp(S i pi/4)
-  C o1 = o[1]; o[1] = mk<C>(h * (o1.x - S * o1.y), h * (o1.y + S * o1.x));
-  o[2] = cmuli<S>(o[2]);
-  C o3 = o[3]; o[3] = mk<C>(h * (-o3.x - S * o3.y), h * (-o3.y + S * o3.x));
-#pragma unroll
-  for (int m = 0; m < 4; ++m) { x[m] = cadd(e[m], o[m]); x[m + 4] = csub(e[m], o[m]); }
+  // o[m] *= w8^m, w8 = exp(S i pi/4): w8 = h (1 + S i), w8^3 = h (-1 + S i)
+  const C o1 = bf_scale(bf_add_muli<S>(o[1], o[1]), h);
+  const C o3 = bf_scale(bf_sub_muli<S>(o[3], o[3]), -h);
+  x[0] = bf_add(e[0], o[0]); x[4] = bf_sub(e[0], o[0]);
+  x[1] = bf_add(e[1], o1); x[5] = bf_sub(e[1], o1);
+  x[2] = bf_add_muli<S>(e[2], o[2]); x[6] = bf_sub_muli<S>(e[2], o[2]);
+  x[3] = bf_add(e[3], o3); x[7] = bf_sub(e[3], o3);
 }
 template <typename C, int S> __device__ __forceinline__ void dft3(C* x) {
   using R = decltype(C{}.x);
   const R s3 = (R)0.86602540378443864676372317075294;  // sin(pi/3)
-  C t = cadd(x[1], x[2]);
-  C d = cmuli<S>(csub(x[1], x[2]));
-  C m = csub(x[0], cscale(t, (R)0.5));
-  x[0] = cadd(x[0], t);
-  x[1] = cadd(m, cscale(d, s3));
-  x[2] = csub(m, cscale(d, s3));
+  C t = bf_add(x[1], x[2]);
+  C d = bf_sub(x[1], x[2]);
+  C m = bf_axpy(x[0], (R)-0.5, t);
+  x[0] = bf_add(x[0], t);
+  x[1] = bf_add_muli<S>(m, d, s3);
+  x[2] = bf_sub_muli<S>(m, d, s3);
 }
 template <typename C, int S> __device__ __forceinline__ void dft5(C* x) {
   using R = decltype(C{}.x);
@@ -68,15 +99,15 @@ template <typename C, int S> __device__ __forceinline__ void dft5(C* x) {
   const R c2 = (R)-0.80901699437494742410229341718282;  // cos(4pi/5)
   const R s1 = (R)0.95105651629515357211643933337938;   // sin(2pi/5)
   const R s2 = (R)0.58778525229247312916870595463907;   // sin(4pi/5)
-  C t1 = cadd(x[1], x[4]), t2 = cadd(x[2], x[3]);
-  C d1 = csub(x[1], x[4]), d2 = csub(x[2], x[3]);
-  C a1 = cadd(x[0], cadd(cscale(t1, c1), cscale(t2, c2)));
-  C a2 = cadd(x[0], cadd(cscale(t1, c2), cscale(t2, c1)));
-  C b1 = cmuli<S>(cadd(cscale(d1, s1), cscale(d2, s2)));
-  C b2 = cmuli<S>(csub(cscale(d1, s2), cscale(d2, s1)));
-  x[0] = cadd(x[0], cadd(t1, t2));
-  x[1] = cadd(a1, b1); x[4] = csub(a1, b1);
-  x[2] = cadd(a2, b2); x[3] = csub(a2, b2);
+  C t1 = bf_add(x[1], x[4]), t2 = bf_add(x[2], x[3]);
+  C d1 = bf_sub(x[1], x[4]), d2 = bf_sub(x[2], x[3]);
+  C a1 = bf_add(x[0], bf_axpy(bf_scale(t1, c1), c2, t2));
+  C a2 = bf_add(x[0], bf_axpy(bf_scale(t1, c2), c1, t2));
+  C u1 = bf_axpy(bf_scale(d1, s1), s2, d2);    // b1 = (S i) u1
+  C u2 = bf_axpy(bf_scale(d1, s2), -s1, d2);   // b2 = (S i) u2
+  x[0] = bf_add(x[0], bf_add(t1, t2));
+  x[1] = bf_add_muli<S>(a1, u1); x[4] = bf_sub_muli<S>(a1, u1);
+  x[2] = bf_add_muli<S>(a2, u2); x[3] = bf_sub_muli<S>(a2, u2);
 }
 // exp(-2 pi i m / R) for the composite in-register radices, filled by fft_set_constants
 // (host cos/sin in double).  Offsets: R=6: 0, 9: 6, 10: 15, 12: 25, 15: 37, 16: 52.
