@@ -135,31 +135,31 @@ __global__ void k_splitk_reduce(int M, int N, int nsplit, const cplx<T>* __restr
 constexpr int GEMV_MAXN = 4;
 
 // out[m][j] = sum_k conj(A[k][m]) B[k][j]: one CTA per m, the K loop strided over its threads
-template <typename T>
-__global__ void __launch_bounds__(256) k_cgemv_t(int M, int N, int K, const cplx<T>* __restrict__ A, int64_t lda,
+template <typename T, int NB>
+__global__ void __launch_bounds__(256) k_cgemv_t(int M, int K, const cplx<T>* __restrict__ A, int64_t lda,
                                                  const cplx<T>* __restrict__ B, int64_t ldb, Epi<T> epi) {
   using C = cplx<T>;
-  __shared__ C red[8][GEMV_MAXN];
+  __shared__ C red[8][NB];
   const int m = blockIdx.x;
-  C acc[GEMV_MAXN];
+  C acc[NB];
 #pragma unroll
-  for (int j = 0; j < GEMV_MAXN; ++j) acc[j] = czero<C>();
+  for (int j = 0; j < NB; ++j) acc[j] = czero<C>();
   const C* a = A + (int64_t)m * lda;
+#pragma unroll 4
   for (int k = threadIdx.x; k < K; k += 256) {
     const C x = a[k];
 #pragma unroll
-    for (int j = 0; j < GEMV_MAXN; ++j)
-      if (j < N) {
-        const C b = B[k + (int64_t)j * ldb];
-        acc[j].x = fma(x.x, b.x, acc[j].x);
-        acc[j].x = fma(x.y, b.y, acc[j].x);
-        acc[j].y = fma(x.x, b.y, acc[j].y);
-        acc[j].y = fma(-x.y, b.x, acc[j].y);
-      }
+    for (int j = 0; j < NB; ++j) {
+      const C b = B[k + (int64_t)j * ldb];
+      acc[j].x = fma(x.x, b.x, acc[j].x);
+      acc[j].x = fma(x.y, b.y, acc[j].x);
+      acc[j].y = fma(x.x, b.y, acc[j].y);
+      acc[j].y = fma(-x.y, b.x, acc[j].y);
+    }
   }
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
 #pragma unroll
-  for (int j = 0; j < GEMV_MAXN; ++j) {
+  for (int j = 0; j < NB; ++j) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
       acc[j].x += __shfl_xor_sync(0xffffffffu, acc[j].x, o);
@@ -168,7 +168,7 @@ __global__ void __launch_bounds__(256) k_cgemv_t(int M, int N, int K, const cplx
     if (lane == 0) red[w][j] = acc[j];
   }
   __syncthreads();
-  if (threadIdx.x < N) {
+  if (threadIdx.x < NB) {
     const int j = threadIdx.x;
     C s = czero<C>();
     for (int q = 0; q < 8; ++q) s = cadd(s, red[q][j]);
@@ -176,29 +176,39 @@ __global__ void __launch_bounds__(256) k_cgemv_t(int M, int N, int K, const cplx
   }
 }
 
-// out[i][j] = sum_k A[i][k] B[k][j]: one thread per row i, B's few columns broadcast
-template <typename T>
-__global__ void __launch_bounds__(256) k_cgemv_n(int M, int N, int K, const cplx<T>* __restrict__ A, int64_t lda,
+// out[i][j] = sum_k A[i][k] B[k][j]: one thread per row i, B's few columns broadcast; the K
+// loop is unrolled so that several rows of A are in flight per thread
+template <typename T, int NB>
+__global__ void __launch_bounds__(256) k_cgemv_n(int M, int K, const cplx<T>* __restrict__ A, int64_t lda,
                                                  const cplx<T>* __restrict__ B, int64_t ldb, Epi<T> epi) {
   using C = cplx<T>;
   const int i = blockIdx.x * 256 + threadIdx.x;
   if (i >= M) return;
-  C acc[GEMV_MAXN];
+  C acc[NB];
 #pragma unroll
-  for (int j = 0; j < GEMV_MAXN; ++j) acc[j] = czero<C>();
+  for (int j = 0; j < NB; ++j) acc[j] = czero<C>();
+#pragma unroll 8
   for (int k = 0; k < K; ++k) {
     const C x = A[i + (int64_t)k * lda];
 #pragma unroll
-    for (int j = 0; j < GEMV_MAXN; ++j)
-      if (j < N) {
-        const C b = B[k + (int64_t)j * ldb];
-        acc[j].x = fma(x.x, b.x, acc[j].x);
-        acc[j].x = fma(-x.y, b.y, acc[j].x);
-        acc[j].y = fma(x.x, b.y, acc[j].y);
-        acc[j].y = fma(x.y, b.x, acc[j].y);
-      }
+    for (int j = 0; j < NB; ++j) {
+      const C b = B[k + (int64_t)j * ldb];
+      acc[j].x = fma(x.x, b.x, acc[j].x);
+      acc[j].x = fma(-x.y, b.y, acc[j].x);
+      acc[j].y = fma(x.x, b.y, acc[j].y);
+      acc[j].y = fma(x.y, b.x, acc[j].y);
+    }
   }
-  for (int j = 0; j < N; ++j) epi_apply<T>(epi, i, j, acc[j]);
+#pragma unroll
+  for (int j = 0; j < NB; ++j) epi_apply<T>(epi, i, j, acc[j]);
+}
+
+template <typename T, int NB>
+static void launch_gemv(int ta, int M, int K, const cplx<T>* A, int64_t lda, const cplx<T>* B, int64_t ldb,
+                        const Epi<T>& epi, cudaStream_t st) {
+  if (ta == 1) k_cgemv_t<T, NB><<<M, 256, 0, st>>>(M, K, A, lda, B, ldb, epi);
+  else k_cgemv_n<T, NB><<<(M + 255) / 256, 256, 0, st>>>(M, K, A, lda, B, ldb, epi);
+  count_launch();
 }
 
 template <typename T>
@@ -209,9 +219,12 @@ cudaError_t launch_cgemm(int ta, int tb, int M, int N, int K, const cplx<T>* A, 
   if (tri == GEMM_LOWER_OUT && M != N) return cudaErrorInvalidValue;
   if (tri == GEMM_B_UPPER && N > K) return cudaErrorInvalidValue;
   if (N <= GEMV_MAXN && tb == 0 && tri == GEMM_FULL && K > 0) {
-    if (ta == 1) k_cgemv_t<T><<<M, 256, 0, st>>>(M, N, K, A, lda, B, ldb, epi);
-    else k_cgemv_n<T><<<(M + 255) / 256, 256, 0, st>>>(M, N, K, A, lda, B, ldb, epi);
-    count_launch();
+    switch (N) {
+      case 1: launch_gemv<T, 1>(ta, M, K, A, lda, B, ldb, epi, st); break;
+      case 2: launch_gemv<T, 2>(ta, M, K, A, lda, B, ldb, epi, st); break;
+      case 3: launch_gemv<T, 3>(ta, M, K, A, lda, B, ldb, epi, st); break;
+      default: launch_gemv<T, 4>(ta, M, K, A, lda, B, ldb, epi, st); break;
+    }
     return cudaGetLastError();
   }
   if (K <= 0) nsplit = 1;
