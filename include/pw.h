@@ -121,8 +121,9 @@ PW_API int pw_spectrum_bounds(pw_ctx* ctx, const void* psi, int64_t ld, int nban
 PW_API int pw_chebyshev_filter(pw_ctx* ctx, void* psi, int64_t ldpsi, int nband,
                                int degree, double a, double b, int precision);
 
-/* Rayleigh-Ritz on the complex128 block psi (Alg. 5 preceded by two S-Ortho
- * passes, Alg. 9), all FP64: psi <- S-orthonormalised Ritz vectors, eig (host,
+/* Rayleigh-Ritz on the complex128 block psi (Alg. 5 preceded by S-Ortho, Alg. 9:
+ * one Cholesky-QR pass in the S metric, the Cholesky reduction inside Alg. 5 being the
+ * second), all FP64: psi <- S-orthonormalised Ritz vectors, eig (host,
  * nband, ascending) <- Ritz values, resid (host, nband, may be NULL) <-
  * ||H psi_i - lambda_i S psi_i||.  hpsi (may be NULL, ld = ldpsi) receives H psi.
  * Returns PW_ENOTSPD if the block is numerically rank deficient. */
