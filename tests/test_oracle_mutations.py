@@ -1,0 +1,89 @@
+"""Planted mistakes in the FP64 oracle, each caught by one of its pins.
+
+Every case replaces one piece of the oracle (on the CPU, through monkeypatch) by a
+plausible wrong version -- a dropped term, a wrong sign, a missing conjugate, a wrong
+coefficient -- and runs the pin that must fail.  A pin that still passed would mean the
+oracle could carry that mistake unnoticed.
+"""
+import numpy as np
+import pytest
+import scipy.linalg
+
+import tests.test_oracle_pins as pins
+from oracle import pw_oracle as O
+
+
+def _apply_h_without_kinetic(self, C):
+    C = np.atleast_2d(C)
+    return O.apply_local(self.vloc, self.miller, C) + (self.project(C) @ self.D.T) @ self.P.T
+
+
+def _project_without_conjugate(self, C):
+    return C @ self.P
+
+
+def _sinv_wrong_sign(self, C):
+    C = np.atleast_2d(C)
+    if self.Q is None:
+        return C.copy()
+    return C + (self.project(C) @ self.woodbury_k().T) @ self.P.T
+
+
+def _filter_first_coefficient_everywhere(apply_a, Y0, degree, a, b):
+    c, e = 0.5 * (b + a), 0.5 * (b - a)
+    Yprev, Y = Y0, (apply_a(Y0) - c * Y0) / e
+    for _ in range(1, degree):
+        Yprev, Y = Y, (1.0 / e) * (apply_a(Y) - c * Y) - Yprev
+    return Y
+
+
+def _rr_back_transform_without_conjugate(Y, HY, SY):
+    Hs = Y.conj() @ HY.T
+    Ss = Y.conj() @ SY.T
+    Hs = 0.5 * (Hs + Hs.conj().T)
+    Ss = 0.5 * (Ss + Ss.conj().T)
+    L = np.linalg.cholesky(Ss)
+    Li = scipy.linalg.solve_triangular(L, np.eye(L.shape[0]), lower=True)
+    lam, U = np.linalg.eigh(0.5 * ((Li @ Hs @ Li.conj().T) + (Li @ Hs @ Li.conj().T).conj().T))
+    X = Li.T @ U
+    return lam, X.T @ Y, X.T @ HY, X.T @ SY, X
+
+
+def _plant(monkeypatch, what):
+    if what == "kinetic term dropped from H psi":
+        monkeypatch.setattr(O.Hamiltonian, "apply_h", _apply_h_without_kinetic)
+    elif what == "forward DFT with the inverse sign":
+        fwd = O.forward_dft_direct
+        monkeypatch.setattr(O, "forward_dft_direct", lambda F: np.conj(fwd(np.conj(F))))
+    elif what == "projection without the conjugate":
+        monkeypatch.setattr(O.Hamiltonian, "project", _project_without_conjugate)
+    elif what == "Woodbury correction with the wrong sign":
+        monkeypatch.setattr(O.Hamiltonian, "apply_sinv", _sinv_wrong_sign)
+    elif what == "recurrence coefficient 1/e instead of 2/e":
+        monkeypatch.setattr(O, "chebyshev_filter", _filter_first_coefficient_everywhere)
+    elif what == "Rayleigh-Ritz back-transform not conjugated":
+        monkeypatch.setattr(O, "rayleigh_ritz", _rr_back_transform_without_conjugate)
+    elif what == "potential Fourier component at G' - G":
+        vt = O.vtilde
+        monkeypatch.setattr(O, "vtilde", lambda v, g: vt(v, -np.asarray(g)))
+    else:  # pragma: no cover
+        raise KeyError(what)
+
+
+CASES = [
+    ("kinetic term dropped from H psi", lambda: pins.test_dense_equals_matrix_free(False)),
+    ("forward DFT with the inverse sign", pins.test_local_matches_numpy_fft),
+    ("projection without the conjugate", lambda: pins.test_hermiticity(False)),
+    ("Woodbury correction with the wrong sign", pins.test_woodbury_inverse),
+    ("recurrence coefficient 1/e instead of 2/e", lambda: pins.test_chebyshev_scaling_of_eigenvectors(False)),
+    ("Rayleigh-Ritz back-transform not conjugated", pins.test_rayleigh_ritz_matches_generalized_eigh),
+    ("potential Fourier component at G' - G", lambda: pins.test_dense_equals_matrix_free(False)),
+]
+
+
+@pytest.mark.parametrize("what,pin", CASES, ids=[c[0] for c in CASES])
+def test_planted_mistake_fails_its_pin(monkeypatch, what, pin):
+    pin()                         # the pin passes on the oracle as it stands
+    _plant(monkeypatch, what)
+    with pytest.raises(AssertionError):
+        pin()

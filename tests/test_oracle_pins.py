@@ -239,6 +239,35 @@ def test_s_ortho():
 
 
 @pytest.mark.parametrize("with_q", [False, True])
+def test_one_s_ortho_pass_before_rr_gives_the_same_ritz_pairs(with_q):
+    """Reading r11 of the GPU path: one Cholesky-QR pass, then Alg. 5 (whose Cholesky of
+    S_Psi is the second pass), against the oracle's two passes then Alg. 5, on a filtered
+    (ill-conditioned) block; and Ritz values do not depend on the basis of the span."""
+    p = small_problem(with_q=with_q, nband=8)
+    h = O.Hamiltonian.from_problem(p)
+    Y0 = W.random_block(23, h.npw, 8)
+    Y = O.chebyshev_filter(h.apply_a, Y0, 24, 0.0, 2.0 * p.ecut + 3.0)
+    s = np.linalg.svd(Y, compute_uv=False)
+    assert s[0] / s[-1] > 1e6                 # the case the second pass is there for
+    y2 = Y
+    for _ in range(2):
+        y2, _ = O.s_ortho(y2, h.apply_s(y2))
+    lam2, Yr2, *_ = O.rayleigh_ritz(y2, h.apply_h(y2), h.apply_s(y2))
+    y1, _ = O.s_ortho(Y, h.apply_s(Y))
+    lam1, Yr1, HYr1, SYr1, _ = O.rayleigh_ritz(y1, h.apply_h(y1), h.apply_s(y1))
+    np.testing.assert_allclose(lam1, lam2, rtol=0, atol=1e-11)
+    np.testing.assert_allclose(Yr1.conj() @ SYr1.T, np.eye(8), atol=1e-12)
+    np.testing.assert_allclose(Yr1.conj() @ HYr1.T, np.diag(lam1), atol=1e-11)
+    # another basis of the same span (of a well-conditioned block)
+    B = W.random_block(24, 8, 8) + 3.0 * np.eye(8)
+    ritz = []
+    for Z in (Y0, B @ Y0):
+        z, _ = O.s_ortho(Z, h.apply_s(Z))
+        ritz.append(O.rayleigh_ritz(z, h.apply_h(z), h.apply_s(z))[0])
+    np.testing.assert_allclose(ritz[1], ritz[0], rtol=0, atol=1e-12)
+
+
+@pytest.mark.parametrize("with_q", [False, True])
 def test_chebfi_converges_to_dense(with_q):
     """Brute force: ChebFi eigenvalues -> lowest dense (generalized) eigenvalues."""
     p = small_problem(with_q=with_q, box=(16, 16, 16), ecut=3.0, nband=10)
