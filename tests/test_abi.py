@@ -39,3 +39,21 @@ def test_status_strings_without_gpu():
     h = ctypes.c_void_p()
     assert lib.pw_ctx_create(None, None, ctypes.byref(h)) == -1
     assert b"NULL" in lib.pw_last_error()
+
+
+def test_no_cpu_fallback_without_a_gpu():
+    """The product path has no CPU fallback: without a usable GPU, creating a context fails
+    with PW_ECUDA from the library (the descriptor itself is valid)."""
+    import types
+
+    import pytest
+
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    from paper_2604_11139_gb300 import workloads as W
+
+    prob = W.make_problem("tiny_gamma_fp64", box=(16, 16, 16), ecut=3.0, nband=4)
+    with pytest.raises(pwlib.PWError) as e:
+        pwlib.Context.from_problem(prob, stream=types.SimpleNamespace(cuda_stream=0))
+    assert e.value.status == -3
