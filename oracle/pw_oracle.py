@@ -9,7 +9,7 @@ order) in numpy float64/complex128, with no blocking, fusion or reordering beyon
 what the definition states.  Library primitives used as steps: matrix products,
 ``numpy.linalg.cholesky``/``eigh``, ``scipy.linalg.solve_triangular``.
 
-Conventions (the paper is silent on them; readings listed in the design notes):
+Conventions (the paper is silent on them; these are the readings this oracle takes):
   * bands are stored as rows of an (M, N) array, i.e. the N x M wave-function
     matrix Psi of Sec. 3.1 in column-major order;
   * psi(r) = sum_G c_G exp(i (k+G).r); the inverse DFT is unnormalised (+i),
@@ -22,9 +22,10 @@ Pins (tests marked ``not gpu`` in tests/test_oracle_pins.py): free-electron
 spectrum and shell degeneracies (tests/golden/r3_counts.txt), constant-potential
 shift, Hermiticity, dense == matrix-free == numpy.fft, Woodbury identity,
 Chebyshev scaling of exact eigenvectors against the closed form of T_m, Lanczos
-bound >= lambda_max, Rayleigh-Ritz against scipy's generalized eigensolver,
-ChebFi convergence to dense diagonalisation, Parseval for the density, projector
-symmetries, adjoint against finite differences.
+bound >= lambda_max, Rayleigh quotients and residual norms of exact and perturbed
+pencil eigenpairs against closed forms, Rayleigh-Ritz against scipy's generalized
+eigensolver, ChebFi convergence to dense diagonalisation, Parseval for the
+density, projector symmetries, adjoint against finite differences.
 """
 from __future__ import annotations
 
@@ -338,8 +339,10 @@ def residual_norms(lam, HY, SY) -> np.ndarray:
 
 def chebfi(ham: Hamiltonian, Y0: np.ndarray, v0: np.ndarray, degree: int, cycles: int,
            lanczos_steps: int = 10, return_history: bool = False):
-    """Chebyshev-filtered subspace iteration (Alg. 7 / Alg. 12) with the readings
-    listed in the design notes:
+    """Chebyshev-filtered subspace iteration (Alg. 7 / Alg. 12).  Where the paper is
+    silent this oracle reads it as follows (the filter bounds are not written out in
+    the paper; the Lanczos bound is the Zhou-Li estimate, and S >= I makes H's bound
+    valid for S^{-1}H):
 
       b = theta_max + |beta_k| from Lanczos on H (spectrum of S^{-1}H is below it);
       cycle 1 cut a = max Rayleigh quotient of Psi_0; later a = largest Ritz value;

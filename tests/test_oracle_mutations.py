@@ -49,6 +49,38 @@ def _rr_back_transform_without_conjugate(Y, HY, SY):
     return lam, X.T @ Y, X.T @ HY, X.T @ SY, X
 
 
+def _rq_over_plain_norm(C, HC, SC):
+    num = np.real(np.einsum("ij,ij->i", C.conj(), HC))
+    return num / np.real(np.einsum("ij,ij->i", C.conj(), C))
+
+
+def _rq_without_conjugate(C, HC, SC):
+    num = np.real(np.einsum("ij,ij->i", C, HC))
+    den = np.real(np.einsum("ij,ij->i", C.conj(), SC))
+    return num / den
+
+
+_RES_PSI = [None]
+
+
+def _rr_recording_psi(rr):
+    def wrapped(Y, HY, SY):
+        out = rr(Y, HY, SY)
+        _RES_PSI[0] = out[1]
+        return out
+    return wrapped
+
+
+def _residual_with_psi_for_s_psi(lam, HY, SY):
+    # the S-less residual || H psi - lambda psi ||: psi (recorded from the last
+    # Rayleigh-Ritz call) in place of S psi
+    return np.linalg.norm(HY - lam[:, None] * _RES_PSI[0], axis=1)
+
+
+def _residual_zeros(lam, HY, SY):
+    return np.zeros(HY.shape[0])
+
+
 def _plant(monkeypatch, what):
     if what == "kinetic term dropped from H psi":
         monkeypatch.setattr(O.Hamiltonian, "apply_h", _apply_h_without_kinetic)
@@ -66,6 +98,15 @@ def _plant(monkeypatch, what):
     elif what == "potential Fourier component at G' - G":
         vt = O.vtilde
         monkeypatch.setattr(O, "vtilde", lambda v, g: vt(v, -np.asarray(g)))
+    elif what == "Rayleigh quotient over |psi|^2 instead of psi^dagger S psi":
+        monkeypatch.setattr(O, "rayleigh_quotients", _rq_over_plain_norm)
+    elif what == "Rayleigh quotient numerator without the conjugate":
+        monkeypatch.setattr(O, "rayleigh_quotients", _rq_without_conjugate)
+    elif what == "residual returning zeros":
+        monkeypatch.setattr(O, "residual_norms", _residual_zeros)
+    elif what == "residual with psi in place of S psi":
+        monkeypatch.setattr(O, "rayleigh_ritz", _rr_recording_psi(O.rayleigh_ritz))
+        monkeypatch.setattr(O, "residual_norms", _residual_with_psi_for_s_psi)
     else:  # pragma: no cover
         raise KeyError(what)
 
@@ -78,6 +119,12 @@ CASES = [
     ("recurrence coefficient 1/e instead of 2/e", lambda: pins.test_chebyshev_scaling_of_eigenvectors(False)),
     ("Rayleigh-Ritz back-transform not conjugated", pins.test_rayleigh_ritz_matches_generalized_eigh),
     ("potential Fourier component at G' - G", lambda: pins.test_dense_equals_matrix_free(False)),
+    ("Rayleigh quotient over |psi|^2 instead of psi^dagger S psi",
+     lambda: pins.test_rayleigh_quotients_of_exact_and_mixed_vectors(True)),
+    ("Rayleigh quotient numerator without the conjugate",
+     lambda: pins.test_rayleigh_quotients_of_exact_and_mixed_vectors(False)),
+    ("residual returning zeros", lambda: pins.test_residual_norms_of_exact_and_perturbed_pairs(False)),
+    ("residual with psi in place of S psi", lambda: pins.test_chebfi_residuals_match_dense_pencil(True)),
 ]
 
 

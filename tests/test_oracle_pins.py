@@ -267,6 +267,72 @@ def test_one_s_ortho_pass_before_rr_gives_the_same_ritz_pairs(with_q):
     np.testing.assert_allclose(ritz[1], ritz[0], rtol=0, atol=1e-12)
 
 
+def _exact_pairs(with_q, nvec=6):
+    """Lowest generalized eigenpairs of the dense pencil (H, S) by LAPACK: S-orthonormal
+    columns V (V^dagger S V = I), H V = S V diag(lam).  Returned as band rows."""
+    p = small_problem(with_q=with_q)
+    h = O.Hamiltonian.from_problem(p)
+    H, S = h.dense()
+    lam, V = scipy.linalg.eigh(H, S)
+    return H, S, lam[:nvec], V[:, :nvec].T.copy()
+
+
+@pytest.mark.parametrize("with_q", [False, True])
+def test_rayleigh_quotients_of_exact_and_mixed_vectors(with_q):
+    """Alg. 12's Rayleigh quotients.  (i) Exact eigenvectors of the pencil give their
+    eigenvalues.  (ii) x = v_i + d v_j (v S-orthonormal eigenvectors, complex d) has the
+    closed form (lam_i + |d|^2 lam_j) / (1 + |d|^2), whatever the scale of x: the
+    numerator is x^dagger H x and the denominator x^dagger S x (not |x|^2 when Q != 0)."""
+    H, S, lam, V = _exact_pairs(with_q)
+    rq = O.rayleigh_quotients(V, V @ H.T, V @ S.T)
+    assert np.isrealobj(rq)
+    np.testing.assert_allclose(rq, lam, rtol=1e-12, atol=1e-12)
+    pairs = [(0, 3, 0.3 + 0.4j), (1, 5, -0.7j), (2, 4, 1.5 - 0.2j), (5, 0, 0.05)]
+    X = np.stack([(2.5 - 1j) * (V[i] + d * V[j]) for i, j, d in pairs])
+    expect = np.array([(lam[i] + abs(d) ** 2 * lam[j]) / (1 + abs(d) ** 2) for i, j, d in pairs])
+    rq = O.rayleigh_quotients(X, X @ H.T, X @ S.T)
+    np.testing.assert_allclose(rq, expect, rtol=1e-12, atol=1e-12)
+
+
+@pytest.mark.parametrize("with_q", [False, True])
+def test_residual_norms_of_exact_and_perturbed_pairs(with_q):
+    """Alg. 12's residual ||H psi_i - lambda_i S psi_i||.  (i) Exact pencil eigenpairs give
+    ~0 (relative to the scale of H psi).  (ii) For x = v_i + d v_j and lambda = lam_i the
+    residual is d (lam_j - lam_i) S v_j, so its norm is |d| |lam_j - lam_i| ||S v_j||; with
+    S = I, ||S v_j|| = 1 and the value is closed-form.  A residual that omits S fails (i)
+    when Q != 0; one that returns zeros fails (ii)."""
+    H, S, lam, V = _exact_pairs(with_q)
+    r = O.residual_norms(lam, V @ H.T, V @ S.T)
+    scale = np.linalg.norm(V @ H.T, axis=1)
+    assert np.all(r <= 1e-10 * scale)
+    pairs = [(0, 3, 0.3 + 0.4j), (1, 5, -0.7j), (4, 2, 0.01)]
+    X = np.stack([V[i] + d * V[j] for i, j, d in pairs])
+    lam_x = np.array([lam[i] for i, _, _ in pairs])
+    r = O.residual_norms(lam_x, X @ H.T, X @ S.T)
+    if with_q:
+        svj = np.array([np.linalg.norm(S @ V[j]) for _, j, _ in pairs])
+        assert np.all(np.abs(svj - 1.0) > 1e-3)      # S v_j is not a unit vector here
+    else:
+        svj = np.ones(len(pairs))
+    expect = np.array([abs(d) * abs(lam[j] - lam[i]) for i, j, d in pairs]) * svj
+    np.testing.assert_allclose(r, expect, rtol=1e-10, atol=1e-13)
+
+
+@pytest.mark.parametrize("with_q", [False, True])
+def test_chebfi_residuals_match_dense_pencil(with_q):
+    """The residuals ChebFi reports (Alg. 12) are ||H y_i - lambda_i S y_i|| of the Ritz
+    pairs it returns, with H and S the dense matrices built entrywise."""
+    p = small_problem(with_q=with_q, nband=8)
+    h = O.Hamiltonian.from_problem(p)
+    H, S = h.dense()
+    Y0 = W.psi0(p.seed, h.npw, p.nband)
+    v0 = W.lanczos_v0(p.seed, h.npw)
+    lam, Y, res, _ = O.chebfi(h, Y0, v0, degree=6, cycles=2)
+    ref = np.linalg.norm(Y @ H.T - lam[:, None] * (Y @ S.T), axis=1)
+    assert ref.min() > 1e-6                      # not yet converged: the values mean something
+    np.testing.assert_allclose(res, ref, rtol=1e-9, atol=1e-12)
+
+
 @pytest.mark.parametrize("with_q", [False, True])
 def test_chebfi_converges_to_dense(with_q):
     """Brute force: ChebFi eigenvalues -> lowest dense (generalized) eigenvalues."""
