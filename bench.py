@@ -71,6 +71,24 @@ def workload_config(prob, npw, nproj):
 
 
 # ------------------------------------------------------------------------- clocks
+def gpu_id(dev):
+    """nvidia-smi selector of CUDA device `dev`: its UUID (nvidia-smi numbers GPUs
+    physically and ignores CUDA_VISIBLE_DEVICES, so an ordinal could name another GPU)."""
+    try:
+        import torch
+        u = str(torch.cuda.get_device_properties(dev).uuid)
+        if u and u != "None":
+            return u if u.startswith("GPU-") else "GPU-" + u
+    except Exception:
+        pass
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+    if vis:
+        ids = [v.strip() for v in vis.split(",") if v.strip()]
+        if 0 <= int(dev) < len(ids):
+            return ids[int(dev)]
+    return str(dev)
+
+
 class ClockSampler:
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -78,12 +96,13 @@ class ClockSampler:
 
     def __init__(self, dev):
         self.dev = dev
+        self.gpu = gpu_id(dev)
         self.p = None
 
     def start(self):
         try:
             self.p = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                                       "-lms", "200", "-i", str(self.dev)], stdout=subprocess.PIPE,
+                                       "-lms", "200", "-i", self.gpu], stdout=subprocess.PIPE,
                                       stderr=subprocess.DEVNULL, text=True)
         except Exception:
             self.p = None
@@ -112,7 +131,7 @@ class ClockSampler:
                 if v.lower().startswith("active"):
                     reasons.add(n)
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
-                "reasons": sorted(reasons), "samples": len(sm)}
+                "reasons": sorted(reasons), "samples": len(sm), "gpu": self.gpu}
 
 
 # ------------------------------------------------------------------------- helpers

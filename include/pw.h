@@ -71,15 +71,29 @@ typedef struct {
   const double* tau;   /* natom*3 cartesian atom positions (bohr) */
   int nchan;           /* projector channels per atom; 4 projectors (s, px, py, pz) each */
   const double* sigma; /* nchan Gaussian widths (bohr) of the projector form factors */
-  const double* D;     /* nproj*nproj real symmetric, column-major, nproj = natom*4*nchan */
+  const double* D;     /* nproj*nproj real symmetric, column-major, nproj = natom*4*nchan
+                          (or the nproj below when proj != NULL) */
   const double* Q;     /* nproj*nproj real symmetric positive definite, or NULL (S = I) */
+  /* Explicit projectors (Sec. 4.2: the nonlocal operator takes the projector functions
+   * <k+G|p_i^R> as data).  proj == NULL: P is generated from natom/tau/nchan/sigma as
+   * described at pw_ctx_create, and nproj is ignored.  proj != NULL: P is read from
+   * this host array of npw*nproj complex128 values (interleaved re/im), column-major
+   * with ld = npw, rows in the canonical plane-wave order of pw_ctx_gvectors (Miller
+   * indices (h, k, l) ascending; npw and the order depend only on lattice, kpt, ecut and
+   * box, so a caller can read them from a context made with natom = 0); tau, nchan and
+   * sigma are then ignored and D (and Q) are nproj x nproj.  The columns are used as
+   * given (no normalisation).  PW_EINVAL if nproj < 1 or D is NULL. */
+  int nproj;
+  const void* proj;
 } pw_problem_desc;
 
 /* Builds the plane-wave sphere, the FFT plans, the projector matrix P (Sec. 4.2:
- * P = <G|p_i^R>, Gaussian s/p form factors, structure phase exp(-i(k+G).R),
- * unit column norm), the permuted V_loc grid and, when Q != NULL, the Woodbury
- * matrices of S^-1 (Sec. 3.3 Sinv).  stream: a cudaStream_t, or NULL for the
- * legacy default stream.  On success *out owns all device memory it uses. */
+ * P = <G|p_i^R>; unless given explicitly, Gaussian s/p form factors, structure phase
+ * exp(-i(k+G).R), unit column norm), the permuted V_loc grid and, when Q != NULL, the
+ * Woodbury matrices of S^-1 (Sec. 3.3 Sinv).  Every precision uses the same P: the
+ * FP64 path as given, the mixed path its complex64 rounding and its bf16 pieces.
+ * stream: a cudaStream_t, or NULL for the legacy default stream.  On success *out owns
+ * all device memory it uses. */
 PW_API int pw_ctx_create(const pw_problem_desc* desc, void* stream, pw_ctx** out);
 PW_API int pw_ctx_destroy(pw_ctx* ctx);
 PW_API int pw_ctx_set_stream(pw_ctx* ctx, void* stream);
@@ -92,8 +106,8 @@ PW_API int pw_ctx_info(const pw_ctx* ctx, int* npw, int* nproj);
  * |k+G|^2/2 (host, npw doubles).  Either pointer may be NULL. */
 PW_API int pw_ctx_gvectors(const pw_ctx* ctx, int32_t* miller, double* kinetic);
 
-/* Copies the generated projector matrix P (npw x nproj complex128, column-major,
- * ld = npw) to the device buffer P_out. */
+/* Copies the projector matrix P in use (generated or given; npw x nproj complex128,
+ * column-major, ld = npw) to the device buffer P_out. */
 PW_API int pw_ctx_projectors(const pw_ctx* ctx, void* P_out);
 
 /* HX / HX_SX of Sec. 3.3: hpsi = H psi and, if spsi != NULL, spsi = S psi for
@@ -230,7 +244,9 @@ PW_API int pw_diff_backward(pw_diff* diff, const double* eig_bar, const void* ps
  * scratch lives in one static 32 MiB device array inside the library, held by
  * every GPU that loads it until process exit.  The first call on a device looks
  * up that array's address (cudaGetSymbolAddress); make it before any stream
- * capture.  Calls share the array: calls that overlap on the GPU race.  Bands are
+ * capture.  The address is cached per device for the life of the process, so after a
+ * cudaDeviceReset of that device this entry point must not be called again.  Calls
+ * share the array: calls that overlap on the GPU race.  Bands are
  * processed in chunks that fit; PW_EINVAL if even one band's scratch (half-box
  * planes + projections) exceeds 32 MiB.  psi, hpsi: complex128 device blocks. */
 PW_API int pw_hamiltonian_apply_noalloc(pw_ctx* ctx, const void* psi, int64_t ldpsi, int nband,

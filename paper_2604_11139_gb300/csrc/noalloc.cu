@@ -12,7 +12,9 @@
 // every GPU that loads this library until the process exits.  Host code never
 // dereferences the symbol; it obtains the device address once per device with
 // cudaGetSymbolAddress (done on the first call on that device, so that first call
-// must happen before any stream capture) and passes it to the kernels.
+// must happen before any stream capture) and passes it to the kernels.  The cached
+// address belongs to the device's primary context: after cudaDeviceReset it is stale,
+// so a process that resets a device must not call this entry point on it again.
 // Every call shares the array and leaves its last contents behind; calls that
 // overlap on the GPU (different streams, different host threads) race on it.
 // No part of it has to start at zero: each kernel writes the region it reads
@@ -98,7 +100,7 @@ extern "C" PW_API int pw_hamiltonian_apply_noalloc(pw_ctx* ctx, const void* psi_
     if (e == cudaSuccess && np > 0) {
       Epi<double> ec;
       ec.mode = EPI_STORE; ec.out = Cm; ec.ldo = np; ec.alpha = 1.0; ec.beta = 0; ec.shift = 0;
-      ec.yk = nullptr; ec.ykm1 = nullptr; ec.ldy = 0; ec.ldy2 = 0;
+      ec.yk = nullptr; ec.ykm1 = nullptr; ec.ldy = 0; ec.ldy2 = 0; ec.dev_ce = nullptr; ec.first = 0;
       e = launch_cgemm<double>(1, 0, np, nb, npw, ctx->P64, npw, x, ldpsi, ec, nsplit, spl, st);
       if (e == cudaSuccess)
         e = launch_dblock<double>(np, nb, ctx->D64, ctx->blk0, ctx->blklen, Cm, np, Z, np, st);

@@ -859,8 +859,14 @@ int create_impl(const pw_problem_desc* d, void* stream, pw_ctx** out) {
   if (!d || !out) return set_error(PW_EINVAL, "NULL argument");
   *out = nullptr;
   if (!d->vloc) return set_error(PW_EINVAL, "vloc is NULL");
-  if (d->natom < 0 || d->nchan < 0 || d->nchan > kMaxChan) return set_error(PW_EINVAL, "bad natom/nchan");
-  if (d->natom > 0 && (!d->tau || !d->sigma || !d->D)) return set_error(PW_EINVAL, "tau/sigma/D missing");
+  const bool given_p = d->proj != nullptr;
+  if (given_p) {
+    if (d->nproj < 1) return set_error(PW_EINVAL, "explicit projectors need nproj >= 1 (got %d)", d->nproj);
+    if (!d->D) return set_error(PW_EINVAL, "explicit projectors need D");
+  } else {
+    if (d->natom < 0 || d->nchan < 0 || d->nchan > kMaxChan) return set_error(PW_EINVAL, "bad natom/nchan");
+    if (d->natom > 0 && (!d->tau || !d->sigma || !d->D)) return set_error(PW_EINVAL, "tau/sigma/D missing");
+  }
   if (!(d->ecut > 0)) return set_error(PW_EINVAL, "ecut must be positive");
   pw_ctx* ctx = new (std::nothrow) pw_ctx();
   if (!ctx) return set_error(PW_ENOMEM, "host allocation");
@@ -988,13 +994,16 @@ int create_impl(const pw_problem_desc* d, void* stream, pw_ctx** out) {
   PW_TRY(upload(ctx, &ctx->vperm32, (const float*)nullptr, ntot));
   CU_TRY(setup_vperm(vraw, ctx->n, ctx->rho_perm, 1.0 / (double)ntot, ctx->vperm64, ctx->vperm32, st), "vperm");
   // projectors
-  ctx->natom = d->natom;
-  ctx->nchan = d->nchan;
-  ctx->nproj = d->natom * d->nchan * 4;
+  ctx->natom = given_p ? 0 : d->natom;
+  ctx->nchan = given_p ? 0 : d->nchan;
+  ctx->nproj = given_p ? d->nproj : d->natom * d->nchan * 4;
   const int np = ctx->nproj;
-  PW_TRY(upload(ctx, &ctx->P64, (const double2*)nullptr, (size_t)ctx->npw * std::max(np, 1)));
+  PW_TRY(upload(ctx, &ctx->P64, given_p ? (const double2*)d->proj : (const double2*)nullptr,
+                (size_t)ctx->npw * std::max(np, 1)));
   PW_TRY(upload(ctx, &ctx->P32, (const float2*)nullptr, (size_t)ctx->npw * std::max(np, 1)));
-  if (np > 0) {
+  if (given_p) {
+    CU_TRY(cast_z2c(ctx->P64, ctx->P32, (int64_t)ctx->npw * np, st), "P cast");
+  } else if (np > 0) {
     ProjParams pp;
     memcpy(pp.B, B, sizeof(B));
     memcpy(pp.kred, d->kpt, sizeof(pp.kred));

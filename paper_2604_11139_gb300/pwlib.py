@@ -46,7 +46,7 @@ class _Desc(ctypes.Structure):
                 ("box", ctypes.c_int * 3), ("vloc", ctypes.POINTER(ctypes.c_double)), ("natom", ctypes.c_int),
                 ("tau", ctypes.POINTER(ctypes.c_double)), ("nchan", ctypes.c_int),
                 ("sigma", ctypes.POINTER(ctypes.c_double)), ("D", ctypes.POINTER(ctypes.c_double)),
-                ("Q", ctypes.POINTER(ctypes.c_double))]
+                ("Q", ctypes.POINTER(ctypes.c_double)), ("nproj", ctypes.c_int), ("proj", ctypes.c_void_p)]
 
 
 _LIB = None
@@ -143,7 +143,10 @@ def _dtype(precision):
 class Context:
     """One k-point problem (pw_ctx): sphere, FFT plans, projectors, Woodbury matrices."""
 
-    def __init__(self, lattice, kpt, ecut, box, vloc, tau, sigmas, D, Q=None, stream=None):
+    def __init__(self, lattice, kpt, ecut, box, vloc, tau, sigmas, D, Q=None, stream=None, P=None):
+        """P (optional): explicit projector matrix, npw x nproj complex128 in the canonical
+        plane-wave order (numpy array); None generates the Gaussian s/p projectors from
+        tau and sigmas."""
         import torch
         lib = load()
         self._keep = []
@@ -166,6 +169,13 @@ class Context:
         d.nchan = sig.shape[0]
         d.sigma = _dptr(sig)
         d.D = _dptr(D)
+        if P is not None:
+            Pa = np.asfortranarray(np.asarray(P, dtype=np.complex128))
+            if Pa.ndim != 2 or D.shape != (Pa.shape[1], Pa.shape[1]):
+                raise ValueError("P must be npw x nproj with D nproj x nproj")
+            self._keep.append(Pa)
+            d.nproj = Pa.shape[1]
+            d.proj = ctypes.c_void_p(Pa.ctypes.data)
         if Q is not None:
             Qa = np.asfortranarray(np.asarray(Q, dtype=np.float64))
             self._keep.append(Qa)
@@ -186,9 +196,9 @@ class Context:
         self._dependents = weakref.WeakSet()   # handles that borrow this context
 
     @classmethod
-    def from_problem(cls, prob, kpt=None, ecut=None, stream=None):
+    def from_problem(cls, prob, kpt=None, ecut=None, stream=None, P=None):
         return cls(prob.lattice, prob.kpt if kpt is None else kpt, prob.ecut if ecut is None else ecut, prob.box,
-                   prob.vloc, prob.tau, prob.sigmas, prob.D, prob.Q, stream=stream)
+                   prob.vloc, prob.tau, prob.sigmas, prob.D, prob.Q, stream=stream, P=P)
 
     def close(self):
         for d in list(getattr(self, "_dependents", ())):

@@ -57,3 +57,22 @@ def test_no_cpu_fallback_without_a_gpu():
     with pytest.raises(pwlib.PWError) as e:
         pwlib.Context.from_problem(prob, stream=types.SimpleNamespace(cuda_stream=0))
     assert e.value.status == -3
+
+
+def test_explicit_projector_descriptor_checked_on_the_host():
+    """Explicit projectors with nproj < 1 or without D are rejected before any CUDA call."""
+    lib = pwlib.load()
+    d = pwlib._Desc()
+    d.ecut = 1.0
+    d.box[:] = [8, 8, 8]
+    v = (ctypes.c_double * 512)()
+    d.vloc = ctypes.cast(v, ctypes.POINTER(ctypes.c_double))
+    buf = (ctypes.c_double * 4)()
+    d.proj = ctypes.cast(buf, ctypes.c_void_p)
+    d.nproj = 0
+    h = ctypes.c_void_p()
+    assert lib.pw_ctx_create(ctypes.byref(d), None, ctypes.byref(h)) == -1
+    assert b"nproj" in lib.pw_last_error()
+    d.nproj = 2
+    assert lib.pw_ctx_create(ctypes.byref(d), None, ctypes.byref(h)) == -1
+    assert b"need D" in lib.pw_last_error()

@@ -26,8 +26,12 @@ def rel(a, b):
     return (torch.linalg.vector_norm(a - b, dim=1) / torch.linalg.vector_norm(b, dim=1)).max().item()
 
 
+# tiny: one chunk; 96^3: chunks of 4 bands (matrix-vector GEMM forms); 64^3 with 40 bands:
+# chunks of 17, 17 and 6 bands, so the tiled split-K GEMM reuses the partials and the C/Z
+# regions of the scratch from one chunk to the next
 @pytest.mark.parametrize("kw", [dict(name="tiny_gamma_fp64", nband=16),
-                                dict(name="fp64_at_scale", nband=24)])
+                                dict(name="fp64_at_scale", nband=24),
+                                dict(name="differentiation", nband=40)])
 def test_noalloc_matches_hamiltonian_apply_twice(kw):
     kw = dict(kw)
     prob = W.make_problem(kw.pop("name"), **kw)
