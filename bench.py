@@ -6,11 +6,14 @@ call / filter time), mixed precision (complex64 FFTs, FP32-accumulated projector
 GEMMs) against the plain FP64 GPU path on the same inputs, with the eigenvalue
 error of one filter + Rayleigh-Ritz cycle between the two.
 
-Workload: the 96^3-box, ~55k plane-wave, 64-atom / 512-projector, 256-band,
-degree-10 Gamma-point problem (seeded synthetic inputs from workloads.py).  One
-step = one ChebFi cycle on one batch: the degree-m filter (timed: `value`)
-followed by the FP64 S-Ortho + Rayleigh-Ritz step.  Inputs are resident in HBM
-when the timed region starts; L2 is flushed (256 MB write) between steps.
+Workload (default): the precision form, a PAW-like generalized problem on a 120^3 box
+with ~100k plane waves, 108 atoms / 864 projectors, overlap S = I + P Q P^dagger applied
+as S^-1 through the Woodbury formula, 512 bands, degree-12 filter (seeded synthetic inputs
+from workloads.py).  One step = one ChebFi cycle on one batch: the degree-m filter (timed:
+`value`) followed by the FP64 S-Ortho + Rayleigh-Ritz step.  Inputs are resident in HBM
+when the timed region starts; L2 is flushed (256 MB write) between steps.  The batched
+k-point form (32 k-points, one captured graph per filter) is measured after it in the same
+run and reported under "batched_kpoints" (skip with --no-batched).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -38,7 +41,7 @@ from paper_2604_11139_gb300 import workloads as W  # noqa: E402
 
 METRIC = "band·H-applies/s in Chebyshev filter, mixed vs FP64 GPU, at ≤1e-6 Ha eig error"
 UNIT = "band-applies/s"
-WORKLOAD = "fp64_at_scale"
+WORKLOAD = "paw_precision"
 
 
 def parse():
@@ -47,10 +50,12 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--fp64-steps", type=int, default=2)
+    ap.add_argument("--fp64-steps", type=int, default=10,
+                    help="timed runs of the FP64 filter (the denominator of the mixed-vs-FP64 ratio; median)")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--tc-pieces", type=int, default=2,
                     help="bf16 pieces of the mixed GEMM operands: 2 (3 products) or 3 (6 products)")
@@ -349,8 +354,20 @@ def run_ours(args):
             ts.append(e0.elapsed_time(e1) / 1e3)
         eig64, _ = ctx.rayleigh_ritz(Y64)
         eig_err = float(np.abs(eig64 - eig_mixed).max())
-        fp64 = {"value": M * m / statistics.mean(ts), "unit": UNIT, "filter_ms": 1e3 * statistics.mean(ts),
-                "steps": len(ts)}
+        # context: the same filter with every FP64 GEMM on DFMA (one run)
+        ctx.fp64_config(0)
+        Y64.copy_(Y0)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        ctx.chebyshev_filter(Y64, m, a, b, precision=pwlib.PW_FP64)
+        e1.record(st)
+        torch.cuda.synchronize()
+        t_dfma = e0.elapsed_time(e1) / 1e3
+        ctx.fp64_config(1)
+        (t64,) = max_over_ranks([statistics.median(ts)], dist, "cuda")
+        fp64 = {"value": weak_value(world, M * m, t64), "unit": UNIT, "filter_ms": 1e3 * t64, "steps": len(ts),
+                "statistic": "median", "gemms": "FP64-accurate digit-sliced tensor-core GEMMs (pw_fp64_config 1)",
+                "dfma_gemms": {"value": M * m / t_dfma, "filter_ms": 1e3 * t_dfma, "steps": 1}}
 
     # end to end through the public C ABI with host buffers: H2D psi, one ChebFi cycle, D2H psi + eigenvalues
     host_in = torch.from_numpy(psi0).pin_memory()
@@ -369,7 +386,9 @@ def run_ours(args):
     e2e_val = None
     if e2e_t:
         (t_e2e,) = max_over_ranks([statistics.mean(e2e_t)], dist, "cuda")
-        e2e_val = weak_value(world, M * m, t_e2e)
+        # H-applies of one cycle: the M x m of the filter and one more per band for the
+        # Rayleigh-Ritz step's H Psi
+        e2e_val = weak_value(world, M * (m + 1), t_e2e)
     bytes_psi = psi0.nbytes
 
     # roofline of the dominant kernel class of the filter, and of every class
@@ -386,16 +405,22 @@ def run_ours(args):
     pieces = ctx.tc_config()
     # pass 3 carries the recurrence (reads P Z and Y_{k-1}, writes the bf16 pieces of Y_{k+1})
     # when the warp-group plane kernels run without Q
-    fused = (fft_cfg[1] // 8 == 2) and prob.Q is None
+    fused = (fft_cfg[1] // 8 in (2, 3)) and prob.Q is None
+    # GEMM launches per filter step: the projection of Y_k (and, with Q, of W = (T + V) Y_k for
+    # the Woodbury correction), one back-projection; the class times also hold the bf16 splits
+    # of the operands and the split-K sums of the projection
+    nproj_gemms = 2 if prob.Q is not None else 1
     alg = {"plane_inv": ("hbm", nb_avg * (npw + half) * c8),
            "xline": ("hbm", nb_avg * 2 * half * c8 + box[0] * box[1] * box[2] * 4),
            "plane_fwd": ("hbm", nb_avg * ((half + (4 if fused else 2) * npw) * c8 + (4 * pieces * npw if fused else 0))),
            # bf16 products of one projector GEMM call over all bands: 2 (2 Np)(2 N) M per product
            "gemm_proj": ("tensor", 2.0 * (2 * nproj) * (2 * npw) * M * (3 if pieces == 2 else 6)),
            "gemm_back": ("tensor", 2.0 * (2 * nproj) * (2 * npw) * M * (3 if pieces == 2 else 6))}
+    launches = {"gemm_proj": args.steps * m * nproj_gemms, "gemm_back": args.steps * m}
     per_class = {}
     for cname, (bnd, units) in alg.items():
         ms_c, n_c = prof[cname]
+        n_c = launches.get(cname, n_c)
         per_launch = ms_c / 1e3 / max(n_c, 1)
         if bnd == "hbm":
             a = units / per_launch / 1e9
@@ -415,19 +440,29 @@ def run_ours(args):
     else:
         roof = None
 
+    # measured FP64 FMA rate (the roofline of the DFMA-bound kernels), with its clock record
+    c64 = ClockSampler(dev)
+    c64.start()
+    fma64 = pwlib.fp64_fma_rate()
+    fp64_peak = {"tflops": fma64, "how": "pw_diag_fp64_fma_rate: independent FMA chains on every SM, best of 3",
+                 "clocks": c64.stop()}
     cpu = None
     if rank == 0 and not args.no_cpu and world == 1:
         cpu = cpu_oracle_rate(prob, args.cpu_seconds)
+    batched = None
+    if world == 1 and not args.no_batched and args.workload != "batched_kpoints":
+        ctx.close()
+        batched = run_batched(args, emit_line=False)
 
     if rank == 0:
         emit({"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
               "warmup": args.warmup, "ms_per_step": 1e3 * t_step / args.steps, "higher_is_better": True,
               "scaling": "weak", "vs_baseline": None, "dtype": "c64", "data": "synthetic",
               "config": workload_config(prob, npw, nproj),
-              "precision": f"filter: complex64 FFTs + BF16-split tcgen05 projector GEMMs ({ctx.tc_config()} pieces per "
-                           f"operand, {3 if ctx.tc_config() == 2 else 6} products, FP32 accumulation); RR: FP64",
+              "precision": f"filter: complex64 FFTs + BF16-split tcgen05 projector GEMMs ({pieces} pieces per "
+                           f"operand, {3 if pieces == 2 else 6} products, FP32 accumulation); RR: FP64",
               "filter_ms": 1e3 * t_filter / args.steps, "wall_s": wall, "autotune_local_ms": tune_ms,
-              "tc_pieces": ctx.tc_config(),
+              "tc_pieces": pieces,
               "fft_config": {"batch_bytes": fft_cfg[0],
                              "xline_kernel": ["line groups", "one thread per line", "warp groups",
                                               "warp groups, table twiddles",
@@ -438,11 +473,12 @@ def run_ours(args):
               "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": bytes_psi,
                       "d2h_bytes_per_step": bytes_psi + 8 * M,
                       "what": "H2D psi (pinned) + pw_chebfi_solve (Lanczos bound, 1 mixed filter + FP64 RR) "
-                              "+ D2H psi and eigenvalues"},
+                              "+ D2H psi and eigenvalues; M (m + 1) band-applies per cycle (filter + RR's H Psi)"},
               "roofline": roof, "roofline_per_class": per_class,
               "cpu_baseline": cpu, "clocks": clk, "gpu_launches": int(launches),
               "kernels_ms_per_step": {k: v[0] / args.steps for k, v in prof.items()},
-              "kernel_launches_per_step": {k: v[1] / args.steps for k, v in prof.items()}})
+              "kernel_launches_per_step": {k: v[1] / args.steps for k, v in prof.items()},
+              "fp64_fma_peak": fp64_peak, "batched_kpoints": batched})
     if dist is not None:
         dist.barrier()
         dist.destroy_process_group()
@@ -451,9 +487,10 @@ def run_ours(args):
 
 
 # ------------------------------------------------------------------------- batched k-points
-def run_batched(args):
+def run_batched(args, emit_line=True):
     """All k-points of the 4x4x2 Monkhorst-Pack-like grid (ragged spheres) filtered by one
-    captured graph per call (pw_batch_filter)."""
+    captured graph per call (pw_batch_filter).  emit_line=False returns the result as a dict
+    (the default run attaches it to the headline line)."""
     import torch
     from paper_2604_11139_gb300 import pwlib
     torch.cuda.set_device(0)
@@ -469,9 +506,13 @@ def run_batched(args):
     bounds = [c.spectrum_bounds(y, 10, v) for c, y, v in zip(ctxs, y0, v0)]
     a = [bd[1] for bd in bounds]
     b = [bd[2] for bd in bounds]
-    for c in ctxs:
+    # one box for every k-point: tune the FFT forms and band batch on the first, reuse them
+    ctxs[0].tc_config(args.tc_pieces)
+    ctxs[0].autotune(M, pwlib.PW_MIXED)
+    bb, var = ctxs[0].fft_config(pwlib.PW_MIXED)
+    for c in ctxs[1:]:
         c.tc_config(args.tc_pieces)
-        c.autotune(M, pwlib.PW_MIXED)
+        c.fft_config(pwlib.PW_MIXED, batch_bytes=bb, variant=var)
     y32 = [y.to(torch.complex64) for y in y0]
     work = [y.clone() for y in y32]
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
@@ -524,7 +565,7 @@ def run_batched(args):
         err = max(err, float(np.abs(e64 - em).max()))
     bt64.close()
     bt.close()
-    emit({"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
           "ms_per_step": 1e3 * statistics.mean(ts), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
           "dtype": "c64", "data": "synthetic",
           "config": {"workload": f"batched_kpoints: {nk} k-points (4x4x2 grid), 72x72x90 box, "
@@ -534,10 +575,13 @@ def run_batched(args):
                      "l2": "flushed between steps (256 MB write)"},
           "fp64": {"value": sub * M * m / t64, "unit": UNIT, "k_points": sub, "filter_ms": 1e3 * t64},
           "tc_pieces": args.tc_pieces, "eig_err_vs_fp64": err, "gpu_launches": int(launches + nodes * args.steps),
-          "graph_kernel_nodes": int(nodes), "clocks": clk})
+          "graph_kernel_nodes": int(nodes), "clocks": clk}
     for c in ctxs:
         c.close()
-    return 0
+    if emit_line:
+        emit(out)
+        return 0
+    return out
 
 
 # ------------------------------------------------------------------------- differentiation

@@ -98,6 +98,20 @@ PW_API int pw_ctx_create(const pw_problem_desc* desc, void* stream, pw_ctx** out
 PW_API int pw_ctx_destroy(pw_ctx* ctx);
 PW_API int pw_ctx_set_stream(pw_ctx* ctx, void* stream);
 
+/* Waits for the work queued on the context's stream and reports device-side failures:
+ * PW_ETIMEDOUT if a bounded wait of a tensor-core kernel expired (the context is then
+ * poisoned and must be destroyed; the GPU and other contexts stay usable), PW_ECUDA for a
+ * CUDA error.  Asynchronous entry points report such failures only at the next call that
+ * synchronises (this one, or any that returns host values). */
+PW_API int pw_ctx_sync(pw_ctx* ctx);
+
+/* Failure-detection test hook: the next tensor-core GEMM launched for this context issues no
+ * copies and gives up its waits after a few thousand polls, so its first bounded wait expires
+ * and it leaves through its failure path (records the failing stage, waits for anything it
+ * issued, releases tensor memory, returns).  The following pw_ctx_sync returns PW_ETIMEDOUT.
+ * No device fault is involved; it exists so that the failure path can be tested. */
+PW_API int pw_ctx_test_wait_expiry(pw_ctx* ctx);
+
 /* Sizes: number of plane waves N and projectors N_projs. */
 PW_API int pw_ctx_info(const pw_ctx* ctx, int* npw, int* nproj);
 
@@ -275,7 +289,8 @@ enum pw_prof_class {
  * compile-time twiddles, 2 groups of warps per 32 lines with compile-time twiddles,
  * 3 the same with run-time butterfly indices and table twiddles, 4 as 3 with several bands
  * per CTA; plane forms: 0 line groups, 1 one thread per line, 2 groups of warps per 32
- * lines with table twiddles.  Forms other than 0 cover box lengths with two-stage radix
+ * lines with table twiddles over the whole plane in shared memory, 3 the same over the
+ * plane's sphere rows and 32-column slices (less shared memory per CTA on large boxes).  Forms other than 0 cover box lengths with two-stage radix
  * plans.  Keeps the fastest for `precision` in the context.  Synchronises the stream;
  * *best_ms (may be NULL) receives the best time of one apply. */
 PW_API int pw_autotune(pw_ctx* ctx, int nband, int precision, double* best_ms);
@@ -292,6 +307,24 @@ PW_API int pw_fft_config(pw_ctx* ctx, int precision, int64_t set_batch_bytes, in
  * relative per product, the default) or 2 (three products, ~2^-16).  The tensor-core
  * operands of P are rebuilt on the next mixed-precision call. */
 PW_API int pw_tc_config(pw_ctx* ctx, int set_pieces, int* pieces);
+
+/* Reads (*mode, may be NULL) and then, for set_mode >= 0, sets how the FP64 complex GEMMs of
+ * the context run (the projector products of the FP64 H-apply and filter, Sec. 4.2, and the
+ * Rayleigh-Ritz Grams and rotations, Alg. 5): 1 (the default) as FP64-accurate GEMMs on the
+ * bf16 tensor cores by exact digit slicing (each row of op(A) and column of op(B) scaled by a
+ * power of two and cut into seven 7-bit integer digits; the 28 digit products with the seven
+ * leading weights summed exactly in FP32 per 256-wide K chunk, combined in 64-bit integers and
+ * accumulated in FP64; error per product below 2^-44 of the row and column maxima), 0 as DFMA
+ * GEMMs.  Products with at most 4 columns (matrix-vector forms) and the M x M x M products of
+ * the subspace step always use DFMA. */
+PW_API int pw_fp64_config(pw_ctx* ctx, int set_mode, int* mode);
+
+/* Measured FP64 FMA rate of the current GPU (the roofline of DFMA-bound kernels: the DFMA
+ * GEMM form and the complex128 FFT passes): a kernel of independent FMA chains on every SM,
+ * best of three timed runs on `stream` (a cudaStream_t or NULL) after one warm-up.  *tflops
+ * receives 2 x FMAs / second / 1e12, *ms (may be NULL) the kernel time.  Allocates and frees
+ * a small device buffer; synchronises the stream. */
+PW_API int pw_diag_fp64_fma_rate(void* stream, double* tflops, double* ms);
 
 PW_API int pw_profile_enable(pw_ctx* ctx, int on);
 PW_API int pw_profile_read(pw_ctx* ctx, double* ms, int64_t* launches);

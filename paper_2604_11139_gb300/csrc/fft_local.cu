@@ -2094,8 +2094,326 @@ static cudaError_t plane_wg(int which, const cplx<T>* psi, int64_t ldpsi, cplx<T
   PW_WG_CASE(64, 64, 4)
   PW_WG_CASE(72, 90, 4)
   PW_WG_CASE(96, 96, 4)
-  PW_WG_CASE(120, 120, 4)
+  PW_WG_CASE(120, 120, 8)
 #undef PW_WG_CASE
+  return cudaErrorNotSupported;
+}
+
+// Plane passes with a compact row buffer and 32-column slices (plane form 3).  The CTA keeps
+// only the plane's sphere rows R[nr][N3 + 1] (the z-lines) and one slice S[N2][33] of 32
+// y-columns at a time, instead of the whole N2 x N3 plane: on a 120^3 box that is 88 KB
+// instead of 117 KB, so that two CTAs share an SM and one CTA's loads overlap the other's
+// butterflies.  Lane = line in both stages, the TW warps of the CTA split the butterflies by
+// index mod TW; the y-lines of a slice go through S, the z-lines stay in R.
+template <int N2, int N3, int TW> struct PlaneR {
+  static constexpr CPlan P2 = make_cplan(N2), P3 = make_cplan(N3);
+  static constexpr int FR = N3 + 1;
+  static constexpr int SP = 33;
+  static constexpr int NSL = (N3 + 31) / 32;
+  static constexpr int THREADS = 32 * TW;
+  static constexpr bool ok = (P2.nst == 2 && P3.nst == 2);
+};
+
+template <typename T, int N2, int N3, int TW>
+__global__ void __launch_bounds__(PlaneR<N2, N3, TW>::THREADS) k_plane_inv_rs(const cplx<T>* __restrict__ psi,
+                                                                               int64_t ldpsi, cplx<T>* __restrict__ hb,
+                                                                               int64_t hb_bs, SphereDev sp, FftPlan plan,
+                                                                               const cplx<T>* __restrict__ tw) {
+  using C = cplx<T>;
+  using PR = PlaneR<N2, N3, TW>;
+  constexpr int FR = PR::FR, SP = PR::SP;
+  constexpr int Y1 = PR::P2.radix[0], Y2 = PR::P2.radix[1];
+  constexpr int Z1 = PR::P3.radix[0], Z2 = PR::P3.radix[1];
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* R = reinterpret_cast<C*>(smem_raw);
+  C* S = R + (size_t)sp.max_rows * FR;
+  int* ymap = reinterpret_cast<int*>(S + N2 * SP);
+  const int lane = threadIdx.x & 31, t = threadIdx.x >> 5;
+  const int p = blockIdx.x, b = blockIdx.y;
+  const int r0 = sp.plane_row0[p], nr = sp.plane_row0[p + 1] - r0;
+  const C* src = psi + (int64_t)b * ldpsi;
+  const C* twy = tw + plan.d[1].tw_off[0];
+  const C* twz = tw + plan.d[2].tw_off[0];
+  for (int i = threadIdx.x; i < N2; i += blockDim.x) ymap[i] = -1;
+  __syncthreads();
+  for (int i = threadIdx.x; i < nr; i += blockDim.x) ymap[pmod(sp.row_k[r0 + i], N2)] = i;
+  // z-lines of the sphere rows into R, 32 rows at a time; the first stage reads the row's run
+  // of coefficients straight from the block
+  for (int c0 = 0; c0 < nr; c0 += 32) {
+    const int row = c0 + lane;
+    const bool live = row < nr;
+    C* line = R + (size_t)(live ? row : 0) * FR;
+    if (live) {
+      const int g0 = sp.row_g0[r0 + row], cnt = sp.row_cnt[r0 + row], l0 = sp.row_l0[r0 + row];
+#pragma unroll 1
+      for (int J = t; J < Z2; J += TW) {
+        C x[Z1];
+#pragma unroll
+        for (int a = 0; a < Z1; ++a) {
+          const int idx = pmod(J + Z2 * a - l0, N3);
+          x[a] = idx < cnt ? src[g0 + idx] : czero<C>();
+        }
+        dftR<C, +1, Z1>(x);
+        if (J) {
+#pragma unroll
+          for (int m = 1; m < Z1; ++m) x[m] = cmul(x[m], cconj(__ldg(&twz[J * (Z1 - 1) + m - 1])));
+        }
+#pragma unroll
+        for (int m = 0; m < Z1; ++m) line[J + Z2 * m] = x[m];
+      }
+    }
+    __syncthreads();
+    if (live) {
+#pragma unroll 1
+      for (int blk = t; blk < Z1; blk += TW) {
+        C y[Z2];
+#pragma unroll
+        for (int m = 0; m < Z2; ++m) y[m] = line[blk * Z2 + m];
+        dftR<C, +1, Z2>(y);
+#pragma unroll
+        for (int m = 0; m < Z2; ++m) line[blk * Z2 + m] = y[m];
+      }
+    }
+  }
+  __syncthreads();
+  // y-lines, one slice of 32 columns at a time; rows without coefficients read as zero
+  C* dst = hb + (int64_t)b * hb_bs + (int64_t)p * N2 * N3;
+  C* col = S + lane;
+#pragma unroll 1
+  for (int sc = 0; sc < PR::NSL; ++sc) {
+    const int c = sc * 32 + lane;
+    const bool livec = c < N3;
+#pragma unroll 1
+    for (int J = t; J < Y2; J += TW) {
+      C x[Y1];
+#pragma unroll
+      for (int a = 0; a < Y1; ++a) {
+        const int i = ymap[J + Y2 * a];
+        x[a] = (livec && i >= 0) ? R[(size_t)i * FR + c] : czero<C>();
+      }
+      dftR<C, +1, Y1>(x);
+      if (J) {
+#pragma unroll
+        for (int m = 1; m < Y1; ++m) x[m] = cmul(x[m], cconj(__ldg(&twy[J * (Y1 - 1) + m - 1])));
+      }
+#pragma unroll
+      for (int m = 0; m < Y1; ++m) col[(J + Y2 * m) * SP] = x[m];
+    }
+    __syncthreads();
+#pragma unroll 1
+    for (int blk = t; blk < Y1; blk += TW) {
+      C y[Y2];
+#pragma unroll
+      for (int m = 0; m < Y2; ++m) y[m] = col[(blk * Y2 + m) * SP];
+      dftR<C, +1, Y2>(y);
+      if (livec) {
+#pragma unroll
+        for (int m = 0; m < Y2; ++m) dst[(int64_t)(blk * Y2 + m) * N3 + c] = y[m];
+      }
+    }
+    __syncthreads();
+  }
+}
+
+template <typename T, int N2, int N3, int TW, bool REC>
+__global__ void __launch_bounds__(PlaneR<N2, N3, TW>::THREADS) k_plane_fwd_rs(const cplx<T>* __restrict__ hb,
+                                                                               int64_t hb_bs, SphereDev sp, FftPlan plan,
+                                                                               const cplx<T>* __restrict__ tw,
+                                                                               const T* __restrict__ kin,
+                                                                               const cplx<T>* __restrict__ psi,
+                                                                               int64_t ldpsi, cplx<T>* __restrict__ out,
+                                                                               int64_t ldout, Pass3Rec rec) {
+  using C = cplx<T>;
+  using PR = PlaneR<N2, N3, TW>;
+  constexpr int FR = PR::FR, SP = PR::SP;
+  constexpr int Y1 = PR::P2.radix[0], Y2 = PR::P2.radix[1];
+  constexpr int Z1 = PR::P3.radix[0], Z2 = PR::P3.radix[1];
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* R = reinterpret_cast<C*>(smem_raw);
+  C* S = R + (size_t)sp.max_rows * FR;
+  int* ymap = reinterpret_cast<int*>(S + N2 * SP);
+  const int lane = threadIdx.x & 31, t = threadIdx.x >> 5;
+  const int p = blockIdx.x, b = blockIdx.y;
+  const int r0 = sp.plane_row0[p], nr = sp.plane_row0[p + 1] - r0;
+  const C* srcp = hb + (int64_t)b * hb_bs + (int64_t)p * N2 * N3;
+  const C* twy = tw + plan.d[1].tw_off[0];
+  const C* twz = tw + plan.d[2].tw_off[0];
+  for (int i = threadIdx.x; i < N2; i += blockDim.x) ymap[i] = -1;
+  __syncthreads();
+  for (int i = threadIdx.x; i < nr; i += blockDim.x) ymap[pmod(sp.row_k[r0 + i], N2)] = i;
+  __syncthreads();
+  // y-lines, one slice of 32 columns at a time: radix Y2 blocks read from the half-box plane,
+  // then radix Y1 with twiddles; only the sphere rows are kept (in R)
+  C* col = S + lane;
+#pragma unroll 1
+  for (int sc = 0; sc < PR::NSL; ++sc) {
+    const int c = sc * 32 + lane;
+    const bool livec = c < N3;
+#pragma unroll 1
+    for (int blk = t; blk < Y1; blk += TW) {
+      C y[Y2];
+#pragma unroll
+      for (int m = 0; m < Y2; ++m) y[m] = livec ? srcp[(int64_t)(blk * Y2 + m) * N3 + c] : czero<C>();
+      dftR<C, -1, Y2>(y);
+#pragma unroll
+      for (int m = 0; m < Y2; ++m) col[(blk * Y2 + m) * SP] = y[m];
+    }
+    __syncthreads();
+#pragma unroll 1
+    for (int J = t; J < Y2; J += TW) {
+      C x[Y1];
+#pragma unroll
+      for (int m = 0; m < Y1; ++m) x[m] = col[(J + Y2 * m) * SP];
+      if (J) {
+#pragma unroll
+        for (int m = 1; m < Y1; ++m) x[m] = cmul(x[m], __ldg(&twy[J * (Y1 - 1) + m - 1]));
+      }
+      dftR<C, -1, Y1>(x);
+#pragma unroll
+      for (int a = 0; a < Y1; ++a) {
+        const int i = ymap[J + Y2 * a];
+        if (livec && i >= 0) R[(size_t)i * FR + c] = x[a];
+      }
+    }
+    __syncthreads();
+  }
+  // z-lines of the sphere rows, 32 rows at a time, in place in R
+  for (int c0 = 0; c0 < nr; c0 += 32) {
+    const int row = c0 + lane;
+    const bool live = row < nr;
+    C* line = R + (size_t)(live ? row : 0) * FR;
+    if (live) {
+#pragma unroll 1
+      for (int blk = t; blk < Z1; blk += TW) {
+        C y[Z2];
+#pragma unroll
+        for (int m = 0; m < Z2; ++m) y[m] = line[blk * Z2 + m];
+        dftR<C, -1, Z2>(y);
+#pragma unroll
+        for (int m = 0; m < Z2; ++m) line[blk * Z2 + m] = y[m];
+      }
+    }
+    __syncthreads();
+    if (live) {
+#pragma unroll 1
+      for (int J = t; J < Z2; J += TW) {
+        C x[Z1];
+#pragma unroll
+        for (int m = 0; m < Z1; ++m) x[m] = line[J + Z2 * m];
+        if (J) {
+#pragma unroll
+          for (int m = 1; m < Z1; ++m) x[m] = cmul(x[m], __ldg(&twz[J * (Z1 - 1) + m - 1]));
+        }
+        dftR<C, -1, Z1>(x);
+#pragma unroll
+        for (int a = 0; a < Z1; ++a) line[J + Z2 * a] = x[a];
+      }
+    }
+    __syncthreads();
+  }
+  // gather the plane's coefficients, one warp per row (coalesced reads and writes), with the
+  // kinetic term (and the recurrence)
+  const C* yv = psi + (int64_t)b * ldpsi;
+  C* o = out + (int64_t)b * ldout;
+  T ra = 0, rs = 0;  // recurrence alpha and shift
+  if constexpr (REC) {
+    ra = (T)rec.alpha;
+    rs = (T)rec.shift;
+    if (rec.dev_ce) {
+      rs = (T)rec.dev_ce[0];
+      ra = (T)((rec.first ? 1.0 : 2.0) / rec.dev_ce[1]);
+    }
+  }
+  for (int row = t; row < nr; row += TW) {
+    const int g0 = sp.row_g0[r0 + row], cnt = sp.row_cnt[r0 + row], l0 = sp.row_l0[r0 + row];
+    const C* line = R + (size_t)row * FR;
+    for (int idx = lane; idx < cnt; idx += 32) {
+      const C v = line[pmod(l0 + idx, N3)];
+      const int gg = g0 + idx;
+      const C yy = yv[gg];
+      const T k = kin[gg];
+      if constexpr (!REC) {
+        o[gg] = mk<C>(k * yy.x + v.x, k * yy.y + v.y);
+      } else {
+        const C pz = ((const C*)rec.pz)[(int64_t)b * rec.ldpz + gg];
+        C r = mk<C>(ra * (k * yy.x + v.x + pz.x - rs * yy.x), ra * (k * yy.y + v.y + pz.y - rs * yy.y));
+        if (rec.ykm1) {
+          const C ym = ((const C*)rec.ykm1)[(int64_t)b * rec.ldykm1 + gg];
+          r.x -= (T)rec.beta * ym.x;
+          r.y -= (T)rec.beta * ym.y;
+        }
+        o[gg] = r;
+        if (rec.split) {
+          __nv_bfloat16* sb = (__nv_bfloat16*)rec.split + (int64_t)b * rec.split_ld + 2 * (int64_t)gg;
+          float re = (float)r.x, im = (float)r.y;
+          for (int pc = 0; pc < rec.pieces; ++pc) {
+            const __nv_bfloat16 hr = __float2bfloat16_rn(re), hi = __float2bfloat16_rn(im);
+            __nv_bfloat162 two;
+            two.x = hr;
+            two.y = hi;
+            *reinterpret_cast<__nv_bfloat162*>(sb + (int64_t)pc * rec.split_piece_stride) = two;
+            re -= __bfloat162float(hr);
+            im -= __bfloat162float(hi);
+          }
+        }
+      }
+    }
+  }
+}
+
+template <typename T, int N2, int N3, int TW>
+static size_t plane_rs_smem(const SphereDev& sp) {
+  return sizeof(cplx<T>) * ((size_t)sp.max_rows * PlaneR<N2, N3, TW>::FR + (size_t)N2 * PlaneR<N2, N3, TW>::SP) +
+         sizeof(int) * N2;
+}
+
+template <typename T, int N2, int N3, int TW>
+static cudaError_t plane_rs_pair(int which, const cplx<T>* psi, int64_t ldpsi, cplx<T>* hb, int64_t hb_bs,
+                                 const SphereDev& sp, const FftPlan& plan, const cplx<T>* tw, const T* kin,
+                                 cplx<T>* out, int64_t ldout, int nb, cudaStream_t st, const Pass3Rec* rec) {
+  using PR = PlaneR<N2, N3, TW>;
+  if constexpr (!PR::ok || !std::is_same<T, float>::value) {
+    return cudaErrorNotSupported;
+  } else {
+    const size_t sm = plane_rs_smem<T, N2, N3, TW>(sp);
+    if (sm > 227 * 1024) return cudaErrorNotSupported;
+    cudaError_t e;
+    const dim3 grid(sp.nplane, nb);
+    if (which == 0) {
+      if ((e = cudaFuncSetAttribute(k_plane_inv_rs<T, N2, N3, TW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)sm)))
+        return e;
+      k_plane_inv_rs<T, N2, N3, TW><<<grid, PR::THREADS, sm, st>>>(psi, ldpsi, hb, hb_bs, sp, plan, tw); count_launch();
+    } else if (rec) {
+      if ((e = cudaFuncSetAttribute(k_plane_fwd_rs<T, N2, N3, TW, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)sm)))
+        return e;
+      k_plane_fwd_rs<T, N2, N3, TW, true><<<grid, PR::THREADS, sm, st>>>(hb, hb_bs, sp, plan, tw, kin, psi, ldpsi,
+                                                                        out, ldout, *rec); count_launch();
+    } else {
+      if ((e = cudaFuncSetAttribute(k_plane_fwd_rs<T, N2, N3, TW, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)sm)))
+        return e;
+      k_plane_fwd_rs<T, N2, N3, TW, false><<<grid, PR::THREADS, sm, st>>>(hb, hb_bs, sp, plan, tw, kin, psi, ldpsi,
+                                                                         out, ldout, Pass3Rec{}); count_launch();
+    }
+    return cudaGetLastError();
+  }
+}
+
+template <typename T>
+static cudaError_t plane_rs(int which, const cplx<T>* psi, int64_t ldpsi, cplx<T>* hb, int64_t hb_bs,
+                            const SphereDev& sp, const FftPlan& plan, const cplx<T>* tw, const T* kin, cplx<T>* out,
+                            int64_t ldout, int nb, cudaStream_t st, const Pass3Rec* rec = nullptr) {
+  const int n2 = plan.n[1], n3 = plan.n[2];
+#define PW_RS_CASE(A, B, TWN)                                                                                  \
+  if (n2 == A && n3 == B)                                                                                      \
+    return plane_rs_pair<T, A, B, TWN>(which, psi, ldpsi, hb, hb_bs, sp, plan, tw, kin, out, ldout, nb, st, rec);
+  PW_RS_CASE(64, 64, 8)
+  PW_RS_CASE(72, 90, 8)
+  PW_RS_CASE(96, 96, 8)
+  PW_RS_CASE(120, 120, 8)
+#undef PW_RS_CASE
   return cudaErrorNotSupported;
 }
 
@@ -2227,10 +2545,11 @@ cudaError_t launch_local_apply(const FftPlan& plan, const cplx<T>* tw, const Sph
   // kernel forms (complex64): x-line form = variant % 8 (0 line groups, 1 one thread per
   // line, 2 warp groups with compile-time twiddles, 3 warp groups with table twiddles, 4 the
   // same with several bands per CTA), plane form = variant / 8 (0 line groups, 1 one thread
-  // per line, 2 warp groups)
+  // per line, 2 warp groups over the whole plane, 3 warp groups over sphere rows and 32-column
+  // slices)
   const int fv = (std::is_same<T, float>::value && prof) ? prof->fft_variant[0] : 0;
   const int xf = fv % 8, pf = fv / 8;
-  const bool tpl = pf == 1, pwg = pf == 2;
+  const bool tpl = pf == 1, pwg = pf == 2, prs = pf == 3;
   const bool xtw = xf == 2, xtwr = xf == 3 || xf == 4;
   for (int b0 = 0; b0 < nband; b0 += band_batch) {
     const int nb = min(band_batch, nband - b0);
@@ -2239,6 +2558,7 @@ cudaError_t launch_local_apply(const FftPlan& plan, const cplx<T>* tw, const Sph
     if constexpr (std::is_same<T, float>::value) {
       if (tpl) e = plane_tpl<T>(0, psi + b0 * ldpsi, ldpsi, hb, hb_bs, sp, plan, kin, nullptr, 0, nb, st);
       if (pwg) e = plane_wg<T>(0, psi + b0 * ldpsi, ldpsi, hb, hb_bs, sp, plan, tw, kin, nullptr, 0, nb, st);
+      if (prs) e = plane_rs<T>(0, psi + b0 * ldpsi, ldpsi, hb, hb_bs, sp, plan, tw, kin, nullptr, 0, nb, st);
     }
     if (e == cudaErrorNotSupported) {
       (void)cudaGetLastError();
@@ -2278,6 +2598,8 @@ cudaError_t launch_local_apply(const FftPlan& plan, const cplx<T>* tw, const Sph
       if (tpl) e = plane_tpl<T>(1, psi + b0 * ldpsi, ldpsi, hb, hb_bs, sp, plan, kin, out + b0 * ldout, ldout, nb, st);
       if (pwg)
         e = plane_wg<T>(1, psi + b0 * ldpsi, ldpsi, hb, hb_bs, sp, plan, tw, kin, out + b0 * ldout, ldout, nb, st);
+      if (prs)
+        e = plane_rs<T>(1, psi + b0 * ldpsi, ldpsi, hb, hb_bs, sp, plan, tw, kin, out + b0 * ldout, ldout, nb, st);
     }
     if (e == cudaErrorNotSupported) {
       (void)cudaGetLastError();
@@ -2295,8 +2617,15 @@ cudaError_t launch_local_apply(const FftPlan& plan, const cplx<T>* tw, const Sph
   return cudaGetLastError();
 }
 
+static bool plane_rs_covers(const FftPlan& plan) {
+  const int n2 = plan.n[1], n3 = plan.n[2];
+  return (n2 == 64 && n3 == 64) || (n2 == 72 && n3 == 90) || (n2 == 96 && n3 == 96) || (n2 == 120 && n3 == 120);
+}
+
 bool local_apply_rec_supported(const FftPlan& plan, const ::pw_ctx* prof) {
-  return prof && prof->fft_variant[0] / 8 == 2 && plane_wg_covers(plan);
+  if (!prof) return false;
+  const int pf = prof->fft_variant[0] / 8;
+  return (pf == 2 && plane_wg_covers(plan)) || (pf == 3 && plane_rs_covers(plan));
 }
 
 cudaError_t launch_local_apply_rec(const FftPlan& plan, const float2* tw, const SphereDev& sp, const float* vperm,
@@ -2307,6 +2636,7 @@ cudaError_t launch_local_apply_rec(const FftPlan& plan, const float2* tw, const 
   if (!local_apply_rec_supported(plan, prof)) return cudaErrorNotSupported;
   if (nband <= 0) return cudaSuccess;
   const int xf = prof->fft_variant[0] % 8;
+  const bool prs = prof->fft_variant[0] / 8 == 3;
   const int64_t hb_bs = (int64_t)sp.nplane * plan.n[1] * plan.n[2];
   const int nyz = plan.n[1] * plan.n[2];
   const int lyz = 32;
@@ -2315,7 +2645,9 @@ cudaError_t launch_local_apply_rec(const FftPlan& plan, const float2* tw, const 
   for (int b0 = 0; b0 < nband; b0 += band_batch) {
     const int nb = min(band_batch, nband - b0);
     prof_begin(prof, PW_PROF_PLANE_INV);
-    if ((e = plane_wg<T>(0, psi + b0 * ldpsi, ldpsi, hb, hb_bs, sp, plan, tw, kin, nullptr, 0, nb, st))) return e;
+    if ((e = (prs ? plane_rs<T> : plane_wg<T>)(0, psi + b0 * ldpsi, ldpsi, hb, hb_bs, sp, plan, tw, kin, nullptr, 0,
+                                                nb, st, nullptr)))
+      return e;
     prof_end(prof, PW_PROF_PLANE_INV);
     prof_begin(prof, PW_PROF_XLINE);
     e = cudaErrorNotSupported;
@@ -2339,8 +2671,8 @@ cudaError_t launch_local_apply_rec(const FftPlan& plan, const float2* tw, const 
     r.pz = rec.pz + b0 * rec.ldpz;
     if (rec.ykm1) r.ykm1 = rec.ykm1 + b0 * rec.ldykm1;
     if (rec.split) r.split = (__nv_bfloat16*)rec.split + b0 * rec.split_ld;
-    if ((e = plane_wg<T>(1, psi + b0 * ldpsi, ldpsi, hb, hb_bs, sp, plan, tw, kin, out + b0 * ldout, ldout, nb, st,
-                         &r)))
+    if ((e = (prs ? plane_rs<T> : plane_wg<T>)(1, psi + b0 * ldpsi, ldpsi, hb, hb_bs, sp, plan, tw, kin,
+                                                out + b0 * ldout, ldout, nb, st, &r)))
       return e;
     prof_end(prof, PW_PROF_PLANE_FWD);
   }

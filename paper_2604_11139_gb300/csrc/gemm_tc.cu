@@ -13,9 +13,11 @@
 //
 // Kernel: one 128 x 128 output tile per CTA, K in 64-wide slices; warp 0 lane 0
 // issues TMA loads (128B-swizzled, K-major) into a multi-stage ring, warp 1 lane 0
-// issues tcgen05.mma from shared memory into a 128-column TMEM accumulator, all four
-// warps run the epilogue (tcgen05.ld, one TMEM lane = one output row per thread).
-// Every mbarrier wait is bounded; on expiry the kernel records an error and returns.
+// issues tcgen05.mma from shared memory into 128-column TMEM accumulators, four warps
+// promote them into a running sum and four more write the output (tcgen05.ld, one TMEM lane
+// = one output row per thread).
+// Every mbarrier wait is bounded; on expiry the kernel records the stage in *err, waits
+// (bounded) for the copies and MMAs it has issued, releases TMEM and returns.
 #include <cuda.h>
 #include <cuda_bf16.h>
 
@@ -23,6 +25,7 @@
 
 #include "pw_internal.cuh"
 #include "tc.cuh"
+#include "tc_ptx.cuh"
 
 namespace pw {
 namespace tc {
@@ -30,6 +33,7 @@ namespace tc {
 constexpr int BM = 128, BN = 128, BK = 64;
 constexpr int TILE_BYTES = BM * BK * 2;  // 16 KB; BN == BM
 constexpr uint32_t kSpinLimit = 1u << 24;
+constexpr uint32_t kSpinTest = 1u << 12;  // wait limit of the failure-path test (no copies issued)
 
 template <int P> struct Cfg {
   static constexpr int STAGE_BYTES = 2 * P * TILE_BYTES;
@@ -47,10 +51,10 @@ __device__ __forceinline__ void mbar_init(uint64_t* b, uint32_t count) {
 __device__ __forceinline__ void mbar_expect_tx(uint64_t* b, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(b)), "r"(bytes) : "memory");
 }
-// bounded wait for the phase of parity `par` to complete; false on expiry
-__device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t par) {
+// bounded wait for the phase of parity `par` to complete; false after `limit` polls
+__device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t par, uint32_t limit) {
   const uint32_t a = smem_u32(b);
-  for (uint32_t it = 0; it < kSpinLimit; ++it) {
+  for (uint32_t it = 0; it < limit; ++it) {
     uint32_t ok;
     asm volatile(
         "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
@@ -183,17 +187,20 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* b) {
 //   warp 0 lane 0: TMA producer over the units' K slices (ring of STAGES slots);
 //   warp 1 lane 0: MMA issuer; each group of kprom 64-wide K slices accumulates into one
 //                  of two TMEM buffers (128 columns each), starting from zero;
-//   warps 2-5:     drain each finished buffer into a third TMEM buffer holding the
+//   warps 2-5:     drain each finished buffer into a TMEM buffer holding the unit's
 //                  running sum (round-to-nearest FP32 adds in registers, one output
-//                  row per thread, 32 columns at a time), then run the output
-//                  epilogue once per unit.
+//                  row per thread, 32 columns at a time); two running-sum buffers
+//                  alternate between units;
+//   warps 6-9:     run the output epilogue of a finished unit from its running-sum buffer
+//                  while warps 2-5 accumulate the next unit in the other one.
 // The tensor core adds its products into the TMEM accumulator with truncation; summing
 // few K slices there (one with 3 pieces) and the groups in registers keeps the
 // accumulated rounding bias below the error of the bf16 pieces themselves.
 template <int P>
-__global__ void __launch_bounds__(192, 1) k_tc_gemm(const __grid_constant__ CUtensorMap tmA,
+__global__ void __launch_bounds__(320, 1) k_tc_gemm(const __grid_constant__ CUtensorMap tmA,
                                                     const __grid_constant__ CUtensorMap tmB, int M, int N, int K,
-                                                    int kchunk, int nsplit, int kprom, TcEpi epi, int* err) {
+                                                    int kchunk, int nsplit, int kprom, TcEpi epi, int* err,
+                                                    uint32_t spin, int no_copies) {
   using CF = Cfg<P>;
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t* base = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -201,7 +208,10 @@ __global__ void __launch_bounds__(192, 1) k_tc_gemm(const __grid_constant__ CUte
   uint64_t* empty = full + CF::STAGES;
   uint64_t* tfull = empty + CF::STAGES;  // [2]
   uint64_t* tempty = tfull + 2;          // [2]
-  uint32_t* tmem_slot = (uint32_t*)(tempty + 2);
+  uint64_t* sready = tempty + 2;         // [2] running sum of a unit complete (promotion -> output)
+  uint64_t* sfree = sready + 2;          // [2] running-sum buffer written out (output -> promotion)
+  uint64_t* mdone = sfree + 2;           // completion of every MMA issued (exit path)
+  uint32_t* tmem_slot = (uint32_t*)(mdone + 1);
   volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -210,7 +220,13 @@ __global__ void __launch_bounds__(192, 1) k_tc_gemm(const __grid_constant__ CUte
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < CF::STAGES; ++s) { mbar_init(&full[s], 1); mbar_init(&empty[s], 1); }
-    for (int b = 0; b < 2; ++b) { mbar_init(&tfull[b], 1); mbar_init(&tempty[b], 4); }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&tfull[b], 1);
+      mbar_init(&tempty[b], 4);
+      mbar_init(&sready[b], 4);
+      mbar_init(&sfree[b], 4);
+    }
+    mbar_init(mdone, 1);
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -229,17 +245,21 @@ __global__ void __launch_bounds__(192, 1) k_tc_gemm(const __grid_constant__ CUte
     if (lane == 0) {
       // ---- TMA producer
       int g = 0;
+      int last_it[CF::STAGES];
+      for (int s = 0; s < CF::STAGES; ++s) last_it[s] = -1;
       for (int u = blockIdx.x; u < nunits && !*abort_flag; u += gridDim.x) {
         const int n0 = (u % ntn) * BN, m0 = ((u / ntn) % ntm) * BM, z = u / (ntn * ntm);
         const int kbeg = z * kchunk, kend = min(K, kbeg + kchunk);
         const int nkb = (kend > kbeg) ? (kend - kbeg + BK - 1) / BK : 0;
         for (int kb = 0; kb < nkb; ++kb, ++g) {
           const int s = g % CF::STAGES, it = g / CF::STAGES;
-          if (it > 0 && !mbar_wait(&empty[s], (it - 1) & 1)) {
+          if (it > 0 && !mbar_wait(&empty[s], (it - 1) & 1, spin)) {
             atomicExch(err, 1);
             *abort_flag = 1;
             break;
           }
+          if (no_copies) continue;
+          last_it[s] = it;
           mbar_expect_tx(&full[s], CF::STAGE_BYTES);
           const uint32_t sb = smem_u32(base + s * CF::STAGE_BYTES);
           const int k = kbeg + kb * BK;
@@ -249,6 +269,9 @@ __global__ void __launch_bounds__(192, 1) k_tc_gemm(const __grid_constant__ CUte
           for (int p = 0; p < P; ++p) tma_load_3d(sb + (P + p) * TILE_BYTES, &tmB, k, n0, p, &full[s]);
         }
       }
+      // every copy issued has landed before the CTA may release its shared memory
+      for (int s = 0; s < CF::STAGES; ++s)
+        if (last_it[s] >= 0 && !mbar_wait(&full[s], last_it[s] & 1, spin)) atomicExch(err, 4);
     }
   } else if (warp == 1) {
     if (lane == 0) {
@@ -264,7 +287,7 @@ __global__ void __launch_bounds__(192, 1) k_tc_gemm(const __grid_constant__ CUte
           const bool gfirst = (kb % kprom) == 0;
           const bool glast = ((kb + 1) % kprom) == 0 || kb + 1 == nkb;
           const int tb = G & 1, tu = G >> 1;
-          if (!mbar_wait(&full[s], it & 1) || (gfirst && tu > 0 && !mbar_wait(&tempty[tb], (tu - 1) & 1))) {
+          if (!mbar_wait(&full[s], it & 1, spin) || (gfirst && tu > 0 && !mbar_wait(&tempty[tb], (tu - 1) & 1, spin))) {
             atomicExch(err, 2);
             *abort_flag = 1;
             break;
@@ -293,22 +316,33 @@ __global__ void __launch_bounds__(192, 1) k_tc_gemm(const __grid_constant__ CUte
           }
         }
       }
+      // every MMA issued has completed before TMEM and shared memory are released
+      mma_commit(mdone);
+      if (!mbar_wait(mdone, 0, spin)) atomicExch(err, 5);
     }
-  } else {
-    // ---- epilogue warps 2..5: TMEM lane quarter (warp % 4)
+  } else if (warp < 6) {
+    // ---- promotion warps 2..5: TMEM lane quarter (warp % 4)
     const int q = warp & 3;
     const uint32_t lane_off = (uint32_t)(q * 32) << 16;
     int G = 0;  // promotion groups drained
-    for (int u = blockIdx.x; u < nunits; u += gridDim.x) {
-      const int n0 = (u % ntn) * BN, m0 = ((u / ntn) % ntm) * BM, z = u / (ntn * ntm);
+    int lu = 0;  // units of this CTA so far
+    for (int u = blockIdx.x; u < nunits; u += gridDim.x, ++lu) {
+      const int z = u / (ntn * ntm);
       const int kbeg = z * kchunk, kend = min(K, kbeg + kchunk);
       const int nkb = (kend > kbeg) ? (kend - kbeg + BK - 1) / BK : 0;
       const int ngrp = (nkb + kprom - 1) / kprom;
-      const uint32_t sum_base = tmem + lane_off + (uint32_t)(2 * BN);  // running-sum buffer
+      const int sb = lu & 1;
+      const uint32_t sum_base = tmem + lane_off + (uint32_t)((2 + sb) * BN);  // running sum of this unit
+      // the writers have finished the unit that used this running-sum buffer before
+      if (lu >= 2 && !mbar_wait(&sfree[sb], ((lu >> 1) + 1) & 1, spin)) {
+        atomicExch(err, 6);
+        *abort_flag = 1;
+        break;
+      }
       bool ok = true;
       for (int kb = 0; kb < ngrp; ++kb, ++G) {
         const int tb = G & 1, tu = G >> 1;
-        if (!mbar_wait(&tfull[tb], tu & 1)) {
+        if (!mbar_wait(&tfull[tb], tu & 1, spin)) {
           ok = false;
           atomicExch(err, 3);
           *abort_flag = 1;
@@ -339,56 +373,83 @@ __global__ void __launch_bounds__(192, 1) k_tc_gemm(const __grid_constant__ CUte
         if (lane == 0) mbar_arrive(&tempty[tb]);
       }
       if (!ok) break;
+      // the unit's running sum is complete: hand it to the writers
+      fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&sready[sb]);
+    }
+  } else {
+    // ---- output warps 6..9: TMEM lane quarter (warp % 4); they write unit u's result while
+    // the promotion warps already accumulate unit u + 1 in the other running-sum buffer
+    const int q = warp & 3;
+    const uint32_t lane_off = (uint32_t)(q * 32) << 16;
+    int lu = 0;
+    for (int u = blockIdx.x; u < nunits; u += gridDim.x, ++lu) {
+      const int n0 = (u % ntn) * BN, m0 = ((u / ntn) % ntm) * BM, z = u / (ntn * ntm);
+      const int kbeg = z * kchunk, kend = min(K, kbeg + kchunk);
+      const int nkb = (kend > kbeg) ? (kend - kbeg + BK - 1) / BK : 0;
+      const int sb = lu & 1;
+      if (!mbar_wait(&sready[sb], (lu >> 1) & 1, spin)) {
+        atomicExch(err, 7);
+        *abort_flag = 1;
+        break;
+      }
+      fence_after();
+      const uint32_t sum_base = tmem + lane_off + (uint32_t)((2 + sb) * BN);
       const int r = m0 + q * 32 + lane;
+      float alpha = epi.alpha, shift = epi.shift;
+      if (epi.mode == TC_EPI_CHEB && epi.dev_ce) {
+        shift = (float)epi.dev_ce[0];
+        alpha = (float)((epi.first ? 1.0 : 2.0) / epi.dev_ce[1]);
+      }
 #pragma unroll 1
-      for (int c = 0; c < BN / 32; ++c) {
-        float acc[32];
+      for (int c = 0; c < BN / 16; ++c) {
+        uint32_t ar[16];
+        float acc[16];
         if (nkb > 0) {
-          tmem_ld32(sum_base + (uint32_t)(c * 32), acc);
+          tcp::tmem_ld16_async(sum_base + (uint32_t)(c * 16), ar);
+          tcp::tmem_wait_ld16(ar);
+#pragma unroll
+          for (int i = 0; i < 16; ++i) acc[i] = __uint_as_float(ar[i]);
         } else {
 #pragma unroll
-          for (int i = 0; i < 32; ++i) acc[i] = 0.f;
+          for (int i = 0; i < 16; ++i) acc[i] = 0.f;
         }
         if (r >= M) continue;
-        const int jc = n0 + c * 32;
+        const int jc = n0 + c * 16;
         if (epi.mode == TC_EPI_PARTIAL) {
           float* __restrict__ o = epi.part + (int64_t)z * epi.part_split_stride + (int64_t)jc * epi.part_ld + r;
 #pragma unroll
-          for (int i = 0; i < 32; ++i)
+          for (int i = 0; i < 16; ++i)
             if (jc + i < N) o[(int64_t)i * epi.part_ld] = acc[i];
         } else if (epi.mode == TC_EPI_STORE) {
           float* __restrict__ o = epi.out + (int64_t)jc * epi.ldo + r;
 #pragma unroll
-          for (int i = 0; i < 32; ++i)
-            if (jc + i < N) o[(int64_t)i * epi.ldo] = epi.alpha * acc[i];
+          for (int i = 0; i < 16; ++i)
+            if (jc + i < N) o[(int64_t)i * epi.ldo] = alpha * acc[i];
         } else if (epi.mode == TC_EPI_ACCUM) {
           float* __restrict__ o = epi.out + (int64_t)jc * epi.ldo + r;
-          float wv[32];
+          float wv[16];
 #pragma unroll
-          for (int i = 0; i < 32; ++i) wv[i] = (jc + i < N) ? o[(int64_t)i * epi.ldo] : 0.f;
+          for (int i = 0; i < 16; ++i) wv[i] = (jc + i < N) ? o[(int64_t)i * epi.ldo] : 0.f;
 #pragma unroll
-          for (int i = 0; i < 32; ++i)
-            if (jc + i < N) o[(int64_t)i * epi.ldo] = wv[i] + epi.alpha * acc[i];
+          for (int i = 0; i < 16; ++i)
+            if (jc + i < N) o[(int64_t)i * epi.ldo] = wv[i] + alpha * acc[i];
         } else {
           float* __restrict__ o = epi.out + (int64_t)jc * epi.ldo + r;
           const float* __restrict__ yk = epi.yk + (int64_t)jc * epi.ldyk + r;
           const float* __restrict__ ym = epi.ykm1 ? epi.ykm1 + (int64_t)jc * epi.ldykm1 + r : nullptr;
-          float alpha = epi.alpha, shift = epi.shift;
-          if (epi.dev_ce) {
-            shift = (float)epi.dev_ce[0];
-            alpha = (float)((epi.first ? 1.0 : 2.0) / epi.dev_ce[1]);
-          }
-          // issue all loads of the 32 columns before using any of them
-          float wv[32], y1[32], y2[32];
+          // issue all loads of the 16 columns before using any of them
+          float wv[16], y1[16], y2[16];
 #pragma unroll
-          for (int i = 0; i < 32; ++i) {
+          for (int i = 0; i < 16; ++i) {
             const bool v = (jc + i) < N;
             wv[i] = v ? o[(int64_t)i * epi.ldo] : 0.f;
             y1[i] = v ? yk[(int64_t)i * epi.ldyk] : 0.f;
             y2[i] = (v && ym) ? ym[(int64_t)i * epi.ldykm1] : 0.f;
           }
 #pragma unroll
-          for (int i = 0; i < 32; ++i) {
+          for (int i = 0; i < 16; ++i) {
             if (jc + i < N) {
               const float y = alpha * (wv[i] + acc[i] - shift * y1[i]) - epi.beta * y2[i];
               o[(int64_t)i * epi.ldo] = y;
@@ -397,6 +458,9 @@ __global__ void __launch_bounds__(192, 1) k_tc_gemm(const __grid_constant__ CUte
           }
         }
       }
+      fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&sfree[sb]);
     }
   }
   fence_before();
@@ -511,7 +575,8 @@ static bool make_map(CUtensorMap* m, const __nv_bfloat16* ptr, int64_t kext, int
 bool available() { return encode_fn() != nullptr; }
 
 cudaError_t gemm(const Operand& A, const Operand& B, int M, int N, int K, int pieces, int nsplit, const TcEpi& epi,
-                 int* err, cudaStream_t st) {
+                 int* err, cudaStream_t st, int test_no_copies) {
+  const uint32_t spin = test_no_copies ? kSpinTest : kSpinLimit;
   // K slices summed in TMEM between promotions to the FP32 running sum.  One: with four
   // slices per promotion in the back-projection (2 pieces) the filter's eigenvalue error
   // against FP64 grew from 2.7e-7 to 6.8e-7 Ha on the 96^3 workload for 2.5% of speed.
@@ -536,10 +601,12 @@ cudaError_t gemm(const Operand& A, const Operand& B, int M, int N, int K, int pi
   cudaError_t e;
   if (pieces == 2) {
     if ((e = cudaFuncSetAttribute(k_tc_gemm<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg<2>::SMEM))) return e;
-    k_tc_gemm<2><<<grid, 192, Cfg<2>::SMEM, st>>>(ma, mb, M, N, K, kchunk, nsplit, kprom, epi, err); count_launch();
+    k_tc_gemm<2><<<grid, 320, Cfg<2>::SMEM, st>>>(ma, mb, M, N, K, kchunk, nsplit, kprom, epi, err, spin,
+                                                   test_no_copies); count_launch();
   } else {
     if ((e = cudaFuncSetAttribute(k_tc_gemm<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg<3>::SMEM))) return e;
-    k_tc_gemm<3><<<grid, 192, Cfg<3>::SMEM, st>>>(ma, mb, M, N, K, kchunk, nsplit, kprom, epi, err); count_launch();
+    k_tc_gemm<3><<<grid, 320, Cfg<3>::SMEM, st>>>(ma, mb, M, N, K, kchunk, nsplit, kprom, epi, err, spin,
+                                                   test_no_copies); count_launch();
   }
   return cudaGetLastError();
 }

@@ -17,6 +17,7 @@
 #include "pw_internal.cuh"
 #include "setup.cuh"
 #include "tc.cuh"
+#include "zgemm.cuh"
 
 namespace pw {
 
@@ -298,6 +299,14 @@ int tc_split(pw_ctx* ctx, const float2* x, int64_t ld, int nrow, int nb, int64_t
   return PW_OK;
 }
 
+// bf16 pieces of a complex64 block into rows of an existing buffer with piece stride `ps`
+int tc_split_into(pw_ctx* ctx, const float2* x, int64_t ld, int nrow, int nb, int64_t pitch, int64_t ps,
+                  __nv_bfloat16* buf) {
+  CU_TRY(tc::split_f32((const float*)x, 2 * ld, 2 * nrow, nb, ctx->tc_pieces, buf, pitch, ps, ctx->stream),
+         "bf16 split");
+  return PW_OK;
+}
+
 // C (np x nb complex64, ld np) = P^dagger Y from the bf16 pieces of Y
 int tc_project(pw_ctx* ctx, const __nv_bfloat16* ysplit, int nb, float2* Cout) {
   const int np = ctx->nproj, npw = ctx->npw, pc = ctx->tc_pieces;
@@ -322,7 +331,9 @@ int tc_project(pw_ctx* ctx, const __nv_bfloat16* ysplit, int nb, float2* Cout) {
   e.part = part;
   e.part_ld = M;
   e.part_split_stride = (int64_t)M * N;
-  CU_TRY(tc::gemm(A, B, M, N, K, pc, ns, e, ctx->tc_err, ctx->stream), "tc projection");
+  const int test = ctx->test_wait_expiry;
+  ctx->test_wait_expiry = 0;
+  CU_TRY(tc::gemm(A, B, M, N, K, pc, ns, e, ctx->tc_err, ctx->stream, test), "tc projection");
   CU_TRY(tc::reduce_partials(part, ns, (int64_t)M * N, M, M, N, (float*)Cout, 2 * (int64_t)np, ctx->stream),
          "tc reduce");
   return PW_OK;
@@ -334,8 +345,102 @@ int tc_backproject(pw_ctx* ctx, const __nv_bfloat16* zsplit, int nb, tc::TcEpi e
   const int M = 2 * npw, N = nb, K = 2 * np;
   tc::Operand A{(const __nv_bfloat16*)ctx->tcA2, M, ctx->kp2, (int64_t)M * ctx->kp2};
   tc::Operand B{zsplit, N, ctx->kp2, (int64_t)N * ctx->kp2};
-  CU_TRY(tc::gemm(A, B, M, N, K, pc, 1, e, ctx->tc_err, ctx->stream), "tc back-projection");
+  const int test = ctx->test_wait_expiry;
+  ctx->test_wait_expiry = 0;
+  CU_TRY(tc::gemm(A, B, M, N, K, pc, 1, e, ctx->tc_err, ctx->stream, test), "tc back-projection");
   return PW_OK;
+}
+
+// ---------------------------------------------------------------------------
+// FP64 GEMMs: FP64-accurate digit-sliced tensor-core GEMMs (zgemm_tc.cu), or DFMA
+// ---------------------------------------------------------------------------
+int ensure_err_flag(pw_ctx* ctx) {
+  if (ctx->tc_err) return PW_OK;
+  CU_TRY(cudaMalloc(&ctx->tc_err, sizeof(int)), "error flag allocation");
+  CU_TRY(cudaMemsetAsync(ctx->tc_err, 0, sizeof(int), ctx->stream), "error flag reset");
+  return PW_OK;
+}
+
+// digit planes of P^dagger and of P (the FP64 projector products), built once per context
+int ensure_ozp(pw_ctx* ctx) {
+  if (ctx->ozPH) return PW_OK;
+  const int np = ctx->nproj, npw = ctx->npw;
+  const cudaStream_t st = ctx->stream;
+  const int64_t p1 = oz::digit_pitch(2 * npw), p2 = oz::digit_pitch(2 * np);
+  WS(amax, unsigned long long, WS_OZAMAX, std::max(np, npw));
+  CU_TRY(cudaMalloc(&ctx->ozPH, oz::digit_bytes(2 * np, 2 * npw)), "P^dagger digit planes");
+  CU_TRY(cudaMalloc(&ctx->ozP, oz::digit_bytes(2 * npw, 2 * np)), "P digit planes");
+  CU_TRY(cudaMalloc(&ctx->ozPH_exp, sizeof(int) * (size_t)np), "P^dagger exponents");
+  CU_TRY(cudaMalloc(&ctx->ozP_exp, sizeof(int) * (size_t)npw), "P exponents");
+  CU_TRY(oz::slice(ctx->P64, npw, 1, 1, np, npw, 1, (__nv_bfloat16*)ctx->ozPH, p1, 2 * (int64_t)np * p1, amax,
+                   ctx->ozPH_exp, st), "P^dagger digits");
+  CU_TRY(oz::slice(ctx->P64, 1, npw, 0, npw, np, 1, (__nv_bfloat16*)ctx->ozP, p2, 2 * (int64_t)npw * p2, amax,
+                   ctx->ozP_exp, st), "P digits");
+  return PW_OK;
+}
+
+// C (M x N) = op(A) op(B) in FP64 with the epilogue e (conventions of launch_cgemm).  The
+// digit-sliced tensor-core GEMM runs unless the context asks for DFMA or op(B) has at most 4
+// columns (matrix-vector forms, memory-bound); op(A) = P^dagger or P uses the context's cached
+// digit planes.  dfma_ns / dfma_ws: split-K of the DFMA form.
+int zgemm(pw_ctx* ctx, int ta, int tb, int M, int N, int K, const double2* A, int64_t lda, const double2* B,
+          int64_t ldb, const Epi<double>& e, int dfma_ns, double2* dfma_ws, int tri, const char* where) {
+  if (M <= 0 || N <= 0) return PW_OK;
+  const cudaStream_t st = ctx->stream;
+  if (!ctx->fp64_tc || N <= 4 || K <= 0 || !oz::available()) {
+    CU_TRY(launch_cgemm<double>(ta, tb, M, N, K, A, lda, B, ldb, e, dfma_ns, dfma_ws, st, tri), where);
+    return PW_OK;
+  }
+  PW_TRY(ensure_err_flag(ctx));
+  const int lower = (tri == GEMM_LOWER_OUT);
+  oz::Digits Ad{nullptr, 2 * M, 2 * K, oz::digit_pitch(2 * K), 0, nullptr};
+  Ad.plane = (int64_t)Ad.rows * Ad.pitch;
+  const bool is_p = (A == ctx->P64 && ctx->nproj > 0 && lda == ctx->npw);
+  if (is_p && ta == 1 && M == ctx->nproj && K == ctx->npw) {
+    PW_TRY(ensure_ozp(ctx));
+    Ad.dig = (const __nv_bfloat16*)ctx->ozPH;
+    Ad.exp = ctx->ozPH_exp;
+  } else if (is_p && ta == 0 && M == ctx->npw && K == ctx->nproj) {
+    PW_TRY(ensure_ozp(ctx));
+    Ad.dig = (const __nv_bfloat16*)ctx->ozP;
+    Ad.exp = ctx->ozP_exp;
+  }
+  oz::Digits Bd{nullptr, N, 2 * K, oz::digit_pitch(2 * K), 0, nullptr};
+  Bd.plane = (int64_t)Bd.rows * Bd.pitch;
+  WS(amax, unsigned long long, WS_OZAMAX, std::max(M, N));
+  WS(ex, int, WS_OZEXP, (size_t)M + N);
+  if (!Ad.dig) {
+    WS(ad, __nv_bfloat16, WS_OZA, (size_t)oz::kDigits * Ad.plane);
+    CU_TRY(oz::slice(A, ta ? lda : 1, ta ? 1 : lda, ta, M, K, 1, ad, Ad.pitch, Ad.plane, amax, ex, st), where);
+    Ad.dig = ad;
+    Ad.exp = ex;
+  }
+  WS(bd, __nv_bfloat16, WS_OZB, (size_t)oz::kDigits * Bd.plane);
+  CU_TRY(oz::slice(B, tb ? 1 : ldb, tb ? ldb : 1, tb, N, K, 0, bd, Bd.pitch, Bd.plane, amax, ex + M, st), where);
+  Bd.dig = bd;
+  Bd.exp = ex + M;
+  const int ns = oz::split_count(2 * M, N, 2 * K, lower);
+  double* part = nullptr;
+  if (ns > 1) {
+    WS(pp, double, WS_OZPART, (size_t)ns * N * 2 * M);
+    part = pp;
+  }
+  const int test = ctx->test_wait_expiry;
+  ctx->test_wait_expiry = 0;
+  CU_TRY(oz::gemm(Ad, Bd, M, N, K, e, lower, ns, part, ctx->tc_err, test, st), where);
+  return PW_OK;
+}
+
+// complex GEMM of the filter / H-apply precision: FP64 through zgemm, complex64 on FFMA
+template <typename T>
+int cg(pw_ctx* ctx, int ta, int tb, int M, int N, int K, const cplx<T>* A, int64_t lda, const cplx<T>* B,
+       int64_t ldb, const Epi<T>& e, int ns, cplx<T>* ws, cudaStream_t st, int tri, const char* where) {
+  if constexpr (std::is_same<T, double>::value) {
+    return zgemm(ctx, ta, tb, M, N, K, A, lda, B, ldb, e, ns, ws, tri, where);
+  } else {
+    CU_TRY(launch_cgemm<T>(ta, tb, M, N, K, A, lda, B, ldb, e, ns, ws, st, tri), where);
+    return PW_OK;
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -380,16 +485,14 @@ int apply_impl(pw_ctx* ctx, const cplx<T>* psi, int64_t ldpsi, int nband, cplx<T
   } else if (np > 0) {
     {
       ProfScope ps(ctx, PW_PROF_GEMM_PROJ);
-      CU_TRY(launch_cgemm<T>(1, 0, np, nband, npw, Prec<T>::P(ctx), npw, psi, ldpsi, epi<T>(EPI_STORE, Cm, np), ns,
-                             sp, st), "projection gemm");
+      PW_TRY(cg<T>(ctx, 1, 0, np, nband, npw, Prec<T>::P(ctx), npw, psi, ldpsi, epi<T>(EPI_STORE, Cm, np), ns, sp, st, GEMM_FULL, "projection gemm"));
     }
     {
       ProfScope ps(ctx, PW_PROF_SMALL);
       CU_TRY(launch_dblock<T>(np, nband, Prec<T>::D(ctx), ctx->blk0, ctx->blklen, Cm, np, Z, np, st), "D block");
     }
     ProfScope ps(ctx, PW_PROF_GEMM_BACK);
-    CU_TRY(launch_cgemm<T>(0, 0, npw, nband, np, Prec<T>::P(ctx), npw, Z, np, epi<T>(EPI_ACCUM, hpsi, ldout), 1,
-                           sp, st), "back-projection gemm");
+    PW_TRY(cg<T>(ctx, 0, 0, npw, nband, np, Prec<T>::P(ctx), npw, Z, np, epi<T>(EPI_ACCUM, hpsi, ldout), 1, sp, st, GEMM_FULL, "back-projection gemm"));
   }
   if (spsi) {
     CU_TRY(cudaMemcpy2DAsync(spsi, sizeof(C) * ldout, psi, sizeof(C) * ldpsi, sizeof(C) * npw, nband,
@@ -397,13 +500,31 @@ int apply_impl(pw_ctx* ctx, const cplx<T>* psi, int64_t ldpsi, int nband, cplx<T
     if constexpr (std::is_same<T, double>::value) {
       if (ctx->has_q && np > 0) {
         CU_TRY(launch_dblock<double>(np, nband, ctx->Q64, ctx->qblk0, ctx->qblklen, Cm, np, Z, np, st), "Q block");
-        CU_TRY(launch_cgemm<T>(0, 0, npw, nband, np, Prec<T>::P(ctx), npw, Z, np, epi<T>(EPI_ACCUM, spsi, ldout), 1,
-                               sp, st), "overlap gemm");
+        PW_TRY(cg<T>(ctx, 0, 0, npw, nband, np, Prec<T>::P(ctx), npw, Z, np, epi<T>(EPI_ACCUM, spsi, ldout), 1, sp, st, GEMM_FULL, "overlap gemm"));
       }
     } else {
       if (ctx->has_q && np > 0) return set_error(PW_EUNSUPPORTED, "S apply is FP64 only");
     }
   }
+  return PW_OK;
+}
+
+// S psi = psi + P Q P^dagger psi alone (FP64; the S-Ortho pass needs no H psi)
+int apply_s64(pw_ctx* ctx, const double2* psi, int64_t ldpsi, int nband, double2* spsi, int64_t ldout) {
+  const int npw = ctx->npw, np = ctx->nproj;
+  const cudaStream_t st = ctx->stream;
+  CU_TRY(cudaMemcpy2DAsync(spsi, sizeof(double2) * ldout, psi, sizeof(double2) * ldpsi, sizeof(double2) * npw, nband,
+                           cudaMemcpyDeviceToDevice, st), "copy S psi");
+  if (!ctx->has_q || np == 0) return PW_OK;
+  WS(Cm, double2, WS_C, (size_t)np * nband);
+  WS(Z, double2, WS_Z, (size_t)np * nband);
+  const int ns = nsplit_for(np, nband, npw);
+  WS(sp, double2, WS_SPLIT, (size_t)ns * np * nband);
+  PW_TRY(cg<double>(ctx, 1, 0, np, nband, npw, ctx->P64, npw, psi, ldpsi, epi<double>(EPI_STORE, Cm, np), ns, sp, st,
+                    GEMM_FULL, "S projection"));
+  CU_TRY(launch_dblock<double>(np, nband, ctx->Q64, ctx->qblk0, ctx->qblklen, Cm, np, Z, np, st), "Q block");
+  PW_TRY(cg<double>(ctx, 0, 0, npw, nband, np, ctx->P64, npw, Z, np, epi<double>(EPI_ACCUM, spsi, ldout), 1, sp, st,
+                    GEMM_FULL, "S back-projection"));
   return PW_OK;
 }
 
@@ -421,9 +542,13 @@ int filter_impl(pw_ctx* ctx, cplx<T>* psi, int64_t ldpsi, int nband, int degree,
   const int bb = band_batch(ctx, nband, sizeof(C));
   const int64_t hb_bs = (int64_t)ctx->sp.nplane * ctx->n[1] * ctx->n[2];
   WS(hb, C, WS_HB, hb_bs * bb);
-  WS(Cm, C, WS_C, (size_t)np * nband);
+  constexpr bool kMixedQ = std::is_same<T, float>::value;
+  // complex64 with Q: C_proj = P^dagger Y_k and C_w = P^dagger W side by side (one GEMM)
+  const bool joint = kMixedQ && ctx->has_q;
+  WS(Cm, C, WS_C, (size_t)np * nband * (joint ? 2 : 1));
   WS(Z, C, WS_Z, (size_t)np * nband);
-  WS(Cw, C, WS_CW, (size_t)np * nband);
+  WS(Cwb, C, WS_CW, (size_t)np * nband);
+  C* Cw = joint ? Cm + (size_t)np * nband : Cwb;
   const int ns = nsplit_for(np, nband, npw);
   WS(spl, C, WS_SPLIT, (size_t)ns * np * nband);
   WS(Y1, C, WS_Y1, (size_t)npw * nband);
@@ -433,10 +558,18 @@ int filter_impl(pw_ctx* ctx, cplx<T>* psi, int64_t ldpsi, int nband, int degree,
   const double cc = 0.5 * (b + a), e = 0.5 * (b - a);
   constexpr bool kMixed = std::is_same<T, float>::value;
   __nv_bfloat16* ys = nullptr;
+  // with Q the projections of Y_k and of W = (T + V) Y_k run as one GEMM over 2 nband
+  // columns: the bf16 pieces hold Y_k in rows [0, nband) and W in rows [nband, 2 nband), so P's
+  // pieces are streamed once per step
+  const int ycols = (kMixed && ctx->has_q) ? 2 * nband : nband;
+  int64_t ys_ps = 0;  // piece stride of the bf16 pieces; kp1 is known once the operands of P exist
   if (kMixed && np > 0) {
     PW_TRY(ensure_tc(ctx));
+    ys_ps = (int64_t)ycols * ctx->kp1;
     ProfScope ps(ctx, PW_PROF_GEMM_PROJ);
-    PW_TRY(tc_split(ctx, (const float2*)psi, ldpsi, npw, nband, ctx->kp1, WS_YSPLIT, &ys));
+    WS(ysb, __nv_bfloat16, WS_YSPLIT, (size_t)ctx->tc_pieces * ys_ps);
+    ys = ysb;
+    PW_TRY(tc_split_into(ctx, (const float2*)psi, ldpsi, npw, nband, ctx->kp1, ys_ps, ys));
   }
   // complex64 with S = I and the warp-group plane kernels: the nonlocal term first
   // (projection, D, back-projection into PZ), then the FFT passes with the recurrence and
@@ -505,11 +638,12 @@ int filter_impl(pw_ctx* ctx, cplx<T>* psi, int64_t ldpsi, int nband, int degree,
     if (kMixed && np > 0) {
       {
         ProfScope ps(ctx, PW_PROF_GEMM_PROJ);
-        PW_TRY(tc_project(ctx, ys, nband, (float2*)Cm));
         if (ctx->has_q) {
-          __nv_bfloat16* wsp;
-          PW_TRY(tc_split(ctx, (const float2*)dst, ldd, npw, nband, ctx->kp1, WS_WSPLIT, &wsp));
-          PW_TRY(tc_project(ctx, wsp, nband, (float2*)Cw));
+          PW_TRY(tc_split_into(ctx, (const float2*)dst, ldd, npw, nband, ctx->kp1, ys_ps,
+                               ys + (int64_t)nband * ctx->kp1));
+          PW_TRY(tc_project(ctx, ys, 2 * nband, (float2*)Cm));  // [P^dagger Y_k, P^dagger W]
+        } else {
+          PW_TRY(tc_project(ctx, ys, nband, (float2*)Cm));
         }
       }
       __nv_bfloat16* zs;
@@ -518,10 +652,8 @@ int filter_impl(pw_ctx* ctx, cplx<T>* psi, int64_t ldpsi, int nband, int degree,
         if (!ctx->has_q) {
           CU_TRY(launch_dblock<T>(np, nband, Prec<T>::D(ctx), ctx->blk0, ctx->blklen, Cm, np, Z, np, st), "filter D");
         } else {
-          CU_TRY(launch_cgemm<T>(0, 0, np, nband, np, Prec<T>::E(ctx), np, Cm, np, epi<T>(EPI_STORE, Z, np), 1, spl,
-                                 st), "filter E C");
-          CU_TRY(launch_cgemm<T>(0, 0, np, nband, np, Prec<T>::K(ctx), np, Cw, np, epi<T>(EPI_ACCUM, Z, np, (T)-1),
-                                 1, spl, st), "filter K Cw");
+          PW_TRY(cg<T>(ctx, 0, 0, np, nband, np, Prec<T>::E(ctx), np, Cm, np, epi<T>(EPI_STORE, Z, np), 1, spl, st, GEMM_FULL, "filter E C"));
+          PW_TRY(cg<T>(ctx, 0, 0, np, nband, np, Prec<T>::K(ctx), np, Cw, np, epi<T>(EPI_ACCUM, Z, np, (T)-1), 1, spl, st, GEMM_FULL, "filter K Cw"));
         }
         PW_TRY(tc_split(ctx, (const float2*)Z, np, np, nband, ctx->kp2, WS_ZSPLIT, &zs));
       }
@@ -541,7 +673,7 @@ int filter_impl(pw_ctx* ctx, cplx<T>* psi, int64_t ldpsi, int nband, int degree,
       te.first = (k == 0);
       te.split = ys;
       te.split_ld = ctx->kp1;
-      te.split_piece_stride = (int64_t)nband * ctx->kp1;
+      te.split_piece_stride = ys_ps;
       te.out_pieces = (k + 1 < degree) ? ctx->tc_pieces : 0;
       PW_TRY(tc_backproject(ctx, zs, nband, te));
       continue;
@@ -559,11 +691,9 @@ int filter_impl(pw_ctx* ctx, cplx<T>* psi, int64_t ldpsi, int nband, int degree,
       {
         ProfScope ps(ctx, PW_PROF_GEMM_PROJ);
         // C = P^dagger Y_k
-        CU_TRY(launch_cgemm<T>(1, 0, np, nband, npw, Prec<T>::P(ctx), npw, cur, ldc, epi<T>(EPI_STORE, Cm, np), ns,
-                               spl, st), "filter projection");
+        PW_TRY(cg<T>(ctx, 1, 0, np, nband, npw, Prec<T>::P(ctx), npw, cur, ldc, epi<T>(EPI_STORE, Cm, np), ns, spl, st, GEMM_FULL, "filter projection"));
         if (ctx->has_q)
-          CU_TRY(launch_cgemm<T>(1, 0, np, nband, npw, Prec<T>::P(ctx), npw, dst, ldd, epi<T>(EPI_STORE, Cw, np), ns,
-                                 spl, st), "filter projection of W");
+          PW_TRY(cg<T>(ctx, 1, 0, np, nband, npw, Prec<T>::P(ctx), npw, dst, ldd, epi<T>(EPI_STORE, Cw, np), ns, spl, st, GEMM_FULL, "filter projection of W"));
       }
       {
         ProfScope ps(ctx, PW_PROF_SMALL);
@@ -571,17 +701,15 @@ int filter_impl(pw_ctx* ctx, cplx<T>* psi, int64_t ldpsi, int nband, int degree,
           CU_TRY(launch_dblock<T>(np, nband, Prec<T>::D(ctx), ctx->blk0, ctx->blklen, Cm, np, Z, np, st), "filter D");
         } else {
           // S^-1 H Y = W + P [E C - K P^dagger W],  E = (I - K P^dagger P) D  (Woodbury, Sec. 3.3)
-          CU_TRY(launch_cgemm<T>(0, 0, np, nband, np, Prec<T>::E(ctx), np, Cm, np, epi<T>(EPI_STORE, Z, np), 1, spl,
-                                 st), "filter E C");
-          CU_TRY(launch_cgemm<T>(0, 0, np, nband, np, Prec<T>::K(ctx), np, Cw, np, epi<T>(EPI_ACCUM, Z, np, (T)-1),
-                                 1, spl, st), "filter K Cw");
+          PW_TRY(cg<T>(ctx, 0, 0, np, nband, np, Prec<T>::E(ctx), np, Cm, np, epi<T>(EPI_STORE, Z, np), 1, spl, st, GEMM_FULL, "filter E C"));
+          PW_TRY(cg<T>(ctx, 0, 0, np, nband, np, Prec<T>::K(ctx), np, Cw, np, epi<T>(EPI_ACCUM, Z, np, (T)-1), 1, spl, st, GEMM_FULL, "filter K Cw"));
         }
       }
       ProfScope ps(ctx, PW_PROF_GEMM_BACK);
-      CU_TRY(launch_cgemm<T>(0, 0, npw, nband, np, Prec<T>::P(ctx), npw, Z, np, ce, 1, spl, st), "filter recurrence");
+      PW_TRY(cg<T>(ctx, 0, 0, npw, nband, np, Prec<T>::P(ctx), npw, Z, np, ce, 1, spl, st, GEMM_FULL, "filter recurrence"));
     } else {
       ProfScope ps(ctx, PW_PROF_GEMM_BACK);
-      CU_TRY(launch_cgemm<T>(0, 0, npw, nband, 0, Prec<T>::P(ctx), npw, Z, 1, ce, 1, spl, st), "filter recurrence");
+      PW_TRY(cg<T>(ctx, 0, 0, npw, nband, 0, Prec<T>::P(ctx), npw, Z, 1, ce, 1, spl, st, GEMM_FULL, "filter recurrence"));
     }
   }
   if (degree % 3 != 0) {
@@ -655,8 +783,7 @@ int recur_step(pw_ctx* ctx, const cplx<T>* cur, int64_t ldc, const cplx<T>* prev
   if (np > 0) {
     {
       ProfScope ps(ctx, PW_PROF_GEMM_PROJ);
-      CU_TRY(launch_cgemm<T>(1, 0, np, nband, npw, Prec<T>::P(ctx), npw, cur, ldc, epi<T>(EPI_STORE, Cp, np), ns,
-                             spl, st), "recurrence projection");
+      PW_TRY(cg<T>(ctx, 1, 0, np, nband, npw, Prec<T>::P(ctx), npw, cur, ldc, epi<T>(EPI_STORE, Cp, np), ns, spl, st, GEMM_FULL, "recurrence projection"));
     }
     {
       ProfScope ps(ctx, PW_PROF_SMALL);
@@ -664,10 +791,10 @@ int recur_step(pw_ctx* ctx, const cplx<T>* cur, int64_t ldc, const cplx<T>* prev
              "recurrence D");
     }
     ProfScope ps(ctx, PW_PROF_GEMM_BACK);
-    CU_TRY(launch_cgemm<T>(0, 0, npw, nband, np, Prec<T>::P(ctx), npw, Z, np, ce, 1, spl, st), "recurrence");
+    PW_TRY(cg<T>(ctx, 0, 0, npw, nband, np, Prec<T>::P(ctx), npw, Z, np, ce, 1, spl, st, GEMM_FULL, "recurrence"));
   } else {
     ProfScope ps(ctx, PW_PROF_GEMM_BACK);
-    CU_TRY(launch_cgemm<T>(0, 0, npw, nband, 0, Prec<T>::P(ctx), npw, Z, 1, ce, 1, spl, st), "recurrence");
+    PW_TRY(cg<T>(ctx, 0, 0, npw, nband, 0, Prec<T>::P(ctx), npw, Z, 1, ce, 1, spl, st, GEMM_FULL, "recurrence"));
   }
   return PW_OK;
 }
@@ -682,8 +809,7 @@ int gram_herm(pw_ctx* ctx, const double2* Y, int64_t ldy, const double2* B, int6
   const int tl = (m + 63) / 64;
   const int ns = nsplit_tiles(tl * (tl + 1) / 2, ctx->npw);
   WS(spl, double2, WS_SPLIT, (size_t)ns * m * m);
-  CU_TRY(launch_cgemm<double>(1, 0, m, m, ctx->npw, Y, ldy, B, ldb, epi<double>(EPI_STORE, G, m), ns, spl, st,
-                              GEMM_LOWER_OUT), "gram");
+  PW_TRY(cg<double>(ctx, 1, 0, m, m, ctx->npw, Y, ldy, B, ldb, epi<double>(EPI_STORE, G, m), ns, spl, st, GEMM_LOWER_OUT, "gram"));
   CU_TRY(la_herm_from_lower(G, m, m, st), "gram Hermitian");
   return PW_OK;
 }
@@ -738,13 +864,12 @@ int rr_impl(pw_ctx* ctx, double2* Y, int64_t ldy, int m, double2* hpsi_out, doub
     const double2* SY = Y;
     int64_t lds = ldy;
     if (ctx->has_q) {
-      PW_TRY(apply_impl<double>(ctx, Y, ldy, m, HY, SYb, npw));  // HY is scratch here
+      PW_TRY(apply_s64(ctx, Y, ldy, m, SYb, npw));
       SY = SYb;
       lds = npw;
     }
     PW_TRY(gram_chol(ctx, Y, ldy, SY, lds, m, G, Linv, tmp, scal));
-    CU_TRY(launch_cgemm<double>(0, 1, npw, m, m, Y, ldy, Linv, m, epi<double>(EPI_STORE, ROT, npw), 1, nullptr, st,
-                                GEMM_B_UPPER), "s-ortho rotate");
+    PW_TRY(cg<double>(ctx, 0, 1, npw, m, m, Y, ldy, Linv, m, epi<double>(EPI_STORE, ROT, npw), 1, nullptr, st, GEMM_B_UPPER, "s-ortho rotate"));
     CU_TRY(cudaMemcpy2DAsync(Y, sizeof(double2) * ldy, ROT, sizeof(double2) * npw, sizeof(double2) * npw, m,
                              cudaMemcpyDeviceToDevice, st), "s-ortho copy");
   }
@@ -768,21 +893,20 @@ int rr_impl(pw_ctx* ctx, double2* Y, int64_t ldy, int m, double2* hpsi_out, doub
   // X = Linv^dagger U  -> tmp
   CU_TRY(launch_cgemm<double>(1, 0, m, m, m, Linv, m, U, m, epi<double>(EPI_STORE, tmp, m), 1, nullptr, st), "back-transform");
   if (q_out)
-    CU_TRY(launch_cgemm<double>(0, 1, npw, m, m, Y, ldy, Linv, m, epi<double>(EPI_STORE, q_out, npw), 1, nullptr, st,
-                                GEMM_B_UPPER), "Q");
+    PW_TRY(cg<double>(ctx, 0, 1, npw, m, m, Y, ldy, Linv, m, epi<double>(EPI_STORE, q_out, npw), 1, nullptr, st, GEMM_B_UPPER, "Q"));
   if (x_out) CU_TRY(cudaMemcpyAsync(x_out, U, sizeof(double2) * m * m, cudaMemcpyDeviceToDevice, st), "copy X");
   if (eig_dev_out)
     CU_TRY(cudaMemcpyAsync(eig_dev_out, eig, sizeof(double) * m, cudaMemcpyDeviceToDevice, st), "copy eig");
   // rotate Y, HY, SY
-  CU_TRY(launch_cgemm<double>(0, 0, npw, m, m, Y, ldy, tmp, m, epi<double>(EPI_STORE, ROT, npw), 1, nullptr, st), "rotate Y");
+  PW_TRY(cg<double>(ctx, 0, 0, npw, m, m, Y, ldy, tmp, m, epi<double>(EPI_STORE, ROT, npw), 1, nullptr, st, GEMM_FULL, "rotate Y"));
   CU_TRY(cudaMemcpy2DAsync(Y, sizeof(double2) * ldy, ROT, sizeof(double2) * npw, sizeof(double2) * npw, m,
                            cudaMemcpyDeviceToDevice, st), "rotate copy");
-  CU_TRY(launch_cgemm<double>(0, 0, npw, m, m, HY, npw, tmp, m, epi<double>(EPI_STORE, ROT, npw), 1, nullptr, st), "rotate HY");
+  PW_TRY(cg<double>(ctx, 0, 0, npw, m, m, HY, npw, tmp, m, epi<double>(EPI_STORE, ROT, npw), 1, nullptr, st, GEMM_FULL, "rotate HY"));
   double2* HYr = ROT;
   const double2* SYr = Y;
   int64_t ldsr = ldy;
   if (ctx->has_q) {
-    CU_TRY(launch_cgemm<double>(0, 0, npw, m, m, SYb, npw, tmp, m, epi<double>(EPI_STORE, HY, npw), 1, nullptr, st), "rotate SY");
+    PW_TRY(cg<double>(ctx, 0, 0, npw, m, m, SYb, npw, tmp, m, epi<double>(EPI_STORE, HY, npw), 1, nullptr, st, GEMM_FULL, "rotate SY"));
     SYr = HY;
     ldsr = npw;
   }
@@ -1090,6 +1214,10 @@ void destroy_impl(pw_ctx* ctx) {
   if (ctx->tcA1) cudaFree(ctx->tcA1);
   if (ctx->tcA2) cudaFree(ctx->tcA2);
   if (ctx->tc_err) cudaFree(ctx->tc_err);
+  if (ctx->ozPH) cudaFree(ctx->ozPH);
+  if (ctx->ozP) cudaFree(ctx->ozP);
+  if (ctx->ozPH_exp) cudaFree(ctx->ozPH_exp);
+  if (ctx->ozP_exp) cudaFree(ctx->ozP_exp);
   for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
   for (void* p : ctx->owned) cudaFree(p);
   for (auto& b : ctx->ws)
@@ -1489,11 +1617,11 @@ PW_API int pw_autotune(pw_ctx* ctx, int nband, int precision, double* best_ms) {
     return PW_OK;
   };
   // batch size with the current kernel forms, every kernel form at that size (complex64:
-  // x-line form (0-4) + 8 * plane form (0-2)), the batch size again with the forms kept
+  // x-line form (0-4) + 8 * plane form (0-3)), the batch size again with the forms kept
   for (size_t c : cand) PW_TRY(consider(c, best_v));
   const size_t c1 = best_c;
   if (precision == PW_MIXED) {
-    for (int pf = 0; pf < 3; ++pf)
+    for (int pf = 0; pf < 4; ++pf)
       for (int xf = 0; xf < 5; ++xf) PW_TRY(consider(c1, xf + 8 * pf));
   }
   const int v1 = best_v;
@@ -1508,7 +1636,8 @@ PW_API int pw_fft_config(pw_ctx* ctx, int precision, int64_t set_batch_bytes, in
                          int* variant) {
   PW_TRY(check_ctx(ctx));
   if (precision != PW_FP64 && precision != PW_MIXED) return set_error(PW_EINVAL, "unknown precision");
-  if (set_variant > 20 || set_variant % 8 > 4) return set_error(PW_EINVAL, "unknown FFT kernel variant %d", set_variant);
+  if (set_variant > 28 || (set_variant >= 0 && set_variant % 8 > 4))
+    return set_error(PW_EINVAL, "unknown FFT kernel variant %d", set_variant);
   const int slot = precision == PW_MIXED ? 0 : 1;
   if (batch_bytes) *batch_bytes = (int64_t)ctx->fft_batch_bytes[slot];
   if (variant) *variant = ctx->fft_variant[slot];
@@ -1524,6 +1653,27 @@ PW_API int pw_tc_config(pw_ctx* ctx, int set_pieces, int* pieces) {
     if (set_pieces != 2 && set_pieces != 3) return set_error(PW_EINVAL, "bf16 pieces must be 2 or 3");
     ctx->tc_pieces = set_pieces;  // the operands are rebuilt on the next mixed call
   }
+  return PW_OK;
+}
+
+PW_API int pw_ctx_sync(pw_ctx* ctx) {
+  PW_TRY(check_ctx(ctx));
+  PW_TRY(check_tc_flag(ctx));
+  CU_TRY(cudaStreamSynchronize(ctx->stream), "context sync");
+  return PW_OK;
+}
+
+PW_API int pw_ctx_test_wait_expiry(pw_ctx* ctx) {
+  PW_TRY(check_ctx(ctx));
+  ctx->test_wait_expiry = 1;
+  return PW_OK;
+}
+
+PW_API int pw_fp64_config(pw_ctx* ctx, int set_mode, int* mode) {
+  PW_TRY(check_ctx(ctx));
+  if (set_mode > 1) return set_error(PW_EINVAL, "FP64 GEMM mode must be 0 (DFMA) or 1 (tensor-core digits)");
+  if (mode) *mode = ctx->fp64_tc;
+  if (set_mode >= 0) ctx->fp64_tc = set_mode;
   return PW_OK;
 }
 

@@ -287,7 +287,7 @@ struct pw_ctx {
   int64_t prof_n[PW_PROF_NCLASS] = {};
   // grow-only workspaces
   struct Buf { void* p = nullptr; size_t bytes = 0; };
-  Buf ws[32];
+  Buf ws[40];
   bool poisoned = false;
   uint64_t ws_gen = 0;  // bumped whenever a workspace is (re)allocated (captured graphs check it)
   // tuning: bytes of half-box planes per FFT band batch (complex64, complex128); set by pw_autotune
@@ -301,6 +301,18 @@ struct pw_ctx {
   // than 0 cover two-stage plans in complex64 only (otherwise form 0 runs); set by pw_autotune
   int fft_variant[2] = {0, 0};
   int last_sweeps = 0;  // Jacobi sweeps of the last Rayleigh-Ritz step
+  // FP64 GEMMs: 1 = FP64-accurate digit-sliced tensor-core GEMMs where a product is large
+  // enough (zgemm_tc.cu), 0 = DFMA GEMMs everywhere (pw_fp64_config)
+  int fp64_tc = 1;
+  // digit planes of P^dagger (A form, rows 2 nproj, K 2 npw) and of P (A form, rows 2 npw,
+  // K 2 nproj) for the FP64 projector products, built on first use, with their row exponents
+  void* ozPH = nullptr;
+  void* ozP = nullptr;
+  int* ozPH_exp = nullptr;
+  int* ozP_exp = nullptr;
+  // test hook: the next tensor-core GEMM issues no copies and waits briefly (its first wait
+  // expires), so that the bounded-wait failure path can be exercised without a fault
+  int test_wait_expiry = 0;
 };
 
 namespace pw {
@@ -309,7 +321,8 @@ enum WsSlot {
   WS_YSPLIT, WS_WSPLIT, WS_ZSPLIT, WS_TCPART, WS_TCERR,      // tensor-core mixed path
   WS_HY, WS_SY, WS_ROT, WS_Y32,                              // Rayleigh-Ritz / solve
   WS_GRAM, WS_GRAM2, WS_LINV, WS_TMP, WS_U, WS_JAC, WS_EIG,  // subspace matrices
-  WS_LZ, WS_RQ, WS_DEN, WS_SCAL, WS_VPOT, WS_PZ, WS_NUM
+  WS_LZ, WS_RQ, WS_DEN, WS_SCAL, WS_VPOT, WS_PZ,
+  WS_OZA, WS_OZB, WS_OZPART, WS_OZAMAX, WS_OZEXP, WS_NUM
 };
 void* ws_get(pw_ctx* c, int slot, size_t bytes, int* status);
 // process-wide count of kernel launches issued by this library (diagnostics)

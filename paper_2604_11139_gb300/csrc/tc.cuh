@@ -41,8 +41,10 @@ struct Operand {
 bool available();
 // D (M x N) = sum over piece pairs of A (M x K) . B (N x K)^T, FP32 accumulation, then the epilogue.
 // nsplit > 1 splits K (only meaningful with TC_EPI_PARTIAL).  *err (device) is set if a wait expired.
+// test_no_copies: the producer issues no copies and every wait gives up after a few thousand
+// polls, so the first wait expires and the failure path runs (failure-detection test).
 cudaError_t gemm(const Operand& A, const Operand& B, int M, int N, int K, int pieces, int nsplit, const TcEpi& epi,
-                 int* err, cudaStream_t st);
+                 int* err, cudaStream_t st, int test_no_copies = 0);
 int split_count(int K, int nsplit);
 cudaError_t reduce_partials(const float* part, int nsplit, int64_t split_stride, int64_t part_ld, int M, int N,
                             float* out, int64_t ldo, cudaStream_t st);

@@ -30,7 +30,8 @@ EXPORTS = ("pw_ctx_create", "pw_ctx_destroy", "pw_ctx_set_stream", "pw_ctx_info"
            "pw_kernel_launches", "pw_hamiltonian_apply_noalloc", "pw_autotune", "pw_batch_create",
            "pw_batch_destroy", "pw_batch_filter", "pw_batch_chebfi_solve", "pw_ctx_set_vloc", "pw_ctx_set_D",
            "pw_local_apply", "pw_diff_create", "pw_diff_destroy", "pw_diff_tape_bytes", "pw_diff_forward",
-           "pw_diff_backward", "pw_fft_config", "pw_tc_config", "pw_strerror", "pw_last_error")
+           "pw_diff_backward", "pw_fft_config", "pw_tc_config", "pw_fp64_config", "pw_ctx_sync",
+           "pw_ctx_test_wait_expiry", "pw_diag_fp64_fma_rate", "pw_strerror", "pw_last_error")
 
 PROF_CLASSES = ("plane_inv", "xline", "plane_fwd", "gemm_proj", "gemm_back", "small", "rr")
 
@@ -80,6 +81,10 @@ def load(path: Optional[str] = None):
     lib.pw_autotune.argtypes = [vp, ci, ci, pd]
     lib.pw_fft_config.argtypes = [vp, ci, i64, ci, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ci)]
     lib.pw_tc_config.argtypes = [vp, ci, ctypes.POINTER(ci)]
+    lib.pw_fp64_config.argtypes = [vp, ci, ctypes.POINTER(ci)]
+    lib.pw_ctx_sync.argtypes = [vp]
+    lib.pw_diag_fp64_fma_rate.argtypes = [vp, pd, pd]
+    lib.pw_ctx_test_wait_expiry.argtypes = [vp]
     pvp = ctypes.POINTER(vp)
     pi64 = ctypes.POINTER(ctypes.c_int64)
     lib.pw_batch_create.argtypes = [pvp, ci, vp, pvp]
@@ -106,6 +111,16 @@ def load(path: Optional[str] = None):
             getattr(lib, name).restype = ctypes.c_int
     _LIB = lib
     return lib
+
+
+def fp64_fma_rate(stream=None):
+    """Measured FP64 FMA rate of the current GPU in TFLOP/s (pw_diag_fp64_fma_rate)."""
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    t, ms = ctypes.c_double(0.0), ctypes.c_double(0.0)
+    _check(load().pw_diag_fp64_fma_rate(ctypes.c_void_p(stream.cuda_stream), ctypes.byref(t), ctypes.byref(ms)))
+    return t.value
 
 
 def kernel_launches() -> int:
@@ -247,6 +262,21 @@ class Context:
         v = ctypes.c_int(0)
         _check(load().pw_tc_config(self._h, -1 if pieces is None else int(pieces), ctypes.byref(v)))
         return v.value if pieces is None else int(pieces)
+
+    def sync(self):
+        """Waits for the context's queued work; raises PWError (PW_ETIMEDOUT) if a bounded
+        device wait expired."""
+        _check(load().pw_ctx_sync(self._h))
+
+    def test_wait_expiry(self):
+        """Arms the failure-detection test hook (the next tensor-core GEMM's first wait expires)."""
+        _check(load().pw_ctx_test_wait_expiry(self._h))
+
+    def fp64_config(self, mode=None):
+        """FP64 GEMM mode: 1 digit-sliced tensor-core GEMMs, 0 DFMA; sets it if given."""
+        v = ctypes.c_int(0)
+        _check(load().pw_fp64_config(self._h, -1 if mode is None else int(mode), ctypes.byref(v)))
+        return v.value if mode is None else int(mode)
 
     def profile(self, on=True):
         _check(load().pw_profile_enable(self._h, 1 if on else 0))

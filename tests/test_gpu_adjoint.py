@@ -131,6 +131,11 @@ def test_adjoint_fp64_matches_central_differences(case):
     prob = case["prob"]
     g = gpu_grads(case)
     ctx, handle = g["ctx"], g["handle"]
+    # The central differences of the forward use the DFMA GEMMs: the digit-sliced tensor-core
+    # GEMMs (the default FP64 form, error ~2^-44 of the row and column maxima per product) do
+    # not vary smoothly at the 1e-15 level, and a step h = 1e-5 at one grid point divides that
+    # noise by h.  The gradient under test above was computed with the default GEMMs.
+    ctx.fp64_config(0)
     rng = np.random.default_rng(prob.seed + 11)
     n = float(np.prod(prob.box))
     rho_t = torch.from_numpy(case["rho_t"]).cuda()
@@ -229,6 +234,7 @@ def test_full_size_differentiation_workload():
         return V.grad.cpu().numpy(), D.grad.cpu().numpy()
 
     gV, gD = grads(h64)
+    ctx.fp64_config(0)   # central differences of the DFMA forward (see the small-box test)
 
     def loss(V, D):
         ctx.set_vloc(V)
@@ -268,6 +274,7 @@ def test_full_size_differentiation_workload():
     err_d = maxrel(np.array(ad), np.array(fd))
     ctx.set_vloc(prob.vloc)
     ctx.set_D(prob.D)
+    ctx.fp64_config(1)
     h32 = pwlib.Diff(ctx, M, m, C, ckpt=2, precision=pwlib.PW_MIXED)
     gV32, gD32 = grads(h32)
     e32v, e32d = maxrel(gV32, gV), maxrel(gD32, gD)

@@ -91,7 +91,7 @@ def test_hamiltonian_apply_fp64(key):
         assert torch.count_nonzero(h[:, ctx.npw:]) == 0
 
 
-@pytest.mark.parametrize("variant", [0, 1, 2, 3, 4, 8, 11, 16, 19, 20])
+@pytest.mark.parametrize("variant", [0, 1, 2, 3, 4, 8, 11, 16, 19, 20, 24, 27, 28])
 @pytest.mark.parametrize("key", ["cubic16_q", "ortho_k_ragged", "tiny_24_aliasing", "box_64_tl8"])
 def test_hamiltonian_apply_mixed(key, variant):
     """The complex64 FFT pass kernel forms (variant = x-line form + 8 * plane form: line
@@ -125,7 +125,7 @@ def test_filter_fp64(key):
             assert rel(t.cpu().numpy()[:, :ctx.npw], ref).max() < 1e-10, degree
 
 
-@pytest.mark.parametrize("variant", [0, 1, 2, 3, 4, 8, 11, 16, 19, 20])
+@pytest.mark.parametrize("variant", [0, 1, 2, 3, 4, 8, 11, 16, 19, 20, 24, 27, 28])
 @pytest.mark.parametrize("key", ["cubic16_q", "tiny_24_aliasing", "box_64_tl8"])
 def test_filter_mixed(key, variant):
     prob, ham, ctx = setup(key)
@@ -276,7 +276,7 @@ def test_full_size_fp64_at_scale_sampled_bands():
         torch.cuda.synchronize()
         ref = ham.apply_h(psi)
         assert rel(h.cpu().numpy()[:, :ctx.npw], ref).max() < 1e-11
-        for variant in (0, 1, 2, 3, 4, 8, 11, 16, 19, 20):
+        for variant in (0, 1, 2, 3, 4, 8, 11, 16, 19, 20, 24, 27, 28):
             ctx.fft_config(pwlib.PW_MIXED, variant=variant)
             t32 = to_dev(psi, torch.complex64)
             h32 = torch.zeros_like(t32)
@@ -319,7 +319,7 @@ def test_full_size_other_boxes_sampled_bands(key):
         assert err < 1e-11
         if sp is not None:
             assert rel(sp.cpu().numpy()[:, :ctx.npw], ham.apply_s(psi)).max() < 1e-12
-        for variant in (0, 1, 2, 3, 4, 8, 11, 16, 19, 20):
+        for variant in (0, 1, 2, 3, 4, 8, 11, 16, 19, 20, 24, 27, 28):
             ctx.fft_config(pwlib.PW_MIXED, variant=variant)
             t32 = to_dev(psi, torch.complex64)
             h32 = torch.zeros_like(t32)
@@ -382,3 +382,27 @@ def test_rayleigh_ritz_many_bands():
             y, _ = O.s_ortho(y, ham.apply_s(y))
         lam, *_ = O.rayleigh_ritz(y, ham.apply_h(y), ham.apply_s(y))
         np.testing.assert_allclose(eig, lam, atol=1e-10, rtol=0)
+
+
+@pytest.mark.parametrize("key", ["cubic16_q", "box_2_3_5", "tiny_24_aliasing"])
+def test_fp64_digit_gemms_agree_with_dfma(key):
+    """The FP64 GEMMs in their two forms (digit-sliced tensor-core GEMMs, the default, and
+    DFMA): H|psi>, S|psi>, the filter and the Ritz values agree far below the oracle
+    tolerances (error of a digit-sliced product below 2^-44 of the row and column maxima)."""
+    prob, ham, ctx = setup(key)
+    with ctx:
+        psi = W.random_block(150, ctx.npw, prob.nband)
+        out = {}
+        for mode in (1, 0):
+            ctx.fp64_config(mode)
+            t = to_dev(psi)
+            h, s = torch.zeros_like(t), torch.zeros_like(t)
+            ctx.hamiltonian_apply(t, h, s)
+            y = t.clone()
+            ctx.chebyshev_filter(y, 5, -0.5, 2.0 * prob.ecut + 3.0)
+            eig, _ = ctx.rayleigh_ritz(y)
+            out[mode] = (h.cpu().numpy(), s.cpu().numpy(), y.cpu().numpy(), eig)
+        assert ctx.fp64_config() == 0
+        assert rel(out[1][0], out[0][0]).max() < 1e-13
+        assert rel(out[1][1], out[0][1]).max() < 1e-13
+        assert np.abs(out[1][3] - out[0][3]).max() < 1e-12
