@@ -416,11 +416,11 @@ def run_ours(args):
            # bf16 products of one projector GEMM call over all bands: 2 (2 Np)(2 N) M per product
            "gemm_proj": ("tensor", 2.0 * (2 * nproj) * (2 * npw) * M * (3 if pieces == 2 else 6)),
            "gemm_back": ("tensor", 2.0 * (2 * nproj) * (2 * npw) * M * (3 if pieces == 2 else 6))}
-    launches = {"gemm_proj": args.steps * m * nproj_gemms, "gemm_back": args.steps * m}
+    gemm_launches = {"gemm_proj": args.steps * m * nproj_gemms, "gemm_back": args.steps * m}
     per_class = {}
     for cname, (bnd, units) in alg.items():
         ms_c, n_c = prof[cname]
-        n_c = launches.get(cname, n_c)
+        n_c = gemm_launches.get(cname, n_c)
         per_launch = ms_c / 1e3 / max(n_c, 1)
         if bnd == "hbm":
             a = units / per_launch / 1e9
@@ -466,9 +466,13 @@ def run_ours(args):
               "fft_config": {"batch_bytes": fft_cfg[0],
                              "xline_kernel": ["line groups", "one thread per line", "warp groups",
                                               "warp groups, table twiddles",
-                                              "warp groups, table twiddles, bands per CTA"][fft_cfg[1] % 8],
-                             "plane_kernels": ["line groups", "one thread per line",
-                                               "warp groups"][fft_cfg[1] // 8]},
+                                              "warp groups, table twiddles, bands per CTA",
+                                              "warp groups, table twiddles, radices swapped",
+                                              "warp groups, table twiddles, bands per CTA, radices swapped",
+                                              "?"][fft_cfg[1] % 8],
+                             "plane_kernels": ["line groups", "one thread per line", "warp groups, whole plane",
+                                               "warp groups, sphere rows + 32-column slices"][fft_cfg[1] // 8],
+                             "variant": fft_cfg[1]},
               "fp64": fp64, "eig_err_vs_fp64": eig_err,
               "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": bytes_psi,
                       "d2h_bytes_per_step": bytes_psi + 8 * M,

@@ -250,6 +250,39 @@ PW_API int pw_diff_forward(pw_diff* diff, void* psi, int64_t ld, int lanczos_ste
 PW_API int pw_diff_backward(pw_diff* diff, const double* eig_bar, const void* psi_bar, int64_t ld,
                             int split, double* dV, double* dD, int accumulate);
 
+/* ---- self-consistent field loop (Alg. 3) ----
+ * Alg. 3 repeats: solve H Psi = Lambda S Psi, occupations from Lambda, density from the
+ * occupations and Psi, until self-consistent.  The paper leaves open how the density sets the
+ * next Hamiltonian; these entry points close the loop with a minimal published model:
+ * insulating filling (the lowest nocc states hold 2 electrons each), the Hartree potential
+ * V_H(G) = 4 pi rho(G) / |G|^2 (G != 0; neutralising background at G = 0) and Dirac's
+ * local-density exchange v_x = -(3 rho / pi)^(1/3) (energy density -(3/4) (3/pi)^(1/3)
+ * rho^(4/3); no correlation); the next V_loc is V_in + beta (V_ion + V_H + v_x - V_in).
+ *
+ * dctx is a "density context": the same cell and FFT box at the Gamma point, no projectors
+ * (natom = 0, D empty), E_cut four times the wave functions' (its sphere holds every Fourier
+ * component of a density of the E_cut orbitals; its box must hold that sphere).
+ *
+ * pw_scf_potential: from rho (device, n1*n2*n3 doubles, C order, electrons / bohr^3), V_ion and
+ * V_in (device grids), writes V_new (device grid) and out[5] (host): (Omega/n) sum (V_in -
+ * V_ion) rho, the Hartree energy (Omega/2n) sum V_H rho, the exchange energy (Omega/n) sum
+ * rho e_x, max |V_ion + V_H + v_x - V_in|, and the electron count (Omega/n) sum rho.
+ * Synchronises dctx's stream. */
+PW_API int pw_scf_potential(pw_ctx* dctx, const double* rho, const double* vion, const double* vin, double beta,
+                            double* vnew, double* out);
+/* The loop: V_in = V_ion (host or device grid, C order), then up to max_iter times
+ * [pw_chebfi_solve(ctx, psi, ..., degree, cycles, 10 Lanczos steps from v0, precision) ->
+ * density of the lowest nocc bands (weights 2 / Omega) -> pw_scf_potential -> V_loc of ctx]
+ * until max |V_out - V_in| < tol.  psi: complex128 device block (ld), carried from one
+ * iteration to the next; eig (host, nband): the last eigenvalues; history (host, 2 max_iter,
+ * may be NULL): per iteration the energy sum_i f_i lambda_i - (Omega/n) sum (V_in - V_ion) rho
+ * + E_H + E_x and max |V_out - V_in|; *iterations (may be NULL) the iterations run.  On
+ * return ctx holds the last input potential.  Allocates 4 grids of scratch for the call.
+ * PW_ENOTCONV if tol was not reached. */
+PW_API int pw_scf_run(pw_ctx* ctx, pw_ctx* dctx, void* psi, int64_t ld, int nband, int nocc, int degree, int cycles,
+                      int max_iter, double beta, double tol, const void* v0, const double* vion, int precision,
+                      double* eig, double* history, int* iterations);
+
 /* H psi = (T + V_loc + P D P^dagger) psi in FP64, like pw_hamiltonian_apply with
  * spsi = NULL, but without allocating any device memory.  The paper has no
  * counterpart; this exists for callers that may not call cudaMalloc/cudaFree at
@@ -288,12 +321,19 @@ enum pw_prof_class {
  * 0 line groups of 1-8 threads with shared-memory twiddles, 1 one thread per line with
  * compile-time twiddles, 2 groups of warps per 32 lines with compile-time twiddles,
  * 3 the same with run-time butterfly indices and table twiddles, 4 as 3 with several bands
- * per CTA; plane forms: 0 line groups, 1 one thread per line, 2 groups of warps per 32
+ * per CTA, 5 and 6 as 3 and 4 with the two radices of the x plan in the other order (the
+ * radix plan of the x-lines is thus a tuned choice; V_loc is kept permuted for both
+ * orders).  Plane forms: 0 line groups, 1 one thread per line, 2 groups of warps per 32
  * lines with table twiddles over the whole plane in shared memory, 3 the same over the
- * plane's sphere rows and 32-column slices (less shared memory per CTA on large boxes).  Forms other than 0 cover box lengths with two-stage radix
- * plans.  Keeps the fastest for `precision` in the context.  Synchronises the stream;
- * *best_ms (may be NULL) receives the best time of one apply. */
+ * plane's sphere rows and 32-column slices (less shared memory per CTA on large boxes).
+ * Forms other than 0 cover box lengths with two-stage radix plans.  Keeps the fastest for
+ * `precision` in the context.  Synchronises the stream; *best_ms (may be NULL) receives
+ * the best time of one apply. */
 PW_API int pw_autotune(pw_ctx* ctx, int nband, int precision, double* best_ms);
+/* (pw_autotune, PW_MIXED, continued) It then times the K-split counts of the projection
+ * GEMM C = P^dagger Y around the whole-waves rule for nband columns (and 2 nband with Q, where
+ * the projections of Y and of (T + V) Y run as one GEMM) and keeps the fastest per column
+ * count; other column counts use the rule. */
 /* Reads (*batch_bytes, *variant; either pointer may be NULL) and then, for arguments
  * >= 0, sets the FFT configuration of `precision`: bytes of half-box planes per band
  * batch (>= 1 band is always used) and the pass-kernel forms (as for

@@ -96,6 +96,8 @@ def projectors(lattice, kpt, miller, tau, sigmas) -> np.ndarray:
             cols.append(g * phase)
             for a in range(3):
                 cols.append(-1j * q[:, a] * s * g * phase)
+    if not cols:                  # no atoms: no nonlocal term
+        return np.zeros((miller.shape[0], 0), dtype=np.complex128)
     P = np.stack(cols, axis=1)
     P /= np.linalg.norm(P, axis=0, keepdims=True)
     return P

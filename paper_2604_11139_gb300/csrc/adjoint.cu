@@ -462,6 +462,10 @@ PW_API int pw_ctx_set_vloc(pw_ctx* ctx, const double* vloc) {
   if (!raw) return status;
   CU_TRY(cudaMemcpyAsync(raw, vloc, sizeof(double) * ntot, cudaMemcpyDefault, st), "vloc copy");
   CU_TRY(setup_vperm(raw, ctx->n, ctx->rho_perm, 1.0 / (double)ntot, ctx->vperm64, ctx->vperm32, st), "vperm");
+  if (ctx->vperm32_sw) {
+    int* rho_sw[3] = {ctx->rho_x_sw, ctx->rho_perm[1], ctx->rho_perm[2]};
+    CU_TRY(setup_vperm32(raw, ctx->n, rho_sw, 1.0 / (double)ntot, ctx->vperm32_sw, st), "vperm (swapped x plan)");
+  }
   CU_TRY(cudaStreamSynchronize(st), "vloc sync");
   ctx->param_gen++;
   return PW_OK;

@@ -1365,7 +1365,11 @@ __device__ __forceinline__ void xw_stage1_fwd(const C* L, C* hbl, int nyz, int h
 // The same with run-time butterfly indices (one code path for all warps of the group,
 // which keeps the kernel small for the larger radices) and twiddles read from the stage
 // table with warp-uniform indices.
-template <typename C, int S, int R1, int R2>
+// Twiddle w_N^(J m) of butterfly J, output m, read from the host's stage table of the first
+// stage, [j][m] = w_N^(j m) for j < R2, 1 <= m < R1 at j (R1 - 1) + m - 1: TA = R1 - 1, TB = 1.
+// With the radix order swapped the same table serves by symmetry of J m: TA = 1, TB = R1' - 1
+// (R1' the table's own first radix).
+template <typename C, int S, int R1, int R2, int TA = R1 - 1, int TB = 1>
 __device__ __forceinline__ void xw_bf_inv(C* L, const C* hbl, const C* __restrict__ tw1, int J, int nyz, int h0,
                                           int np, int n1, bool live) {
   C x[R1];
@@ -1377,12 +1381,12 @@ __device__ __forceinline__ void xw_bf_inv(C* L, const C* hbl, const C* __restric
   dftR<C, +1, R1>(x);
   if (J) {
 #pragma unroll
-    for (int m = 1; m < R1; ++m) x[m] = cmul(x[m], cconj(__ldg(&tw1[J * (R1 - 1) + m - 1])));
+    for (int m = 1; m < R1; ++m) x[m] = cmul(x[m], cconj(__ldg(&tw1[J * TA + m * TB - 1])));
   }
 #pragma unroll
   for (int m = 0; m < R1; ++m) L[(J + R2 * m) * 32] = x[m];
 }
-template <typename C, int S, int R1, int R2>
+template <typename C, int S, int R1, int R2, int TA = R1 - 1, int TB = 1>
 __device__ __forceinline__ void xw_bf_fwd(const C* L, C* hbl, const C* __restrict__ tw1, int J, int nyz, int h0,
                                           int np, int n1, bool live) {
   C x[R1];
@@ -1390,7 +1394,7 @@ __device__ __forceinline__ void xw_bf_fwd(const C* L, C* hbl, const C* __restric
   for (int m = 0; m < R1; ++m) x[m] = L[(J + R2 * m) * 32];
   if (J) {
 #pragma unroll
-    for (int m = 1; m < R1; ++m) x[m] = cmul(x[m], __ldg(&tw1[J * (R1 - 1) + m - 1]));
+    for (int m = 1; m < R1; ++m) x[m] = cmul(x[m], __ldg(&tw1[J * TA + m * TB - 1]));
   }
   dftR<C, -1, R1>(x);
 #pragma unroll
@@ -1400,14 +1404,16 @@ __device__ __forceinline__ void xw_bf_fwd(const C* L, C* hbl, const C* __restric
   }
 }
 
-template <typename T, int N1, int TW>
+template <typename T, int N1, int TW, bool SW = false>
 __global__ void __launch_bounds__(32 * TW, 24 / TW) k_xline_twr(cplx<T>* __restrict__ hb, int64_t hb_bs,
                                                       const T* __restrict__ vperm, SphereDev sp, FftPlan plan,
                                                       const cplx<T>* __restrict__ tw) {
   using C = cplx<T>;
   constexpr CPlan P = make_cplan(N1);
   static_assert(P.nst == 2, "two-stage plan expected");
-  constexpr int R1 = P.radix[0], R2 = P.radix[1];
+  // SW: the two radices in the other order (same twiddle table, transposed index)
+  constexpr int R1 = SW ? P.radix[1] : P.radix[0], R2 = SW ? P.radix[0] : P.radix[1];
+  constexpr int TA = SW ? 1 : R1 - 1, TB = SW ? R2 - 1 : 1;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int lane = threadIdx.x & 31, t = threadIdx.x >> 5;
   C* L = reinterpret_cast<C*>(smem_raw) + lane;
@@ -1418,7 +1424,7 @@ __global__ void __launch_bounds__(32 * TW, 24 / TW) k_xline_twr(cplx<T>* __restr
   const C* tw1 = tw + plan.d[0].tw_off[0];
   C* hbl = hb + (int64_t)b * hb_bs + (live ? yz : 0);
 #pragma unroll 1
-  for (int J = t; J < R2; J += TW) xw_bf_inv<C, +1, R1, R2>(L, hbl, tw1, J, nyz, h0, np, N1, live);
+  for (int J = t; J < R2; J += TW) xw_bf_inv<C, +1, R1, R2, TA, TB>(L, hbl, tw1, J, nyz, h0, np, N1, live);
   __syncthreads();
   const T* vb = vperm + (live ? yz : 0);
 #pragma unroll 1
@@ -1435,18 +1441,20 @@ __global__ void __launch_bounds__(32 * TW, 24 / TW) k_xline_twr(cplx<T>* __restr
   }
   __syncthreads();
 #pragma unroll 1
-  for (int J = t; J < R2; J += TW) xw_bf_fwd<C, -1, R1, R2>(L, hbl, tw1, J, nyz, h0, np, N1, live);
+  for (int J = t; J < R2; J += TW) xw_bf_fwd<C, -1, R1, R2, TA, TB>(L, hbl, tw1, J, nyz, h0, np, N1, live);
 }
 
 // The same with several bands per CTA: the V values of the CTA's lines stay in registers.
-template <typename T, int N1, int TW>
+template <typename T, int N1, int TW, bool SW = false>
 __global__ void __launch_bounds__(32 * TW, 24 / TW) k_xline_twm(cplx<T>* __restrict__ hb, int64_t hb_bs, int nb,
                                                       int bper, const T* __restrict__ vperm, SphereDev sp,
                                                       FftPlan plan, const cplx<T>* __restrict__ tw) {
   using C = cplx<T>;
   constexpr CPlan P = make_cplan(N1);
   static_assert(P.nst == 2, "two-stage plan expected");
-  constexpr int R1 = P.radix[0], R2 = P.radix[1];
+  // SW: the two radices in the other order (same twiddle table, transposed index)
+  constexpr int R1 = SW ? P.radix[1] : P.radix[0], R2 = SW ? P.radix[0] : P.radix[1];
+  constexpr int TA = SW ? 1 : R1 - 1, TB = SW ? R2 - 1 : 1;
   constexpr int NBK = (R1 + TW - 1) / TW;  // stage-2 blocks per warp (at most)
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int lane = threadIdx.x & 31, t = threadIdx.x >> 5;
@@ -1472,7 +1480,7 @@ __global__ void __launch_bounds__(32 * TW, 24 / TW) k_xline_twm(cplx<T>* __restr
   for (int b = b_lo; b < b_hi; ++b) {
     C* hbl = hb + (int64_t)b * hb_bs + (live ? yz : 0);
 #pragma unroll 1
-    for (int J = t; J < R2; J += TW) xw_bf_inv<C, +1, R1, R2>(L, hbl, tw1, J, nyz, h0, np, N1, live);
+    for (int J = t; J < R2; J += TW) xw_bf_inv<C, +1, R1, R2, TA, TB>(L, hbl, tw1, J, nyz, h0, np, N1, live);
     __syncthreads();
 #pragma unroll
     for (int i = 0; i < NBK; ++i) {
@@ -1491,7 +1499,7 @@ __global__ void __launch_bounds__(32 * TW, 24 / TW) k_xline_twm(cplx<T>* __restr
     }
     __syncthreads();
 #pragma unroll 1
-    for (int J = t; J < R2; J += TW) xw_bf_fwd<C, -1, R1, R2>(L, hbl, tw1, J, nyz, h0, np, N1, live);
+    for (int J = t; J < R2; J += TW) xw_bf_fwd<C, -1, R1, R2, TA, TB>(L, hbl, tw1, J, nyz, h0, np, N1, live);
     __syncthreads();  // the next band's first stage overwrites the lines
   }
 }
@@ -1547,7 +1555,7 @@ static cudaError_t launch_xline_tw(cplx<T>* hb, int64_t hb_bs, const T* vperm, c
   return cudaGetLastError();
 }
 
-template <typename T, int N1, int TW>
+template <typename T, int N1, int TW, bool SW = false>
 static cudaError_t launch_xline_twr(cplx<T>* hb, int64_t hb_bs, const T* vperm, const SphereDev& sp,
                                     const FftPlan& plan, const cplx<T>* tw, int nb, bool multi, cudaStream_t st) {
   const size_t sm = sizeof(cplx<T>) * (size_t)N1 * 32;
@@ -1555,35 +1563,43 @@ static cudaError_t launch_xline_twr(cplx<T>* hb, int64_t hb_bs, const T* vperm, 
   const int gx = (nyz + 31) / 32;
   cudaError_t e;
   if (!multi) {
-    if ((e = cudaFuncSetAttribute(k_xline_twr<T, N1, TW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm)))
+    if ((e = cudaFuncSetAttribute(k_xline_twr<T, N1, TW, SW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm)))
       return e;
-    if ((e = cudaFuncSetAttribute(k_xline_twr<T, N1, TW>, cudaFuncAttributePreferredSharedMemoryCarveout, 100)))
+    if ((e = cudaFuncSetAttribute(k_xline_twr<T, N1, TW, SW>, cudaFuncAttributePreferredSharedMemoryCarveout, 100)))
       return e;
-    k_xline_twr<T, N1, TW><<<dim3(gx, nb), 32 * TW, sm, st>>>(hb, hb_bs, vperm, sp, plan, tw); count_launch();
+    k_xline_twr<T, N1, TW, SW><<<dim3(gx, nb), 32 * TW, sm, st>>>(hb, hb_bs, vperm, sp, plan, tw); count_launch();
     return cudaGetLastError();
   }
-  if ((e = cudaFuncSetAttribute(k_xline_twm<T, N1, TW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm))) return e;
-  if ((e = cudaFuncSetAttribute(k_xline_twm<T, N1, TW>, cudaFuncAttributePreferredSharedMemoryCarveout, 100))) return e;
+  if ((e = cudaFuncSetAttribute(k_xline_twm<T, N1, TW, SW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm)))
+    return e;
+  if ((e = cudaFuncSetAttribute(k_xline_twm<T, N1, TW, SW>, cudaFuncAttributePreferredSharedMemoryCarveout, 100)))
+    return e;
   // several bands per CTA (the V values stay in registers), about six waves of CTAs
   const int bper = std::max(1, (int)(((int64_t)nb * gx + 152 * 36 - 1) / (152 * 36)));
   const int splits = (nb + bper - 1) / bper;
-  k_xline_twm<T, N1, TW><<<dim3(gx, splits), 32 * TW, sm, st>>>(hb, hb_bs, nb, bper, vperm, sp, plan, tw); count_launch();
+  k_xline_twm<T, N1, TW, SW><<<dim3(gx, splits), 32 * TW, sm, st>>>(hb, hb_bs, nb, bper, vperm, sp, plan, tw);
+  count_launch();
   return cudaGetLastError();
 }
 
 // groups of warps per 32 x-lines, run-time butterfly indices (any two-stage plan)
 template <typename T>
 static cudaError_t xline_twr(cplx<T>* hb, int64_t hb_bs, const T* vperm, const SphereDev& sp, const FftPlan& plan,
-                             const cplx<T>* tw, int nb, bool multi, cudaStream_t st) {
+                             const cplx<T>* tw, int nb, bool multi, cudaStream_t st, bool swap = false) {
+#define PW_TWR_CASE(N)                                                                             \
+  case N:                                                                                          \
+    return swap ? launch_xline_twr<T, N, 4, true>(hb, hb_bs, vperm, sp, plan, tw, nb, multi, st)   \
+                : launch_xline_twr<T, N, 4, false>(hb, hb_bs, vperm, sp, plan, tw, nb, multi, st);
   switch (plan.n[0]) {
-    case 24: return launch_xline_twr<T, 24, 4>(hb, hb_bs, vperm, sp, plan, tw, nb, multi, st);
-    case 64: return launch_xline_twr<T, 64, 4>(hb, hb_bs, vperm, sp, plan, tw, nb, multi, st);
-    case 72: return launch_xline_twr<T, 72, 4>(hb, hb_bs, vperm, sp, plan, tw, nb, multi, st);
-    case 90: return launch_xline_twr<T, 90, 4>(hb, hb_bs, vperm, sp, plan, tw, nb, multi, st);
-    case 96: return launch_xline_twr<T, 96, 4>(hb, hb_bs, vperm, sp, plan, tw, nb, multi, st);
-    case 120: return launch_xline_twr<T, 120, 4>(hb, hb_bs, vperm, sp, plan, tw, nb, multi, st);
+    PW_TWR_CASE(24)
+    PW_TWR_CASE(72)
+    PW_TWR_CASE(90)
+    PW_TWR_CASE(96)
+    PW_TWR_CASE(120)
+    case 64: return launch_xline_twr<T, 64, 4>(hb, hb_bs, vperm, sp, plan, tw, nb, multi, st);  // 8 x 8
     default: return cudaErrorNotSupported;
   }
+#undef PW_TWR_CASE
 }
 
 // groups of warps per line where the butterfly counts allow (otherwise not supported)
@@ -2544,13 +2560,24 @@ cudaError_t launch_local_apply(const FftPlan& plan, const cplx<T>* tw, const Sph
   // the shared memory per CTA), when the context selected them
   // kernel forms (complex64): x-line form = variant % 8 (0 line groups, 1 one thread per
   // line, 2 warp groups with compile-time twiddles, 3 warp groups with table twiddles, 4 the
-  // same with several bands per CTA), plane form = variant / 8 (0 line groups, 1 one thread
+  // same with several bands per CTA, 5 and 6 as 3 and 4 with the two radices of the line's
+  // plan in the other order), plane form = variant / 8 (0 line groups, 1 one thread
   // per line, 2 warp groups over the whole plane, 3 warp groups over sphere rows and 32-column
   // slices)
   const int fv = (std::is_same<T, float>::value && prof) ? prof->fft_variant[0] : 0;
-  const int xf = fv % 8, pf = fv / 8;
+  int xf = fv % 8;
+  const int pf = fv / 8;
+  // the swapped-radix x-line forms need V permuted for that order: the context's potential
+  // has such a copy, an arbitrary potential (pw_local_apply) takes the unswapped form; the
+  // fallbacks for lengths those forms do not cover keep the usual permutation
+  const T* vperm_x = vperm;
+  if (xf >= 5) {
+    if (prof && prof->vperm32_sw && (const void*)vperm == (const void*)prof->vperm32)
+      vperm_x = (const T*)prof->vperm32_sw;
+    else xf -= 2;
+  }
   const bool tpl = pf == 1, pwg = pf == 2, prs = pf == 3;
-  const bool xtw = xf == 2, xtwr = xf == 3 || xf == 4;
+  const bool xtw = xf == 2, xtwr = xf >= 3 && xf <= 6;
   for (int b0 = 0; b0 < nband; b0 += band_batch) {
     const int nb = min(band_batch, nband - b0);
     prof_begin(prof, PW_PROF_PLANE_INV);
@@ -2575,7 +2602,8 @@ cudaError_t launch_local_apply(const FftPlan& plan, const cplx<T>* tw, const Sph
     e = cudaErrorNotSupported;
     if constexpr (std::is_same<T, float>::value) {
       if (xtw) e = xline_tw<T>(hb, hb_bs, vperm, sp, plan, nb, st);
-      if (xtwr) e = xline_twr<T>(hb, hb_bs, vperm, sp, plan, tw, nb, xf == 4, st);
+      if (xtwr)
+        e = xline_twr<T>(hb, hb_bs, xf >= 5 ? vperm_x : vperm, sp, plan, tw, nb, xf == 4 || xf == 6, st, xf >= 5);
       if (xf == 1) {
         (void)cudaGetLastError();
         e = xline_tpl<T>(hb, hb_bs, vperm, sp, plan, nb, st);
@@ -2635,7 +2663,12 @@ cudaError_t launch_local_apply_rec(const FftPlan& plan, const float2* tw, const 
   using T = float;
   if (!local_apply_rec_supported(plan, prof)) return cudaErrorNotSupported;
   if (nband <= 0) return cudaSuccess;
-  const int xf = prof->fft_variant[0] % 8;
+  int xf = prof->fft_variant[0] % 8;
+  const float* vperm_x = vperm;
+  if (xf >= 5) {
+    if (prof->vperm32_sw && vperm == prof->vperm32) vperm_x = prof->vperm32_sw;
+    else xf -= 2;
+  }
   const bool prs = prof->fft_variant[0] / 8 == 3;
   const int64_t hb_bs = (int64_t)sp.nplane * plan.n[1] * plan.n[2];
   const int nyz = plan.n[1] * plan.n[2];
@@ -2652,7 +2685,8 @@ cudaError_t launch_local_apply_rec(const FftPlan& plan, const float2* tw, const 
     prof_begin(prof, PW_PROF_XLINE);
     e = cudaErrorNotSupported;
     if (xf == 2) e = xline_tw<T>(hb, hb_bs, vperm, sp, plan, nb, st);
-    if (xf == 3 || xf == 4) e = xline_twr<T>(hb, hb_bs, vperm, sp, plan, tw, nb, xf == 4, st);
+    if (xf >= 3 && xf <= 6)
+      e = xline_twr<T>(hb, hb_bs, xf >= 5 ? vperm_x : vperm, sp, plan, tw, nb, xf == 4 || xf == 6, st, xf >= 5);
     if (xf == 1) e = xline_tpl<T>(hb, hb_bs, vperm, sp, plan, nb, st);
     if (e == cudaErrorNotSupported) {
       (void)cudaGetLastError();

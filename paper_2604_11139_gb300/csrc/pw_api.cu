@@ -307,12 +307,14 @@ int tc_split_into(pw_ctx* ctx, const float2* x, int64_t ld, int nrow, int nb, in
   return PW_OK;
 }
 
-// C (np x nb complex64, ld np) = P^dagger Y from the bf16 pieces of Y
-int tc_project(pw_ctx* ctx, const __nv_bfloat16* ysplit, int nb, float2* Cout) {
-  const int np = ctx->nproj, npw = ctx->npw, pc = ctx->tc_pieces;
-  const int M = 2 * np, N = nb, K = 2 * npw;
-  // split K so that the persistent grid gets a whole number of units per SM (152 SMs)
-  const int tiles = ((M + 127) / 128) * ((N + 127) / 128);
+// K splits of the projection GEMM for nb columns: whole waves of the persistent grid (every
+// SM gets the same number of work units), unless pw_autotune timed the choices for nb
+int tc_proj_split(const pw_ctx* ctx, int nb, int rule_only = 0) {
+  if (!rule_only)
+    for (const auto& e : ctx->tc_proj_splits)
+      if (e.first == nb) return e.second;
+  const int M = 2 * ctx->nproj, K = 2 * ctx->npw;
+  const int tiles = ((M + 127) / 128) * ((nb + 127) / 128);
   int nsm = 152, dev = 0;
   if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
   int ns = 1;
@@ -323,6 +325,14 @@ int tc_project(pw_ctx* ctx, const __nv_bfloat16* ysplit, int nb, float2* Cout) {
     const double eff = (double)u / ((double)((u + nsm - 1) / nsm) * nsm);
     if (eff > best + 1e-9) { best = eff; ns = cc; }
   }
+  return ns;
+}
+
+// C (np x nb complex64, ld np) = P^dagger Y from the bf16 pieces of Y
+int tc_project(pw_ctx* ctx, const __nv_bfloat16* ysplit, int nb, float2* Cout, int force_split = 0) {
+  const int np = ctx->nproj, npw = ctx->npw, pc = ctx->tc_pieces;
+  const int M = 2 * np, N = nb, K = 2 * npw;
+  const int ns = force_split > 0 ? tc::split_count(K, force_split) : tc_proj_split(ctx, nb);
   WS(part, float, WS_TCPART, (size_t)ns * M * N);
   tc::Operand A{(const __nv_bfloat16*)ctx->tcA1, M, ctx->kp1, (int64_t)M * ctx->kp1};
   tc::Operand B{ysplit, N, ctx->kp1, (int64_t)N * ctx->kp1};
@@ -1117,6 +1127,20 @@ int create_impl(const pw_problem_desc* d, void* stream, pw_ctx** out) {
   PW_TRY(upload(ctx, &ctx->vperm64, (const double*)nullptr, ntot));
   PW_TRY(upload(ctx, &ctx->vperm32, (const float*)nullptr, ntot));
   CU_TRY(setup_vperm(vraw, ctx->n, ctx->rho_perm, 1.0 / (double)ntot, ctx->vperm64, ctx->vperm32, st), "vperm");
+  {
+    const FftDim& dx = ctx->plan.d[0];
+    if (dx.nst == 2 && dx.radix[0] != dx.radix[1]) {
+      FftDim sw = dx;
+      sw.radix[0] = dx.radix[1];
+      sw.radix[1] = dx.radix[0];
+      sw.L[1] = dx.n / sw.radix[0];
+      std::vector<int> r = digit_reversal(sw);
+      PW_TRY(upload(ctx, &ctx->rho_x_sw, r.data(), r.size()));
+      PW_TRY(upload(ctx, &ctx->vperm32_sw, (const float*)nullptr, ntot));
+      int* rho_sw[3] = {ctx->rho_x_sw, ctx->rho_perm[1], ctx->rho_perm[2]};
+      CU_TRY(setup_vperm32(vraw, ctx->n, rho_sw, 1.0 / (double)ntot, ctx->vperm32_sw, st), "vperm (swapped x plan)");
+    }
+  }
   // projectors
   ctx->natom = given_p ? 0 : d->natom;
   ctx->nchan = given_p ? 0 : d->nchan;
@@ -1617,18 +1641,62 @@ PW_API int pw_autotune(pw_ctx* ctx, int nband, int precision, double* best_ms) {
     return PW_OK;
   };
   // batch size with the current kernel forms, every kernel form at that size (complex64:
-  // x-line form (0-4) + 8 * plane form (0-3)), the batch size again with the forms kept
+  // x-line form (0-6) + 8 * plane form (0-3)), the batch size again with the forms kept
   for (size_t c : cand) PW_TRY(consider(c, best_v));
   const size_t c1 = best_c;
   if (precision == PW_MIXED) {
     for (int pf = 0; pf < 4; ++pf)
-      for (int xf = 0; xf < 5; ++xf) PW_TRY(consider(c1, xf + 8 * pf));
+      for (int xf = 0; xf < 7; ++xf) PW_TRY(consider(c1, xf + 8 * pf));
   }
   const int v1 = best_v;
   for (size_t c : cand) PW_TRY(consider(c, v1));
   ctx->fft_batch_bytes[slot] = best_c;
   ctx->fft_variant[slot] = best_v;
   if (best_ms) *best_ms = best;
+  // mixed projection GEMM: time the K splits around the whole-waves rule for the column
+  // counts the filter uses (nband, and 2 nband for the joint projection with Q)
+  if (precision == PW_MIXED && ctx->nproj > 0) {
+    PW_TRY(ensure_tc(ctx));
+    const int ncols[2] = {nband, ctx->has_q ? 2 * nband : 0};
+    for (int cols : ncols) {
+      if (cols <= 0) continue;
+      __nv_bfloat16* ysp;
+      PW_TRY(tc_split(ctx, (const float2*)xin, ctx->npw, ctx->npw, std::min(cols, nband), ctx->kp1, WS_YSPLIT, &ysp));
+      if (cols > nband) {  // the second half of the pieces: zeros are as good as data for timing
+        WS(ysb, __nv_bfloat16, WS_YSPLIT, (size_t)ctx->tc_pieces * cols * ctx->kp1);
+        CU_TRY(cudaMemsetAsync(ysb, 0, sizeof(__nv_bfloat16) * (size_t)ctx->tc_pieces * cols * ctx->kp1, st),
+               "autotune pieces");
+        ysp = ysb;
+      }
+      WS(cbuf, float2, WS_C, (size_t)ctx->nproj * cols);
+      const int K = 2 * ctx->npw, rule = tc_proj_split(ctx, cols, 1);
+      std::vector<int> cands;
+      for (int c : {rule, 1, 2, rule / 2, rule - 1, rule + 1, 2 * rule, 3 * rule / 2}) {
+        const int cc = tc::split_count(K, std::max(1, c));
+        if (std::find(cands.begin(), cands.end(), cc) == cands.end() && cc <= 64) cands.push_back(cc);
+      }
+      float tbest = 1e30f;
+      int sbest = rule;
+      for (int cc : cands) {
+        float tot = 0.f;
+        for (int rep = 0; rep < 4; ++rep) {
+          CU_TRY(cudaEventRecord(g.e0, st), "autotune event");
+          PW_TRY(tc_project(ctx, ysp, cols, cbuf, cc));
+          CU_TRY(cudaEventRecord(g.e1, st), "autotune event");
+          CU_TRY(cudaEventSynchronize(g.e1), "autotune sync");
+          float ms = 0.f;
+          cudaEventElapsedTime(&ms, g.e0, g.e1);
+          if (rep > 0) tot += ms;
+        }
+        if (tot < tbest) { tbest = tot; sbest = cc; }
+      }
+      auto& v = ctx->tc_proj_splits;
+      v.erase(std::remove_if(v.begin(), v.end(), [&](const std::pair<int, int>& e) { return e.first == cols; }),
+              v.end());
+      v.push_back({cols, sbest});
+    }
+    PW_TRY(check_tc_flag(ctx));
+  }
   return PW_OK;
 }
 
@@ -1636,7 +1704,7 @@ PW_API int pw_fft_config(pw_ctx* ctx, int precision, int64_t set_batch_bytes, in
                          int* variant) {
   PW_TRY(check_ctx(ctx));
   if (precision != PW_FP64 && precision != PW_MIXED) return set_error(PW_EINVAL, "unknown precision");
-  if (set_variant > 28 || (set_variant >= 0 && set_variant % 8 > 4))
+  if (set_variant > 30 || (set_variant >= 0 && set_variant % 8 > 6))
     return set_error(PW_EINVAL, "unknown FFT kernel variant %d", set_variant);
   const int slot = precision == PW_MIXED ? 0 : 1;
   if (batch_bytes) *batch_bytes = (int64_t)ctx->fft_batch_bytes[slot];

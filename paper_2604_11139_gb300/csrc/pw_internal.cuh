@@ -253,6 +253,11 @@ struct pw_ctx {
   double* vperm64 = nullptr;
   float* vperm32 = nullptr;
   int* rho_perm[3] = {nullptr, nullptr, nullptr};  // digit-reversal maps per dimension
+  // x-line forms 5 and 6 run the two-stage x plan with its radices in the other order: the
+  // x digit reversal of that order and V_loc / n1n2n3 permuted with it (complex64 path);
+  // NULL when the x plan has no such alternative
+  int* rho_x_sw = nullptr;
+  float* vperm32_sw = nullptr;
   double2* P64 = nullptr;   // npw x nproj
   float2* P32 = nullptr;
   double* D64 = nullptr;    // nproj x nproj column-major
@@ -301,6 +306,9 @@ struct pw_ctx {
   // than 0 cover two-stage plans in complex64 only (otherwise form 0 runs); set by pw_autotune
   int fft_variant[2] = {0, 0};
   int last_sweeps = 0;  // Jacobi sweeps of the last Rayleigh-Ritz step
+  // K splits of the mixed projection GEMM per column count, chosen by pw_autotune (columns ->
+  // splits); other column counts use the whole-waves rule
+  std::vector<std::pair<int, int>> tc_proj_splits;
   // FP64 GEMMs: 1 = FP64-accurate digit-sliced tensor-core GEMMs where a product is large
   // enough (zgemm_tc.cu), 0 = DFMA GEMMs everywhere (pw_fp64_config)
   int fp64_tc = 1;
@@ -322,7 +330,7 @@ enum WsSlot {
   WS_HY, WS_SY, WS_ROT, WS_Y32,                              // Rayleigh-Ritz / solve
   WS_GRAM, WS_GRAM2, WS_LINV, WS_TMP, WS_U, WS_JAC, WS_EIG,  // subspace matrices
   WS_LZ, WS_RQ, WS_DEN, WS_SCAL, WS_VPOT, WS_PZ,
-  WS_OZA, WS_OZB, WS_OZPART, WS_OZAMAX, WS_OZEXP, WS_NUM
+  WS_OZA, WS_OZB, WS_OZPART, WS_OZAMAX, WS_OZEXP, WS_SCF, WS_NUM
 };
 void* ws_get(pw_ctx* c, int slot, size_t bytes, int* status);
 // process-wide count of kernel launches issued by this library (diagnostics)

@@ -15,6 +15,9 @@ cudaError_t setup_projectors(int npw, const int* miller_dev, const ProjParams& p
                              cudaStream_t st);
 cudaError_t setup_vperm(const double* V, const int* n, int* const* rho, double scale, double* out64, float* out32,
                         cudaStream_t st);
+// complex64 copy only (the x-line forms with the radix order of the x plan swapped)
+cudaError_t setup_vperm32(const double* V, const int* n, int* const* rho, double scale, float* out32,
+                          cudaStream_t st);
 cudaError_t setup_unperm(const double* in, const int* n, int* const* rho, double* out, int accumulate,
                          cudaStream_t st);
 cudaError_t cast_d2f(const double* a, float* b, int64_t n, cudaStream_t st);

@@ -84,6 +84,14 @@ cudaError_t setup_vperm(const double* V, const int* n, int* const* rho, double s
   return cudaGetLastError();
 }
 
+cudaError_t setup_vperm32(const double* V, const int* n, int* const* rho, double scale, float* out32,
+                          cudaStream_t st) {
+  const int64_t tot = (int64_t)n[0] * n[1] * n[2];
+  const unsigned nb = (unsigned)((tot + 255) / 256);
+  k_vperm<float><<<nb, 256, 0, st>>>(V, n[0], n[1], n[2], rho[0], rho[1], rho[2], scale, out32); count_launch();
+  return cudaGetLastError();
+}
+
 // out[rho_x(jx)][rho_y(jy)][rho_z(jz)] (+)= in[jx][jy][jz]
 __global__ void k_unperm(const double* __restrict__ in, int n1, int n2, int n3, const int* __restrict__ r1,
                          const int* __restrict__ r2, const int* __restrict__ r3, double* __restrict__ out,

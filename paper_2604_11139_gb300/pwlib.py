@@ -31,7 +31,8 @@ EXPORTS = ("pw_ctx_create", "pw_ctx_destroy", "pw_ctx_set_stream", "pw_ctx_info"
            "pw_batch_destroy", "pw_batch_filter", "pw_batch_chebfi_solve", "pw_ctx_set_vloc", "pw_ctx_set_D",
            "pw_local_apply", "pw_diff_create", "pw_diff_destroy", "pw_diff_tape_bytes", "pw_diff_forward",
            "pw_diff_backward", "pw_fft_config", "pw_tc_config", "pw_fp64_config", "pw_ctx_sync",
-           "pw_ctx_test_wait_expiry", "pw_diag_fp64_fma_rate", "pw_strerror", "pw_last_error")
+           "pw_ctx_test_wait_expiry", "pw_diag_fp64_fma_rate", "pw_scf_potential", "pw_scf_run", "pw_strerror",
+           "pw_last_error")
 
 PROF_CLASSES = ("plane_inv", "xline", "plane_fwd", "gemm_proj", "gemm_back", "small", "rr")
 
@@ -84,6 +85,8 @@ def load(path: Optional[str] = None):
     lib.pw_fp64_config.argtypes = [vp, ci, ctypes.POINTER(ci)]
     lib.pw_ctx_sync.argtypes = [vp]
     lib.pw_diag_fp64_fma_rate.argtypes = [vp, pd, pd]
+    lib.pw_scf_potential.argtypes = [vp, vp, vp, vp, cd, vp, pd]
+    lib.pw_scf_run.argtypes = [vp, vp, vp, i64, ci, ci, ci, ci, ci, cd, cd, vp, vp, ci, pd, pd, ctypes.POINTER(ci)]
     lib.pw_ctx_test_wait_expiry.argtypes = [vp]
     pvp = ctypes.POINTER(vp)
     pi64 = ctypes.POINTER(ctypes.c_int64)
@@ -398,6 +401,46 @@ class Context:
         _check(load().pw_density_grad(self._h, ctypes.c_void_p(a.data_ptr()), bp, ld, m, _dptr(w),
                                       ctypes.c_void_p(out.data_ptr()), 1 if accumulate else 0))
         return out
+
+    # -- self-consistent field loop (Alg. 3) -------------------------------------------
+    @classmethod
+    def density_context(cls, lattice, ecut, box, stream=None):
+        """The density context of a wave-function problem (cell, E_cut, box): Gamma point,
+        no projectors, sphere |G|^2/2 <= 4 E_cut (pw_scf_potential)."""
+        return cls(lattice, [0.0, 0.0, 0.0], 4.0 * ecut, box, np.zeros(tuple(box)), np.zeros((0, 3)), [],
+                   np.zeros((0, 0)), stream=stream)
+
+    def scf_potential(self, rho, vion, vin, beta):
+        """V_new and (dc, E_H, E_x, max|V_out - V_in|, electrons) for a density context."""
+        import torch
+        out = np.zeros(5)
+        vnew = torch.empty_like(vin)
+        for t in (rho, vion, vin):
+            if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()):
+                raise TypeError("grids must be contiguous float64 CUDA tensors")
+        self._sync_stream()
+        _check(load().pw_scf_potential(self._h, ctypes.c_void_p(rho.data_ptr()), ctypes.c_void_p(vion.data_ptr()),
+                                       ctypes.c_void_p(vin.data_ptr()), float(beta),
+                                       ctypes.c_void_p(vnew.data_ptr()), _dptr(out)))
+        return vnew, out
+
+    def scf_run(self, dctx, psi, nocc, degree, cycles, v0, vion, max_iter=100, beta=0.3, tol=1e-8,
+                precision=PW_FP64):
+        """The SCF loop of pw_scf_run; returns (eigenvalues, history (iterations x 2), iterations)."""
+        import torch
+        psi, m, ld = _block(psi, torch.complex128, "psi")
+        v0, _, _ = _block(v0, torch.complex128, "v0")
+        vi = np.ascontiguousarray(np.asarray(vion, dtype=np.float64))
+        eig = np.zeros(m)
+        hist = np.zeros(2 * max_iter)
+        its = ctypes.c_int(0)
+        self._sync_stream()
+        st = load().pw_scf_run(self._h, dctx._h, ctypes.c_void_p(psi.data_ptr()), ld, m, int(nocc), int(degree),
+                               int(cycles), int(max_iter), float(beta), float(tol), ctypes.c_void_p(v0.data_ptr()),
+                               ctypes.c_void_p(vi.ctypes.data), precision, _dptr(eig), _dptr(hist),
+                               ctypes.byref(its))
+        _check(st)
+        return eig, hist[:2 * its.value].reshape(-1, 2), its.value
 
     # -- differentiation form ---------------------------------------------------------
     def set_vloc(self, vloc):

@@ -114,7 +114,7 @@ def gaussian_vloc(lattice, box, tau, depth=2.0, width=1.0):
 
 def _block_sym(rng, nproj, block, lo=-0.5, hi=0.5):
     D = np.zeros((nproj, nproj))
-    for s in range(0, nproj, block):
+    for s in range(0, nproj, max(block, 1)):
         B = rng.uniform(lo, hi, size=(block, block))
         D[s:s + block, s:s + block] = 0.5 * (B + B.T)
     return D
@@ -122,7 +122,7 @@ def _block_sym(rng, nproj, block, lo=-0.5, hi=0.5):
 
 def _block_q(rng, nproj, block, umin=0.05, umax=0.3):
     Q = np.zeros((nproj, nproj))
-    for s in range(0, nproj, block):
+    for s in range(0, nproj, max(block, 1)):
         U, _ = np.linalg.qr(rng.standard_normal((block, block)))
         u = rng.uniform(umin, umax, size=block)
         Q[s:s + block, s:s + block] = (U * u) @ U.T
