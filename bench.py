@@ -13,7 +13,9 @@ from workloads.py).  One step = one ChebFi cycle on one batch: the degree-m filt
 `value`) followed by the FP64 S-Ortho + Rayleigh-Ritz step.  Inputs are resident in HBM
 when the timed region starts; L2 is flushed (256 MB write) between steps.  The batched
 k-point form (32 k-points, one captured graph per filter) is measured after it in the same
-run and reported under "batched_kpoints" (skip with --no-batched).
+run and reported under "batched_kpoints" (skip with --no-batched), and the Gamma-point pairing
+of the same bands made real in r-space (M/2 packed complex bands per filter) under
+"gamma_paired" (skip with --no-gamma).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -56,6 +58,7 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-gamma", action="store_true")
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--tc-pieces", type=int, default=2,
                     help="bf16 pieces of the mixed GEMM operands: 2 (3 products) or 3 (6 products)")
@@ -369,6 +372,42 @@ def run_ours(args):
                 "statistic": "median", "gemms": "FP64-accurate digit-sliced tensor-core GEMMs (pw_fp64_config 1)",
                 "dfma_gemms": {"value": M * m / t_dfma, "filter_ms": 1e3 * t_dfma, "steps": 1}}
 
+    # Gamma-point pairing (k = 0): the M bands, made real in r-space, filtered as M / 2 packed
+    # complex bands (pack + filter + unpack timed), against the unpaired filter of the same bands
+    gamma = None
+    if world == 1 and not args.no_gamma and not np.any(prob.kpt) and M % 2 == 0:
+        MX = pwlib.PW_MIXED
+        Ys = Y0_32.clone()
+        ctx.gamma_symmetrize(Ys, precision=MX)
+        Cp = torch.empty((M // 2, npw), dtype=torch.complex64, device="cuda")
+        Yu = torch.empty_like(Ys)
+
+        def gstep():
+            ctx.gamma_pack(Ys, precision=MX, out=Cp)
+            ctx.chebyshev_filter(Cp, m, a, b, precision=MX)
+            ctx.gamma_unpack(Cp, precision=MX, out=Yu)
+
+        for _ in range(2):
+            gstep()
+        gts = []
+        for _ in range(max(3, min(args.steps, 5))):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            gstep()
+            e1.record(st)
+            torch.cuda.synchronize()
+            gts.append(e0.elapsed_time(e1) / 1e3)
+        Yf = Ys.clone()
+        ctx.chebyshev_filter(Yf, m, a, b, precision=MX)
+        rel = (torch.linalg.vector_norm(Yu - Yf, dim=1) / torch.linalg.vector_norm(Yf, dim=1)).max().item()
+        tg = statistics.median(gts)
+        gamma = {"value": M * m / tg, "unit": UNIT, "filter_ms": 1e3 * tg, "steps": len(gts), "statistic": "median",
+                 "bands": M, "packed_bands": M // 2, "max_rel_diff_vs_unpaired": rel,
+                 "what": "pw_gamma_pack + mixed filter of M/2 packed bands + pw_gamma_unpack; the M bands are "
+                         "r-space-real (pw_gamma_symmetrize of the bench's starting block)"}
+        del Ys, Cp, Yu, Yf
+
     # end to end through the public C ABI with host buffers: H2D psi, one ChebFi cycle, D2H psi + eigenvalues
     host_in = torch.from_numpy(psi0).pin_memory()
     host_out = torch.empty_like(host_in).pin_memory()
@@ -482,7 +521,7 @@ def run_ours(args):
               "cpu_baseline": cpu, "clocks": clk, "gpu_launches": int(launches),
               "kernels_ms_per_step": {k: v[0] / args.steps for k, v in prof.items()},
               "kernel_launches_per_step": {k: v[1] / args.steps for k, v in prof.items()},
-              "fp64_fma_peak": fp64_peak, "batched_kpoints": batched})
+              "fp64_fma_peak": fp64_peak, "gamma_paired": gamma, "batched_kpoints": batched})
     if dist is not None:
         dist.barrier()
         dist.destroy_process_group()

@@ -250,6 +250,23 @@ PW_API int pw_diff_forward(pw_diff* diff, void* psi, int64_t ld, int lanczos_ste
 PW_API int pw_diff_backward(pw_diff* diff, const double* eig_bar, const void* psi_bar, int64_t ld,
                             int split, double* dV, double* dD, int accumulate);
 
+/* ---- Gamma-point pairing (time-reversal symmetry at k = 0) ----
+ * At k = 0 a function real in r-space has coefficients c(-G) = conj c(G), and H maps such
+ * functions to such functions when V_loc, D and Q are real and the projectors satisfy
+ * P(-G) = conj P(G) (the generated s/p projectors do; explicit ones must).  Two such bands a,
+ * b then travel as one complex band c = a + i b: H is linear, so H c = H a + i H b, and the
+ * Chebyshev filter p(A) of pw_chebyshev_filter gives p(A) c = p(A) a + i p(A) b, i.e. the
+ * filter of 2 m such bands costs the FFTs and GEMMs of m bands.  In the canonical order the
+ * partner -G of index i is npw - 1 - i.
+ * pw_gamma_symmetrize: psi <- (psi(G) + conj psi(-G)) / 2, the r-space-real part, in place.
+ * pw_gamma_pack: c_j = a_{2j} + i a_{2j+1} for j < nband / 2 (nband even).
+ * pw_gamma_unpack: a_{2j}(G) = (c_j(G) + conj c_j(-G)) / 2, a_{2j+1}(G) = (c_j(G) - conj c_j(-G)) / (2 i).
+ * Blocks: device, element type of `precision`; nband counts the unpacked bands.  PW_EINVAL
+ * unless the context is at k = 0, for odd nband, or for aliasing input and output. */
+PW_API int pw_gamma_symmetrize(pw_ctx* ctx, void* psi, int64_t ld, int nband, int precision);
+PW_API int pw_gamma_pack(pw_ctx* ctx, const void* a, int64_t lda, int nband, void* c, int64_t ldc, int precision);
+PW_API int pw_gamma_unpack(pw_ctx* ctx, const void* c, int64_t ldc, int nband, void* a, int64_t lda, int precision);
+
 /* ---- self-consistent field loop (Alg. 3) ----
  * Alg. 3 repeats: solve H Psi = Lambda S Psi, occupations from Lambda, density from the
  * occupations and Psi, until self-consistent.  The paper leaves open how the density sets the

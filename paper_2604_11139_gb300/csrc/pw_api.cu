@@ -1620,8 +1620,8 @@ PW_API int pw_autotune(pw_ctx* ctx, int nband, int precision, double* best_ms) {
     const int bb = (int)std::max<size_t>(1, std::min<size_t>(c / std::max<size_t>(per, 1), nband));
     if (c != cand[0] && bb * per > c && bb == 1) return PW_OK;
     ctx->fft_variant[slot] = v;
-    float tot = 0.f;
-    for (int rep = 0; rep < 4; ++rep) {
+    float tot = 1e30f;  // the fastest of 4 timed runs (after a warm-up) resists noise best
+    for (int rep = 0; rep < 5; ++rep) {
       CU_TRY(cudaEventRecord(g.e0, st), "autotune event");
       cudaError_t e;
       if (precision == PW_MIXED)
@@ -1635,9 +1635,9 @@ PW_API int pw_autotune(pw_ctx* ctx, int nband, int precision, double* best_ms) {
       CU_TRY(cudaEventSynchronize(g.e1), "autotune sync");
       float ms = 0.f;
       cudaEventElapsedTime(&ms, g.e0, g.e1);
-      if (rep > 0) tot += ms;  // first repetition warms up
+      if (rep > 0) tot = std::min(tot, ms);  // first repetition warms up
     }
-    if (tot / 3.0 < best) { best = tot / 3.0; best_c = c; best_v = v; }
+    if (tot < best) { best = tot; best_c = c; best_v = v; }
     return PW_OK;
   };
   // batch size with the current kernel forms, every kernel form at that size (complex64:
@@ -1678,15 +1678,15 @@ PW_API int pw_autotune(pw_ctx* ctx, int nband, int precision, double* best_ms) {
       float tbest = 1e30f;
       int sbest = rule;
       for (int cc : cands) {
-        float tot = 0.f;
-        for (int rep = 0; rep < 4; ++rep) {
+        float tot = 1e30f;
+        for (int rep = 0; rep < 5; ++rep) {
           CU_TRY(cudaEventRecord(g.e0, st), "autotune event");
           PW_TRY(tc_project(ctx, ysp, cols, cbuf, cc));
           CU_TRY(cudaEventRecord(g.e1, st), "autotune event");
           CU_TRY(cudaEventSynchronize(g.e1), "autotune sync");
           float ms = 0.f;
           cudaEventElapsedTime(&ms, g.e0, g.e1);
-          if (rep > 0) tot += ms;
+          if (rep > 0) tot = std::min(tot, ms);
         }
         if (tot < tbest) { tbest = tot; sbest = cc; }
       }

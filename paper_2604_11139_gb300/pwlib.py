@@ -31,8 +31,8 @@ EXPORTS = ("pw_ctx_create", "pw_ctx_destroy", "pw_ctx_set_stream", "pw_ctx_info"
            "pw_batch_destroy", "pw_batch_filter", "pw_batch_chebfi_solve", "pw_ctx_set_vloc", "pw_ctx_set_D",
            "pw_local_apply", "pw_diff_create", "pw_diff_destroy", "pw_diff_tape_bytes", "pw_diff_forward",
            "pw_diff_backward", "pw_fft_config", "pw_tc_config", "pw_fp64_config", "pw_ctx_sync",
-           "pw_ctx_test_wait_expiry", "pw_diag_fp64_fma_rate", "pw_scf_potential", "pw_scf_run", "pw_strerror",
-           "pw_last_error")
+           "pw_ctx_test_wait_expiry", "pw_diag_fp64_fma_rate", "pw_scf_potential", "pw_scf_run", "pw_gamma_symmetrize",
+           "pw_gamma_pack", "pw_gamma_unpack", "pw_strerror", "pw_last_error")
 
 PROF_CLASSES = ("plane_inv", "xline", "plane_fwd", "gemm_proj", "gemm_back", "small", "rr")
 
@@ -86,6 +86,9 @@ def load(path: Optional[str] = None):
     lib.pw_ctx_sync.argtypes = [vp]
     lib.pw_diag_fp64_fma_rate.argtypes = [vp, pd, pd]
     lib.pw_scf_potential.argtypes = [vp, vp, vp, vp, cd, vp, pd]
+    lib.pw_gamma_symmetrize.argtypes = [vp, vp, i64, ci, ci]
+    lib.pw_gamma_pack.argtypes = [vp, vp, i64, ci, vp, i64, ci]
+    lib.pw_gamma_unpack.argtypes = [vp, vp, i64, ci, vp, i64, ci]
     lib.pw_scf_run.argtypes = [vp, vp, vp, i64, ci, ci, ci, ci, ci, cd, cd, vp, vp, ci, pd, pd, ctypes.POINTER(ci)]
     lib.pw_ctx_test_wait_expiry.argtypes = [vp]
     pvp = ctypes.POINTER(vp)
@@ -400,6 +403,38 @@ class Context:
         self._sync_stream()
         _check(load().pw_density_grad(self._h, ctypes.c_void_p(a.data_ptr()), bp, ld, m, _dptr(w),
                                       ctypes.c_void_p(out.data_ptr()), 1 if accumulate else 0))
+        return out
+
+    # -- Gamma-point pairing -------------------------------------------------------------
+    def gamma_symmetrize(self, psi, precision=PW_FP64):
+        """psi <- its r-space-real part (k = 0 contexts), in place."""
+        psi, m, ld = _block(psi, _dtype(precision), "psi")
+        self._sync_stream()
+        _check(load().pw_gamma_symmetrize(self._h, ctypes.c_void_p(psi.data_ptr()), ld, m, precision))
+        return psi
+
+    def gamma_pack(self, a, precision=PW_FP64, out=None):
+        """Packs 2m r-space-real bands into m complex bands c_j = a_2j + i a_2j+1."""
+        import torch
+        a, m, ld = _block(a, _dtype(precision), "a")
+        if out is None:
+            out = torch.empty((m // 2, self.npw), dtype=_dtype(precision), device="cuda")
+        out, _, ldo = _block(out, _dtype(precision), "out")
+        self._sync_stream()
+        _check(load().pw_gamma_pack(self._h, ctypes.c_void_p(a.data_ptr()), ld, m, ctypes.c_void_p(out.data_ptr()),
+                                    ldo, precision))
+        return out
+
+    def gamma_unpack(self, c, precision=PW_FP64, out=None):
+        """Unpacks m complex bands into the 2m r-space-real bands they carry."""
+        import torch
+        c, m, ld = _block(c, _dtype(precision), "c")
+        if out is None:
+            out = torch.empty((2 * m, self.npw), dtype=_dtype(precision), device="cuda")
+        out, _, ldo = _block(out, _dtype(precision), "out")
+        self._sync_stream()
+        _check(load().pw_gamma_unpack(self._h, ctypes.c_void_p(c.data_ptr()), ld, 2 * m,
+                                      ctypes.c_void_p(out.data_ptr()), ldo, precision))
         return out
 
     # -- self-consistent field loop (Alg. 3) -------------------------------------------
