@@ -9,7 +9,9 @@ import numpy as np
 import pytest
 import scipy.linalg
 
+import tests.test_oracle_lobpcg as lpins
 import tests.test_oracle_pins as pins
+from oracle import pw_lobpcg as L
 from oracle import pw_oracle as O
 
 
@@ -107,6 +109,17 @@ def _plant(monkeypatch, what):
     elif what == "residual with psi in place of S psi":
         monkeypatch.setattr(O, "rayleigh_ritz", _rr_recording_psi(O.rayleigh_ritz))
         monkeypatch.setattr(O, "residual_norms", _residual_with_psi_for_s_psi)
+    elif what == "S-Deflate with psi0 in place of S psi0":
+        sd = L.s_deflate
+        monkeypatch.setattr(L, "s_deflate", lambda X, Y0, SY0: sd(X, Y0, Y0))
+    elif what == "LOBPCG residual with the wrong sign":
+        monkeypatch.setattr(L, "residuals", lambda lam, HX, SX: HX + lam[:, None] * SX)
+    elif what == "preconditioner inverted":
+        tpa = L.tpa_preconditioner
+        monkeypatch.setattr(L, "tpa_preconditioner", lambda kin, e: 1.0 / tpa(kin, e))
+    elif what == "S-Ortho applied to psi only":
+        so = L.s_ortho3
+        monkeypatch.setattr(L, "s_ortho3", lambda X, HX, SX: (so(X, HX, SX)[0], HX, SX))
     else:  # pragma: no cover
         raise KeyError(what)
 
@@ -125,6 +138,11 @@ CASES = [
      lambda: pins.test_rayleigh_quotients_of_exact_and_mixed_vectors(False)),
     ("residual returning zeros", lambda: pins.test_residual_norms_of_exact_and_perturbed_pairs(False)),
     ("residual with psi in place of S psi", lambda: pins.test_chebfi_residuals_match_dense_pencil(True)),
+    ("S-Deflate with psi0 in place of S psi0", lambda: lpins.test_s_deflate_is_the_s_orthogonal_projection(True)),
+    ("LOBPCG residual with the wrong sign",
+     lambda: lpins.test_lobpcg_converges_to_the_dense_eigenpairs(True, 4, 2, 1e-12)),
+    ("preconditioner inverted", lpins.test_tpa_preconditioner_values),
+    ("S-Ortho applied to psi only", lambda: lpins.test_s_ortho_is_s_orthonormal_with_the_same_span(False)),
 ]
 
 
