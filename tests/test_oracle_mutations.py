@@ -11,8 +11,10 @@ import scipy.linalg
 
 import tests.test_oracle_lobpcg as lpins
 import tests.test_oracle_pins as pins
+import tests.test_oracle_slicing as spins
 from oracle import pw_lobpcg as L
 from oracle import pw_oracle as O
+from oracle import pw_slicing as SL
 
 
 def _apply_h_without_kinetic(self, C):
@@ -120,6 +122,26 @@ def _plant(monkeypatch, what):
     elif what == "S-Ortho applied to psi only":
         so = L.s_ortho3
         monkeypatch.setattr(L, "s_ortho3", lambda X, HX, SX: (so(X, HX, SX)[0], HX, SX))
+    elif what == "window coefficients without the factor 2":
+        ic = SL.indicator_coefficients
+
+        def half(degree, ta, tb):
+            mu = ic(degree, ta, tb)
+            mu[1:] *= 0.5
+            return mu
+        monkeypatch.setattr(SL, "indicator_coefficients", half)
+    elif what == "Jackson damping left out":
+        monkeypatch.setattr(SL, "jackson_damping", lambda degree: np.ones(degree + 1))
+    elif what == "first Chebyshev step with 2/e":
+        def sum2(apply_a, X, coef, lo, hi):
+            c, e = 0.5 * (hi + lo), 0.5 * (hi - lo)
+            T0, T1 = X, 2.0 * (apply_a(X) - c * X) / e
+            acc = coef[0] * T0 + coef[1] * T1
+            for j in range(2, len(coef)):
+                T0, T1 = T1, 2.0 * (apply_a(T1) - c * T1) / e - T0
+                acc = acc + coef[j] * T1
+            return acc
+        monkeypatch.setattr(SL, "chebyshev_sum", sum2)
     else:  # pragma: no cover
         raise KeyError(what)
 
@@ -143,6 +165,9 @@ CASES = [
      lambda: lpins.test_lobpcg_converges_to_the_dense_eigenpairs(True, 4, 2, 1e-12)),
     ("preconditioner inverted", lpins.test_tpa_preconditioner_values),
     ("S-Ortho applied to psi only", lambda: lpins.test_s_ortho_is_s_orthonormal_with_the_same_span(False)),
+    ("window coefficients without the factor 2", lambda: spins.test_indicator_coefficients_match_quadrature(-0.3, 0.45)),
+    ("Jackson damping left out", lambda: spins.test_damped_window_is_bounded_and_approaches_the_indicator(40)),
+    ("first Chebyshev step with 2/e", spins.test_recurrence_sum_on_exact_eigenvectors),
 ]
 
 
