@@ -63,7 +63,7 @@ def parse():
     ap.add_argument("--tc-pieces", type=int, default=2,
                     help="bf16 pieces of the mixed GEMM operands: 2 (3 products) or 3 (6 products)")
     ap.add_argument("--fft-variant", type=int, default=None,
-                    help="pin the FFT kernel forms (x-line form + 8 * plane form) instead of autotuning")
+                    help="pin the FFT kernel forms (x-line form + 16 * plane form) instead of autotuning")
     ap.add_argument("--fft-batch-mb", type=int, default=None,
                     help="pin the FFT band batch (MB of half-box planes per launch) instead of autotuning")
     ap.add_argument("--bands", type=int, default=None,
@@ -444,7 +444,7 @@ def run_ours(args):
     pieces = ctx.tc_config()
     # pass 3 carries the recurrence (reads P Z and Y_{k-1}, writes the bf16 pieces of Y_{k+1})
     # when the warp-group plane kernels run without Q
-    fused = (fft_cfg[1] // 8 in (2, 3)) and prob.Q is None
+    fused = (fft_cfg[1] // 16 in (2, 3)) and prob.Q is None
     # GEMM launches per filter step: the projection of Y_k (and, with Q, of W = (T + V) Y_k for
     # the Woodbury correction), one back-projection; the class times also hold the bf16 splits
     # of the operands and the split-K sums of the projection
@@ -508,9 +508,15 @@ def run_ours(args):
                                               "warp groups, table twiddles, bands per CTA",
                                               "warp groups, table twiddles, radices swapped",
                                               "warp groups, table twiddles, bands per CTA, radices swapped",
-                                              "?"][fft_cfg[1] % 8],
+                                              "warp groups, table twiddles, staged planes",
+                                              "warp groups, table twiddles, bands per CTA, staged planes "
+                                              "(double-buffered)",
+                                              "warp groups, table twiddles, staged planes, radices swapped",
+                                              "warp groups, table twiddles, bands per CTA, staged planes "
+                                              "(double-buffered), radices swapped",
+                                              "?", "?", "?", "?", "?"][fft_cfg[1] % 16],
                              "plane_kernels": ["line groups", "one thread per line", "warp groups, whole plane",
-                                               "warp groups, sphere rows + 32-column slices"][fft_cfg[1] // 8],
+                                               "warp groups, sphere rows + 32-column slices"][fft_cfg[1] // 16],
                              "variant": fft_cfg[1]},
               "fp64": fp64, "eig_err_vs_fp64": eig_err,
               "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": bytes_psi,

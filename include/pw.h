@@ -163,8 +163,9 @@ PW_API int pw_rayleigh_ritz(pw_ctx* ctx, void* psi, int64_t ldpsi, int nband,
  * [filter (precision) -> Rayleigh-Ritz (FP64)], the cut of each later cycle
  * being the largest Ritz value.  psi: complex128 device block, overwritten with
  * the Ritz vectors.  eig, resid: host arrays of nband (resid may be NULL).
- * bounds (host, may be NULL) receives {upper, first cut}.  With PW_MIXED and Q == NULL
- * the Rayleigh quotients of the first cut come from the complex64 H-apply. */
+ * bounds (host, may be NULL) receives {upper, first cut}.  With PW_MIXED the Rayleigh
+ * quotients of the first cut take their numerators from the complex64 H-apply (their
+ * denominators, with Q, from the FP64 S-apply). */
 PW_API int pw_chebfi_solve(pw_ctx* ctx, void* psi, int64_t ldpsi, int nband, int degree,
                            int cycles, int lanczos_steps, const void* v0, int precision,
                            double* eig, double* resid, double* bounds);
@@ -250,6 +251,51 @@ PW_API int pw_diff_forward(pw_diff* diff, void* psi, int64_t ld, int lanczos_ste
 PW_API int pw_diff_backward(pw_diff* diff, const double* eig_bar, const void* psi_bar, int64_t ld,
                             int split, double* dV, double* dD, int accumulate);
 
+/* ---- spectrum slicing (the slice-wise solve the paper's closing section proposes) ----
+ * The wanted spectrum is cut into nslice slices [cuts[s], cuts[s+1]] (host, nslice + 1 strictly
+ * ascending values); slice s owns the nper bands [s nper, (s+1) nper) of psi.  Each slice's
+ * block is filtered by a window polynomial that passes that slice only, and then solved by a
+ * small Rayleigh-Ritz step of its own, independent of the other slices.  The paper names the
+ * method without formulas; the windows are the standard ones of the slicing literature: the
+ * Chebyshev expansion of the slice's indicator function on the spectrum mapped to [-1, 1]
+ * (t = (lambda - c)/e, c = (hi + lo)/2, e = (hi - lo)/2; [lo, hi] must contain the spectrum of
+ * A = S^-1 H), mu_0 = (acos ta - acos tb)/pi, mu_j = 2 (sin(j acos ta) - sin(j acos tb))/(j pi),
+ * damped by the Jackson factors g_j of the degree: p_s(t) = sum_{j <= degree} g_j mu_j T_j(t).
+ * pw_slice_filter: psi_s <- p_s(A~) psi_s for every slice, A~ = (A - c)/e.  One recurrence
+ * T_{j+1} = 2 A~ T_j - T_{j-1} runs over all nslice nper bands (the H-applies batched over the
+ * slices, as in pw_chebyshev_filter) and each band accumulates its own slice's coefficients.
+ * psi: device, element type of precision (complex128 / complex64).
+ * pw_spectrum_slice: pw_slice_filter (complex64 copy with PW_MIXED), then per slice an FP64
+ * S-Ortho + Rayleigh-Ritz step (as pw_rayleigh_ritz) on its nper bands.  psi: complex128,
+ * out: the Ritz vectors slice by slice; eig (host, nslice nper): each slice's Ritz values
+ * ascending; resid (host, may be NULL): their residual norms.  The caller keeps the values
+ * inside each slice.  PW_EINVAL for bad sizes, bounds or cuts; PW_ENOTSPD if a slice's block
+ * is numerically rank deficient (more vectors than the window leaves alive: lower nper). */
+PW_API int pw_slice_filter(pw_ctx* ctx, void* psi, int64_t ldpsi, int nslice, int nper, int degree, double lo,
+                           double hi, const double* cuts, int precision);
+PW_API int pw_spectrum_slice(pw_ctx* ctx, void* psi, int64_t ldpsi, int nslice, int nper, int degree, double lo,
+                             double hi, const double* cuts, int precision, double* eig, double* resid);
+
+/* ---- LOBPCG (Alg. 11), the vector-oriented solver the paper compares ChebFi with ----
+ * nblocks blocks of nband / nblocks consecutive bands, treated one after the other, each with
+ * up to nline line minimisations; FP64 throughout (H-apply, Grams, rotations).  Per block i:
+ * S-Deflate (Alg. 8) against the finished blocks (i > 1), H and S applied, S-Ortho (Alg. 9),
+ * Rayleigh-Ritz (Alg. 10); then per line minimisation the residual W = (H - Lambda S) Psi_i
+ * (the loop ends once every residual norm of the block is below tol; tol = 0: never), the
+ * diagonal Teter-Payne-Allan preconditioner K_G = p / (p + 16 x^4), p = 27 + 18 x + 12 x^2 +
+ * 8 x^3, x = t_G / E_kin(psi) (the paper names K a diagonal preconditioner without giving it),
+ * S-Deflate of W, H W and S W, S-Ortho + RR on [Psi_i W_i] (first minimisation) or [Psi_i W_i
+ * P_i], keeping the nband / nblocks lowest Ritz pairs: P_i <- the W and P part of the kept
+ * vectors, Psi_i <- the Psi part + P_i.  With nblocks > 1 a final S-Ortho + RR over all bands.
+ * psi: device complex128 block (ld >= npw), in: the starting bands, out: the S-orthonormal Ritz
+ * vectors.  eig (host, nband): Ritz values ascending; resid (host, nband, may be NULL):
+ * ||H psi_i - lambda_i S psi_i||; iters (host, nblocks, may be NULL): line minimisations done
+ * per block.  PW_EINVAL if nband is not a multiple of nblocks or nline < 0; PW_ENOTSPD if a
+ * Gram of S-Ortho is not numerically positive definite (a basis [Psi W P] that has lost rank,
+ * typically well past convergence: stop earlier with tol). */
+PW_API int pw_lobpcg_solve(pw_ctx* ctx, void* psi, int64_t ldpsi, int nband, int nblocks, int nline, double tol,
+                           double* eig, double* resid, int* iters);
+
 /* ---- Gamma-point pairing (time-reversal symmetry at k = 0) ----
  * At k = 0 a function real in r-space has coefficients c(-G) = conj c(G), and H maps such
  * functions to such functions when V_loc, D and Q are real and the projectors satisfy
@@ -334,13 +380,15 @@ enum pw_prof_class {
 };
 /* Autotuner: times the local-potential FFT passes on nband bands for several band
  * batch sizes (the batch's half-box planes from 16 MB to 2 GB) and, for PW_MIXED, the
- * forms of the pass kernels, variant = x-line form + 8 * plane form.  x-line forms:
+ * forms of the pass kernels, variant = x-line form + 16 * plane form.  x-line forms:
  * 0 line groups of 1-8 threads with shared-memory twiddles, 1 one thread per line with
  * compile-time twiddles, 2 groups of warps per 32 lines with compile-time twiddles,
  * 3 the same with run-time butterfly indices and table twiddles, 4 as 3 with several bands
  * per CTA, 5 and 6 as 3 and 4 with the two radices of the x plan in the other order (the
  * radix plan of the x-lines is thus a tuned choice; V_loc is kept permuted for both
- * orders).  Plane forms: 0 line groups, 1 one thread per line, 2 groups of warps per 32
+ * orders), 7-10 as 3-6 with each band's planes staged into shared memory by asynchronous
+ * copies (the several-band forms 8 and 10 double-buffered: band b + 1 in flight while band
+ * b is transformed).  Plane forms: 0 line groups, 1 one thread per line, 2 groups of warps per 32
  * lines with table twiddles over the whole plane in shared memory, 3 the same over the
  * plane's sphere rows and 32-column slices (less shared memory per CTA on large boxes).
  * Forms other than 0 cover box lengths with two-stage radix plans.  Keeps the fastest for

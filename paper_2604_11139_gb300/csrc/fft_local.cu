@@ -29,6 +29,13 @@
 
 namespace pw {
 
+// x-line kernel forms 3-10 (run-time butterfly indices, table twiddles): several bands per
+// CTA, the radices of the x plan swapped, the planes staged by asynchronous copies
+constexpr bool xf_twr(int xf) { return xf >= 3 && xf <= 10; }
+constexpr bool xf_multi(int xf) { return xf == 4 || xf == 6 || xf == 8 || xf == 10; }
+constexpr bool xf_swap(int xf) { return xf == 5 || xf == 6 || xf == 9 || xf == 10; }
+constexpr bool xf_staged(int xf) { return xf >= 7 && xf <= 10; }
+
 // ---- butterfly arithmetic ---------------------------------------------------------
 // complex64 butterflies use the paired FP32 instructions of sm_100-class SMs (one add,
 // multiply or fused multiply-add for both halves of a float2, each half rounded to nearest
@@ -1404,6 +1411,184 @@ __device__ __forceinline__ void xw_bf_fwd(const C* L, C* hbl, const C* __restric
   }
 }
 
+// Asynchronous global -> shared copies (LDGSTS) of the x-line forms: the CTA issues every
+// load of its lines at once and the data bypasses the registers, so the memory system sees
+// many requests in flight per SM while the butterflies of other CTAs run.
+template <int B>
+__device__ __forceinline__ void cp_async_el(void* sdst, const void* gsrc) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(sdst);
+  if constexpr (B == 16)
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gsrc) : "memory");
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(s), "l"(gsrc), "n"(B) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N> __device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+// Copies one band's np planes of the CTA's 32 lines into the line buffer Lb (element p of
+// lane l at Lb[p * 32 + l], which is where the first stage reads and writes it); lanes past
+// the end of the yz range are not copied (their results are never stored).
+template <typename C>
+__device__ __forceinline__ void xw_stage_planes(C* Lb, const C* hbb, int yz0, int nyz, int np) {
+  const int nl = min(32, nyz - yz0);
+  for (int q = threadIdx.x; q < np * 32; q += blockDim.x) {
+    const int p = q >> 5, l = q & 31;
+    if (l < nl) cp_async_el<sizeof(C)>(Lb + q, hbb + (int64_t)p * nyz + yz0 + l);
+  }
+  cp_async_commit();
+}
+
+// First inverse stage on lines already staged in shared memory, in place: butterfly J reads
+// and writes the slots J + R2 a, a < R1 (slots p >= np hold no plane and read as zero)
+template <typename C, int R1, int R2, int TA = R1 - 1, int TB = 1>
+__device__ __forceinline__ void xw_bf_inv_s(C* L, const C* __restrict__ tw1, int J, int np) {
+  C x[R1];
+#pragma unroll
+  for (int a = 0; a < R1; ++a) {
+    const int p = J + R2 * a;
+    x[a] = p < np ? L[p * 32] : czero<C>();
+  }
+  dftR<C, +1, R1>(x);
+  if (J) {
+#pragma unroll
+    for (int m = 1; m < R1; ++m) x[m] = cmul(x[m], cconj(__ldg(&tw1[J * TA + m * TB - 1])));
+  }
+#pragma unroll
+  for (int m = 0; m < R1; ++m) L[(J + R2 * m) * 32] = x[m];
+}
+
+// Staged form: the planes arrive by asynchronous copies and the V values of the thread's
+// second-stage blocks are loaded into registers while they are in flight.
+template <typename T, int N1, int TW, bool SW = false>
+__global__ void __launch_bounds__(32 * TW, 24 / TW) k_xline_tws(cplx<T>* __restrict__ hb, int64_t hb_bs,
+                                                      const T* __restrict__ vperm, SphereDev sp, FftPlan plan,
+                                                      const cplx<T>* __restrict__ tw) {
+  using C = cplx<T>;
+  constexpr CPlan P = make_cplan(N1);
+  static_assert(P.nst == 2, "two-stage plan expected");
+  constexpr int R1 = SW ? P.radix[1] : P.radix[0], R2 = SW ? P.radix[0] : P.radix[1];
+  constexpr int TA = SW ? 1 : R1 - 1, TB = SW ? R2 - 1 : 1;
+  constexpr int NBK = (R1 + TW - 1) / TW;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int lane = threadIdx.x & 31, t = threadIdx.x >> 5;
+  C* L0 = reinterpret_cast<C*>(smem_raw);
+  C* L = L0 + lane;
+  const int nyz = plan.n[1] * plan.n[2];
+  const int yz0 = blockIdx.x * 32, yz = yz0 + lane, b = blockIdx.y;
+  const bool live = yz < nyz;
+  const int np = sp.nplane;
+  const C* tw1 = tw + plan.d[0].tw_off[0];
+  C* hbb = hb + (int64_t)b * hb_bs;
+  xw_stage_planes<C>(L0, hbb, yz0, nyz, np);
+  T vr[NBK][R2];
+  {
+    const T* vb = vperm + (live ? yz : 0);
+#pragma unroll
+    for (int i = 0; i < NBK; ++i) {
+      const int blk = t + TW * i;
+#pragma unroll
+      for (int m = 0; m < R2; ++m) vr[i][m] = (live && blk < R1) ? vb[(int64_t)(blk * R2 + m) * nyz] : (T)0;
+    }
+  }
+  cp_async_wait<0>();
+  __syncthreads();
+#pragma unroll 1
+  for (int J = t; J < R2; J += TW) xw_bf_inv_s<C, R1, R2, TA, TB>(L, tw1, J, np);
+  __syncthreads();
+#pragma unroll
+  for (int i = 0; i < NBK; ++i) {
+    const int blk = t + TW * i;
+    if (blk < R1) {
+      C y[R2];
+#pragma unroll
+      for (int m = 0; m < R2; ++m) y[m] = L[(blk * R2 + m) * 32];
+      dftR<C, +1, R2>(y);
+#pragma unroll
+      for (int m = 0; m < R2; ++m) y[m] = cscale(y[m], vr[i][m]);
+      dftR<C, -1, R2>(y);
+#pragma unroll
+      for (int m = 0; m < R2; ++m) L[(blk * R2 + m) * 32] = y[m];
+    }
+  }
+  __syncthreads();
+  C* hbl = hbb + (live ? yz : 0);
+#pragma unroll 1
+  for (int J = t; J < R2; J += TW) xw_bf_fwd<C, -1, R1, R2, TA, TB>(L, hbl, tw1, J, nyz, 0, np, N1, live);
+}
+
+// Staged form with several bands per CTA and two line buffers: the copies of band b + 1 are
+// in flight while band b is transformed; the V values stay in registers for all bands.
+template <typename T, int N1, int TW, bool SW = false>
+__global__ void __launch_bounds__(32 * TW, 12 / TW) k_xline_twd(cplx<T>* __restrict__ hb, int64_t hb_bs, int nb,
+                                                      int bper, const T* __restrict__ vperm, SphereDev sp,
+                                                      FftPlan plan, const cplx<T>* __restrict__ tw) {
+  using C = cplx<T>;
+  constexpr CPlan P = make_cplan(N1);
+  static_assert(P.nst == 2, "two-stage plan expected");
+  constexpr int R1 = SW ? P.radix[1] : P.radix[0], R2 = SW ? P.radix[0] : P.radix[1];
+  constexpr int TA = SW ? 1 : R1 - 1, TB = SW ? R2 - 1 : 1;
+  constexpr int NBK = (R1 + TW - 1) / TW;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int lane = threadIdx.x & 31, t = threadIdx.x >> 5;
+  C* Lbuf = reinterpret_cast<C*>(smem_raw);  // two buffers of N1 * 32
+  const int nyz = plan.n[1] * plan.n[2];
+  const int yz0 = blockIdx.x * 32, yz = yz0 + lane;
+  const bool live = yz < nyz;
+  const int np = sp.nplane;
+  const C* tw1 = tw + plan.d[0].tw_off[0];
+  const int b_lo = blockIdx.y * bper, b_hi = min(nb, b_lo + bper);
+  if (b_lo >= b_hi) return;
+  xw_stage_planes<C>(Lbuf, hb + (int64_t)b_lo * hb_bs, yz0, nyz, np);
+  T vr[NBK][R2];
+  {
+    const T* vb = vperm + (live ? yz : 0);
+#pragma unroll
+    for (int i = 0; i < NBK; ++i) {
+      const int blk = t + TW * i;
+#pragma unroll
+      for (int m = 0; m < R2; ++m) vr[i][m] = (live && blk < R1) ? vb[(int64_t)(blk * R2 + m) * nyz] : (T)0;
+    }
+  }
+#pragma unroll 1
+  for (int b = b_lo; b < b_hi; ++b) {
+    C* Lc = Lbuf + ((b - b_lo) & 1) * (N1 * 32);
+    if (b + 1 < b_hi) {
+      // the other buffer was released by the barrier that ended the previous band
+      xw_stage_planes<C>(Lbuf + ((b + 1 - b_lo) & 1) * (N1 * 32), hb + (int64_t)(b + 1) * hb_bs, yz0, nyz, np);
+      cp_async_wait<1>();
+    } else {
+      cp_async_wait<0>();
+    }
+    __syncthreads();
+    C* L = Lc + lane;
+#pragma unroll 1
+    for (int J = t; J < R2; J += TW) xw_bf_inv_s<C, R1, R2, TA, TB>(L, tw1, J, np);
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < NBK; ++i) {
+      const int blk = t + TW * i;
+      if (blk < R1) {
+        C y[R2];
+#pragma unroll
+        for (int m = 0; m < R2; ++m) y[m] = L[(blk * R2 + m) * 32];
+        dftR<C, +1, R2>(y);
+#pragma unroll
+        for (int m = 0; m < R2; ++m) y[m] = cscale(y[m], vr[i][m]);
+        dftR<C, -1, R2>(y);
+#pragma unroll
+        for (int m = 0; m < R2; ++m) L[(blk * R2 + m) * 32] = y[m];
+      }
+    }
+    __syncthreads();
+    C* hbl = hb + (int64_t)b * hb_bs + (live ? yz : 0);
+#pragma unroll 1
+    for (int J = t; J < R2; J += TW) xw_bf_fwd<C, -1, R1, R2, TA, TB>(L, hbl, tw1, J, nyz, 0, np, N1, live);
+    __syncthreads();  // this buffer is staged again two bands later
+  }
+}
+
 template <typename T, int N1, int TW, bool SW = false>
 __global__ void __launch_bounds__(32 * TW, 24 / TW) k_xline_twr(cplx<T>* __restrict__ hb, int64_t hb_bs,
                                                       const T* __restrict__ vperm, SphereDev sp, FftPlan plan,
@@ -1557,11 +1742,33 @@ static cudaError_t launch_xline_tw(cplx<T>* hb, int64_t hb_bs, const T* vperm, c
 
 template <typename T, int N1, int TW, bool SW = false>
 static cudaError_t launch_xline_twr(cplx<T>* hb, int64_t hb_bs, const T* vperm, const SphereDev& sp,
-                                    const FftPlan& plan, const cplx<T>* tw, int nb, bool multi, cudaStream_t st) {
+                                    const FftPlan& plan, const cplx<T>* tw, int nb, bool multi, cudaStream_t st,
+                                    bool staged = false) {
   const size_t sm = sizeof(cplx<T>) * (size_t)N1 * 32;
   const int nyz = plan.n[1] * plan.n[2];
   const int gx = (nyz + 31) / 32;
   cudaError_t e;
+  if (staged && !multi) {
+    if ((e = cudaFuncSetAttribute(k_xline_tws<T, N1, TW, SW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm)))
+      return e;
+    if ((e = cudaFuncSetAttribute(k_xline_tws<T, N1, TW, SW>, cudaFuncAttributePreferredSharedMemoryCarveout, 100)))
+      return e;
+    k_xline_tws<T, N1, TW, SW><<<dim3(gx, nb), 32 * TW, sm, st>>>(hb, hb_bs, vperm, sp, plan, tw); count_launch();
+    return cudaGetLastError();
+  }
+  if (staged) {
+    const size_t sm2 = 2 * sm;
+    if ((e = cudaFuncSetAttribute(k_xline_twd<T, N1, TW, SW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm2)))
+      return e;
+    if ((e = cudaFuncSetAttribute(k_xline_twd<T, N1, TW, SW>, cudaFuncAttributePreferredSharedMemoryCarveout, 100)))
+      return e;
+    // a few bands per CTA, about three waves of CTAs
+    const int bper = std::max(2, (int)(((int64_t)nb * gx + 152 * 9 - 1) / (152 * 9)));
+    const int splits = (nb + bper - 1) / bper;
+    k_xline_twd<T, N1, TW, SW><<<dim3(gx, splits), 32 * TW, sm2, st>>>(hb, hb_bs, nb, bper, vperm, sp, plan, tw);
+    count_launch();
+    return cudaGetLastError();
+  }
   if (!multi) {
     if ((e = cudaFuncSetAttribute(k_xline_twr<T, N1, TW, SW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm)))
       return e;
@@ -1585,18 +1792,19 @@ static cudaError_t launch_xline_twr(cplx<T>* hb, int64_t hb_bs, const T* vperm, 
 // groups of warps per 32 x-lines, run-time butterfly indices (any two-stage plan)
 template <typename T>
 static cudaError_t xline_twr(cplx<T>* hb, int64_t hb_bs, const T* vperm, const SphereDev& sp, const FftPlan& plan,
-                             const cplx<T>* tw, int nb, bool multi, cudaStream_t st, bool swap = false) {
-#define PW_TWR_CASE(N)                                                                             \
-  case N:                                                                                          \
-    return swap ? launch_xline_twr<T, N, 4, true>(hb, hb_bs, vperm, sp, plan, tw, nb, multi, st)   \
-                : launch_xline_twr<T, N, 4, false>(hb, hb_bs, vperm, sp, plan, tw, nb, multi, st);
+                             const cplx<T>* tw, int nb, bool multi, cudaStream_t st, bool swap = false,
+                             bool staged = false) {
+#define PW_TWR_CASE(N)                                                                                   \
+  case N:                                                                                                \
+    return swap ? launch_xline_twr<T, N, 4, true>(hb, hb_bs, vperm, sp, plan, tw, nb, multi, st, staged)  \
+                : launch_xline_twr<T, N, 4, false>(hb, hb_bs, vperm, sp, plan, tw, nb, multi, st, staged);
   switch (plan.n[0]) {
     PW_TWR_CASE(24)
     PW_TWR_CASE(72)
     PW_TWR_CASE(90)
     PW_TWR_CASE(96)
     PW_TWR_CASE(120)
-    case 64: return launch_xline_twr<T, 64, 4>(hb, hb_bs, vperm, sp, plan, tw, nb, multi, st);  // 8 x 8
+    case 64: return launch_xline_twr<T, 64, 4>(hb, hb_bs, vperm, sp, plan, tw, nb, multi, st, staged);  // 8 x 8
     default: return cudaErrorNotSupported;
   }
 #undef PW_TWR_CASE
@@ -2558,26 +2766,27 @@ cudaError_t launch_local_apply(const FftPlan& plan, const cplx<T>* tw, const Sph
   const int nyz = plan.n[1] * plan.n[2];
   // one-thread-per-line kernels: complex64 only (a complex128 line per thread needs twice
   // the shared memory per CTA), when the context selected them
-  // kernel forms (complex64): x-line form = variant % 8 (0 line groups, 1 one thread per
+  // kernel forms (complex64): x-line form = variant % 16 (0 line groups, 1 one thread per
   // line, 2 warp groups with compile-time twiddles, 3 warp groups with table twiddles, 4 the
   // same with several bands per CTA, 5 and 6 as 3 and 4 with the two radices of the line's
-  // plan in the other order), plane form = variant / 8 (0 line groups, 1 one thread
+  // plan in the other order, 7-10 as 3-6 with the planes staged by asynchronous copies, the
+  // multi-band forms double-buffered), plane form = variant / 16 (0 line groups, 1 one thread
   // per line, 2 warp groups over the whole plane, 3 warp groups over sphere rows and 32-column
   // slices)
   const int fv = (std::is_same<T, float>::value && prof) ? prof->fft_variant[0] : 0;
-  int xf = fv % 8;
-  const int pf = fv / 8;
+  int xf = fv % kFormStride;
+  const int pf = fv / kFormStride;
   // the swapped-radix x-line forms need V permuted for that order: the context's potential
   // has such a copy, an arbitrary potential (pw_local_apply) takes the unswapped form; the
   // fallbacks for lengths those forms do not cover keep the usual permutation
   const T* vperm_x = vperm;
-  if (xf >= 5) {
+  if (xf_swap(xf)) {
     if (prof && prof->vperm32_sw && (const void*)vperm == (const void*)prof->vperm32)
       vperm_x = (const T*)prof->vperm32_sw;
     else xf -= 2;
   }
   const bool tpl = pf == 1, pwg = pf == 2, prs = pf == 3;
-  const bool xtw = xf == 2, xtwr = xf >= 3 && xf <= 6;
+  const bool xtw = xf == 2, xtwr = xf_twr(xf);
   for (int b0 = 0; b0 < nband; b0 += band_batch) {
     const int nb = min(band_batch, nband - b0);
     prof_begin(prof, PW_PROF_PLANE_INV);
@@ -2603,7 +2812,8 @@ cudaError_t launch_local_apply(const FftPlan& plan, const cplx<T>* tw, const Sph
     if constexpr (std::is_same<T, float>::value) {
       if (xtw) e = xline_tw<T>(hb, hb_bs, vperm, sp, plan, nb, st);
       if (xtwr)
-        e = xline_twr<T>(hb, hb_bs, xf >= 5 ? vperm_x : vperm, sp, plan, tw, nb, xf == 4 || xf == 6, st, xf >= 5);
+        e = xline_twr<T>(hb, hb_bs, xf_swap(xf) ? vperm_x : vperm, sp, plan, tw, nb, xf_multi(xf), st, xf_swap(xf),
+                         xf_staged(xf));
       if (xf == 1) {
         (void)cudaGetLastError();
         e = xline_tpl<T>(hb, hb_bs, vperm, sp, plan, nb, st);
@@ -2652,7 +2862,7 @@ static bool plane_rs_covers(const FftPlan& plan) {
 
 bool local_apply_rec_supported(const FftPlan& plan, const ::pw_ctx* prof) {
   if (!prof) return false;
-  const int pf = prof->fft_variant[0] / 8;
+  const int pf = prof->fft_variant[0] / kFormStride;
   return (pf == 2 && plane_wg_covers(plan)) || (pf == 3 && plane_rs_covers(plan));
 }
 
@@ -2663,13 +2873,13 @@ cudaError_t launch_local_apply_rec(const FftPlan& plan, const float2* tw, const 
   using T = float;
   if (!local_apply_rec_supported(plan, prof)) return cudaErrorNotSupported;
   if (nband <= 0) return cudaSuccess;
-  int xf = prof->fft_variant[0] % 8;
+  int xf = prof->fft_variant[0] % kFormStride;
   const float* vperm_x = vperm;
-  if (xf >= 5) {
+  if (xf_swap(xf)) {
     if (prof->vperm32_sw && vperm == prof->vperm32) vperm_x = prof->vperm32_sw;
     else xf -= 2;
   }
-  const bool prs = prof->fft_variant[0] / 8 == 3;
+  const bool prs = prof->fft_variant[0] / kFormStride == 3;
   const int64_t hb_bs = (int64_t)sp.nplane * plan.n[1] * plan.n[2];
   const int nyz = plan.n[1] * plan.n[2];
   const int lyz = 32;
@@ -2685,8 +2895,9 @@ cudaError_t launch_local_apply_rec(const FftPlan& plan, const float2* tw, const 
     prof_begin(prof, PW_PROF_XLINE);
     e = cudaErrorNotSupported;
     if (xf == 2) e = xline_tw<T>(hb, hb_bs, vperm, sp, plan, nb, st);
-    if (xf >= 3 && xf <= 6)
-      e = xline_twr<T>(hb, hb_bs, xf >= 5 ? vperm_x : vperm, sp, plan, tw, nb, xf == 4 || xf == 6, st, xf >= 5);
+    if (xf_twr(xf))
+      e = xline_twr<T>(hb, hb_bs, xf_swap(xf) ? vperm_x : vperm, sp, plan, tw, nb, xf_multi(xf), st, xf_swap(xf),
+                       xf_staged(xf));
     if (xf == 1) e = xline_tpl<T>(hb, hb_bs, vperm, sp, plan, nb, st);
     if (e == cudaErrorNotSupported) {
       (void)cudaGetLastError();

@@ -28,4 +28,13 @@ cudaError_t la_lanczos(const double2* v0, int n, int steps, double2* v, double2*
                        double* bound, ApplyFn apply, void* ctx, cudaStream_t st);
 cudaError_t la_to_c64(const double2* a, int64_t lda, float2* b, int64_t ldb, int n, int m, cudaStream_t st);
 cudaError_t la_to_c128(const float2* a, int64_t lda, double2* b, int64_t ldb, int n, int m, cudaStream_t st);
+// LOBPCG: W = K (HX - lam SX) with the Teter-Payne-Allan preconditioner, rn = residual norms
+cudaError_t la_lob_resid(const double2* HX, const double2* SX, const double2* X, int64_t ld, int npw, int m,
+                         const double* lam, const double* kin, double2* W, int64_t ldw, double* rn, cudaStream_t st);
+// B (k x 2 keep) = [C without its first keep rows | C]
+cudaError_t la_lob_coef(const double2* C, int k, int keep, double2* B, cudaStream_t st);
+// spectrum slicing: out[:, j] = (first ? 0 : out[:, j]) + coef[j] y[:, j] (coef: device, nband)
+template <typename T>
+cudaError_t la_cheb_acc(const cplx<T>* y, int64_t ldy, int npw, int nband, const double* coef, cplx<T>* out,
+                        int64_t ldo, int first, cudaStream_t st);
 }  // namespace pw

@@ -6,6 +6,8 @@
 // quotients, residual norms) and the Lanczos helpers of the spectrum bound.
 #include <math.h>
 
+#include <algorithm>
+
 #include "pw_internal.cuh"
 #include "la.cuh"
 
@@ -595,5 +597,112 @@ cudaError_t la_to_c128(const float2* a, int64_t lda, double2* b, int64_t ldb, in
   k_c64_to_c128<<<(unsigned)((t + 255) / 256), 256, 0, st>>>(a, lda, b, ldb, n, m); count_launch();
   return cudaGetLastError();
 }
+
+
+// ---- LOBPCG helpers (Alg. 11) ----------------------------------------------------------
+// W_j = K_j (HX_j - lam_j SX_j), K_j the Teter-Payne-Allan preconditioner of band j,
+// K = p / (p + 16 x^4), p = 27 + 18 x + 12 x^2 + 8 x^3, x = t_G / E_kin(X_j),
+// E_kin = sum t_G |x_G|^2 / sum |x_G|^2; rn[j] = || HX_j - lam_j SX_j || before K
+__global__ void __launch_bounds__(256) k_lob_resid(const double2* __restrict__ HX, const double2* __restrict__ SX,
+                                                   const double2* __restrict__ X, int64_t ld, int npw,
+                                                   const double* __restrict__ lam, const double* __restrict__ kin,
+                                                   double2* __restrict__ W, int64_t ldw, double* __restrict__ rn) {
+  const int j = blockIdx.x;
+  const double l = lam[j];
+  const double2* h = HX + (int64_t)j * ld;
+  const double2* s = SX + (int64_t)j * ld;
+  const double2* x = X + (int64_t)j * ld;
+  double sk = 0, sn = 0, sr = 0;
+  for (int g = threadIdx.x; g < npw; g += blockDim.x) {
+    const double2 xv = x[g];
+    const double a = xv.x * xv.x + xv.y * xv.y;
+    sk += kin[g] * a;
+    sn += a;
+    const double rx = h[g].x - l * s[g].x, ry = h[g].y - l * s[g].y;
+    sr += rx * rx + ry * ry;
+  }
+  __shared__ double s1[256], s2[256], s3[256];
+  s1[threadIdx.x] = sk; s2[threadIdx.x] = sn; s3[threadIdx.x] = sr;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if (threadIdx.x < o) {
+      s1[threadIdx.x] += s1[threadIdx.x + o];
+      s2[threadIdx.x] += s2[threadIdx.x + o];
+      s3[threadIdx.x] += s3[threadIdx.x + o];
+    }
+    __syncthreads();
+  }
+  const double ekin = s1[0] / s2[0];
+  if (threadIdx.x == 0) rn[j] = sqrt(s3[0]);
+  double2* w = W + (int64_t)j * ldw;
+  for (int g = threadIdx.x; g < npw; g += blockDim.x) {
+    const double xx = kin[g] / ekin;
+    const double p = 27.0 + xx * (18.0 + xx * (12.0 + 8.0 * xx));
+    const double x2 = xx * xx;
+    const double k = p / (p + 16.0 * x2 * x2);
+    w[g] = make_double2(k * (h[g].x - l * s[g].x), k * (h[g].y - l * s[g].y));
+  }
+}
+
+cudaError_t la_lob_resid(const double2* HX, const double2* SX, const double2* X, int64_t ld, int npw, int m,
+                         const double* lam, const double* kin, double2* W, int64_t ldw, double* rn, cudaStream_t st) {
+  if (m <= 0) return cudaSuccess;
+  k_lob_resid<<<m, 256, 0, st>>>(HX, SX, X, ld, npw, lam, kin, W, ldw, rn); count_launch();
+  return cudaGetLastError();
+}
+
+// B (k x 2 keep, ld k) = [C with its first `keep` rows zeroed | C], C (k x keep, ld k): Z B gives
+// [P_new | Psi_new] in one product
+__global__ void k_lob_coef(const double2* __restrict__ C, int k, int keep, double2* __restrict__ B) {
+  const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (idx >= (int64_t)k * 2 * keep) return;
+  const int r = (int)(idx % k), c = (int)(idx / k);
+  const double2 v = C[(int64_t)(c % keep) * k + r];
+  B[idx] = (c < keep && r < keep) ? make_double2(0.0, 0.0) : v;
+}
+
+cudaError_t la_lob_coef(const double2* C, int k, int keep, double2* B, cudaStream_t st) {
+  const int64_t n = (int64_t)k * 2 * keep;
+  if (n <= 0) return cudaSuccess;
+  k_lob_coef<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(C, k, keep, B); count_launch();
+  return cudaGetLastError();
+}
+
+
+// ---- spectrum slicing: per-column Chebyshev sums over the filter's steps ----------------
+// out[:, j] (=, or +=) coef[j] y[:, j]
+template <typename T>
+__global__ void k_cheb_acc(const cplx<T>* __restrict__ y, int64_t ldy, int npw, int nband,
+                           const double* __restrict__ coef, cplx<T>* __restrict__ out, int64_t ldo, int first) {
+  const int64_t total = (int64_t)npw * nband;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int g = (int)(idx % npw), j = (int)(idx / npw);
+    const T c = (T)coef[j];
+    const cplx<T> v = y[(int64_t)j * ldy + g];
+    cplx<T>* o = out + (int64_t)j * ldo + g;
+    if (first) {
+      o->x = c * v.x;
+      o->y = c * v.y;
+    } else {
+      o->x += c * v.x;
+      o->y += c * v.y;
+    }
+  }
+}
+
+template <typename T>
+cudaError_t la_cheb_acc(const cplx<T>* y, int64_t ldy, int npw, int nband, const double* coef, cplx<T>* out,
+                        int64_t ldo, int first, cudaStream_t st) {
+  const int64_t total = (int64_t)npw * nband;
+  if (total <= 0) return cudaSuccess;
+  const unsigned grid = (unsigned)std::min<int64_t>((total + 255) / 256, 152 * 16);
+  k_cheb_acc<T><<<grid, 256, 0, st>>>(y, ldy, npw, nband, coef, out, ldo, first); count_launch();
+  return cudaGetLastError();
+}
+template cudaError_t la_cheb_acc<float>(const cplx<float>*, int64_t, int, int, const double*, cplx<float>*, int64_t,
+                                        int, cudaStream_t);
+template cudaError_t la_cheb_acc<double>(const cplx<double>*, int64_t, int, int, const double*, cplx<double>*,
+                                         int64_t, int, cudaStream_t);
 
 }  // namespace pw

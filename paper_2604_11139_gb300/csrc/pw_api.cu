@@ -1,8 +1,9 @@
 // C ABI of the Chebyshev-filtered plane-wave H-apply: context set-up (plane-wave
 // sphere, FFT plans, projectors, Woodbury matrices) and the entry points of pw.h.
-// Host code here only builds index tables, sizes workspaces and sequences
-// kernel launches; every arithmetic step of the path runs in the kernels of
-// fft_local.cu, gemm_simt.cu, la_fp64.cu and setup_kernels.cu.
+// Host code here only builds index and coefficient tables, sizes workspaces and
+// sequences kernel launches; every arithmetic step of the path runs in the kernels
+// of fft_local.cu, gemm_simt.cu, gemm_tc.cu, zgemm_tc.cu, la_fp64.cu and
+// setup_kernels.cu.
 #include <math.h>
 #include <stdarg.h>
 #include <stdio.h>
@@ -10,8 +11,10 @@
 
 #include <algorithm>
 #include <atomic>
+#include <cmath>
 #include <new>
 #include <type_traits>
+#include <vector>
 
 #include "la.cuh"
 #include "pw_internal.cuh"
@@ -38,6 +41,10 @@ int cuda_status(cudaError_t e, const char* where) {
 }
 
 void* ws_get(pw_ctx* c, int slot, size_t bytes, int* status) {
+  if (slot < 0 || slot >= WS_NUM) {
+    *status = set_error(PW_EINVAL, "workspace slot %d out of range", slot);
+    return nullptr;
+  }
   if (bytes == 0) bytes = 16;
   pw_ctx::Buf& b = c->ws[slot];
   if (b.bytes >= bytes) return b.p;
@@ -541,11 +548,28 @@ int apply_s64(pw_ctx* ctx, const double2* psi, int64_t ldpsi, int nband, double2
 // ---------------------------------------------------------------------------
 // Chebyshev filter (Alg. 7 / Alg. 12)
 // ---------------------------------------------------------------------------
+// Per-column Chebyshev sum carried along the filter's steps (spectrum slicing):
+// out[:, j] = sum_k coef[k nband + j] T_k(A~) psi_j, coef on the device ((degree + 1) x nband)
+template <typename T> struct ChebSum {
+  cplx<T>* out;
+  int64_t ldo;
+  const double* coef;
+};
+
 template <typename T>
 int filter_impl(pw_ctx* ctx, cplx<T>* psi, int64_t ldpsi, int nband, int degree, double a, double b,
-                const double* dev_ce = nullptr) {
+                const double* dev_ce = nullptr, const ChebSum<T>* sum = nullptr) {
   using C = cplx<T>;
   if (degree <= 0 || nband <= 0) return PW_OK;
+  // Y_k = T_k(A~) psi after step k (the unscaled recurrence); the sum takes coef_k Y_k
+  auto add_term = [&](const C* y, int64_t ldy, int k) -> int {
+    if (!sum) return PW_OK;
+    ProfScope ps(ctx, PW_PROF_SMALL);
+    CU_TRY(la_cheb_acc<T>(y, ldy, ctx->npw, nband, sum->coef + (size_t)k * nband, sum->out, sum->ldo, k == 0,
+                          ctx->stream), "Chebyshev sum");
+    return PW_OK;
+  };
+  PW_TRY(add_term(psi, ldpsi, 0));
   if (!dev_ce && !(b > a)) return set_error(PW_EINVAL, "filter interval needs upper > lower (a=%g, b=%g)", a, b);
   const int npw = ctx->npw, np = ctx->nproj;
   const cudaStream_t st = ctx->stream;
@@ -628,6 +652,7 @@ int filter_impl(pw_ctx* ctx, cplx<T>* psi, int64_t ldpsi, int nband, int degree,
         rec.pieces = ctx->tc_pieces;
         CU_TRY(launch_local_apply_rec(ctx->plan, ctx->tw32, ctx->sp, ctx->vperm32, ctx->kin32, (const float2*)cur, ldc,
                                       nband, (float2*)dst, ldd, (float2*)hb, bb, st, ctx, rec), "filter local + recurrence");
+        PW_TRY(add_term(dst, ldd, k + 1));
       }
       if (degree % 3 != 0) {
         CU_TRY(cudaMemcpy2DAsync(psi, sizeof(C) * ldpsi, buf[degree % 3], sizeof(C) * npw, sizeof(C) * npw, nband,
@@ -686,6 +711,7 @@ int filter_impl(pw_ctx* ctx, cplx<T>* psi, int64_t ldpsi, int nband, int degree,
       te.split_piece_stride = ys_ps;
       te.out_pieces = (k + 1 < degree) ? ctx->tc_pieces : 0;
       PW_TRY(tc_backproject(ctx, zs, nband, te));
+      PW_TRY(add_term(dst, ldd, k + 1));
       continue;
     }
     Epi<T> ce = epi<T>(EPI_CHEB, dst, ldd, alpha);
@@ -721,6 +747,7 @@ int filter_impl(pw_ctx* ctx, cplx<T>* psi, int64_t ldpsi, int nband, int degree,
       ProfScope ps(ctx, PW_PROF_GEMM_BACK);
       PW_TRY(cg<T>(ctx, 0, 0, npw, nband, 0, Prec<T>::P(ctx), npw, Z, 1, ce, 1, spl, st, GEMM_FULL, "filter recurrence"));
     }
+    PW_TRY(add_term(dst, ldd, k + 1));
   }
   if (degree % 3 != 0) {
     CU_TRY(cudaMemcpy2DAsync(psi, sizeof(C) * ldpsi, buf[degree % 3], sizeof(C) * npw, sizeof(C) * npw, nband,
@@ -927,6 +954,209 @@ int rr_impl(pw_ctx* ctx, double2* Y, int64_t ldy, int m, double2* hpsi_out, doub
   if (eig_h) CU_TRY(cudaMemcpyAsync(eig_h, eig, sizeof(double) * m, cudaMemcpyDeviceToHost, st), "eig copy");
   if (resid_h) CU_TRY(cudaMemcpyAsync(resid_h, resid, sizeof(double) * m, cudaMemcpyDeviceToHost, st), "resid copy");
   CU_TRY(cudaStreamSynchronize(st), "rr sync");
+  return PW_OK;
+}
+
+// ---------------------------------------------------------------------------
+// LOBPCG with b blocks and k line minimisations (Alg. 11), FP64, with S-Deflate (Alg. 8),
+// S-Ortho (Alg. 9) and RR (Alg. 10) as its steps
+// ---------------------------------------------------------------------------
+// S-Ortho of the k columns of X with H X and S X: S_X = X^dagger S X = L L^dagger (Cholesky),
+// each block <- (.) L^{-dagger}.  tmp: npw x k scratch (ld npw).
+int sortho3(pw_ctx* ctx, double2* X, int64_t ldx, double2* HX, int64_t ldh, double2* SX, int64_t lds, int k,
+            double2* tmp, int* flag, const char* what) {
+  const int npw = ctx->npw;
+  const cudaStream_t st = ctx->stream;
+  WS(G, double2, WS_GRAM, (size_t)k * k);
+  WS(Linv, double2, WS_LINV, (size_t)k * k);
+  WS(t, double2, WS_TMP, (size_t)k * k);
+  CU_TRY(cudaMemsetAsync(flag, 0, sizeof(int), st), "flag reset");
+  PW_TRY(gram_chol(ctx, X, ldx, SX, lds, k, G, Linv, t, flag));
+  PW_TRY(check_flag(ctx, flag, what));
+  double2* blocks[3] = {X, HX, SX};
+  const int64_t lds3[3] = {ldx, ldh, lds};
+  for (int b = 0; b < 3; ++b) {
+    PW_TRY(cg<double>(ctx, 0, 1, npw, k, k, blocks[b], lds3[b], Linv, k, epi<double>(EPI_STORE, tmp, npw), 1, nullptr,
+                      st, GEMM_B_UPPER, "s-ortho rotate"));
+    CU_TRY(cudaMemcpy2DAsync(blocks[b], sizeof(double2) * lds3[b], tmp, sizeof(double2) * npw, sizeof(double2) * npw,
+                             k, cudaMemcpyDeviceToDevice, st), "s-ortho copy");
+  }
+  return PW_OK;
+}
+
+// RR on the basis Z (k columns) with H Z, S Z: H_Z x = lambda S_Z x by Cholesky reduction and the
+// Hermitian eigensolver; C (k x k, ld k) <- the eigenvector coefficients (ascending Ritz values,
+// so the first `keep` columns are the kept pairs), *eig_dev <- the Ritz values (device, k)
+int rr_coeffs(pw_ctx* ctx, const double2* Z, int64_t ldz, const double2* HZ, int64_t ldh, const double2* SZ,
+              int64_t lds, int k, double2* C, double** eig_dev, int* flag) {
+  const cudaStream_t st = ctx->stream;
+  WS(G, double2, WS_GRAM, (size_t)k * k);
+  WS(G2, double2, WS_GRAM2, (size_t)k * k);
+  WS(Linv, double2, WS_LINV, (size_t)k * k);
+  WS(tmp, double2, WS_TMP, (size_t)k * k);
+  WS(U, double2, WS_U, (size_t)k * k);
+  WS(jac, double2, WS_JAC, (size_t)3 * k * k + k + 2);
+  WS(ev, double, WS_EIG, (size_t)2 * k + 4);
+  CU_TRY(cudaMemsetAsync(flag, 0, sizeof(int), st), "flag reset");
+  PW_TRY(gram_herm(ctx, Z, ldz, HZ, ldh, k, G2));
+  PW_TRY(gram_chol(ctx, Z, ldz, SZ, lds, k, G, Linv, tmp, flag));
+  CU_TRY(launch_cgemm<double>(0, 1, k, k, k, G2, k, Linv, k, epi<double>(EPI_STORE, tmp, k), 1, nullptr, st), "reduce 1");
+  CU_TRY(launch_cgemm<double>(0, 0, k, k, k, Linv, k, tmp, k, epi<double>(EPI_STORE, G, k), 1, nullptr, st), "reduce 2");
+  CU_TRY(la_herm_sym(G, k, k, st), "reduced sym");
+  PW_TRY(check_flag(ctx, flag, "LOBPCG Rayleigh-Ritz Cholesky"));
+  int sweeps = 0;
+  PW_TRY(la_jacobi_eigh(G, k, U, ev, jac, ev + 2 * k, st, 40, 1e-13, &sweeps));
+  CU_TRY(launch_cgemm<double>(1, 0, k, k, k, Linv, k, U, k, epi<double>(EPI_STORE, C, k), 1, nullptr, st), "back-transform");
+  *eig_dev = ev;
+  return PW_OK;
+}
+
+int lobpcg_impl(pw_ctx* ctx, double2* psi, int64_t ld, int M, int nblk, int nline, double tol, double* eig_h,
+                double* resid_h, int* its_h) {
+  PW_TRY(check_tc_flag(ctx));
+  const int npw = ctx->npw, bs = M / nblk;
+  const cudaStream_t st = ctx->stream;
+  const size_t zs = (size_t)npw * 3 * bs;  // one of Z = [Psi_i W_i P_i], H Z, S Z
+  WS(Zb, double2, WS_LOBZ, 3 * zs);
+  WS(T, double2, WS_LOBT, (size_t)npw * std::max(3 * bs, M));
+  WS(HY, double2, WS_HY, (size_t)npw * M);
+  WS(SY, double2, WS_SY, (size_t)npw * M);
+  const size_t kc = std::max((size_t)9 * bs * bs, (size_t)M * M);
+  WS(Bb, double2, WS_LOBB, (size_t)6 * bs * bs + kc);
+  double2* B = Bb;            // [C without the Psi rows | C], 3bs x 2bs
+  double2* Cf = Bb + (size_t)6 * bs * bs;
+  WS(R, double, WS_LOBR, (size_t)3 * M + 16);
+  double* lam_all = R;         // device Ritz values, block by block
+  double* rn = R + M;          // residual norms of the current block
+  double* res_all = R + 2 * M;
+  WS(dfl, double2, WS_LOBD, (size_t)M * bs);
+  WS(scal, int, WS_SCAL, 16);
+  double2 *Z = Zb, *HZ = Zb + zs, *SZ = Zb + 2 * zs;
+  const size_t cb = (size_t)npw * bs;  // one column block
+  std::vector<double> rn_h(bs);
+  for (int i = 0; i < nblk; ++i) {
+    double* lam = lam_all + (size_t)i * bs;
+    const int mp = i * bs;
+    // S-Deflate of A (bs columns, ld npw) against the finished blocks psi[:, 0:mp] (S psi in SY)
+    auto deflate = [&](double2* A) -> int {
+      PW_TRY(cg<double>(ctx, 1, 0, mp, bs, npw, SY, npw, A, npw, epi<double>(EPI_STORE, dfl, mp), 1, nullptr, st,
+                        GEMM_FULL, "s-deflate overlap"));
+      PW_TRY(cg<double>(ctx, 0, 0, npw, bs, mp, psi, ld, dfl, mp, epi<double>(EPI_ACCUM, A, npw, -1.0), 1, nullptr, st,
+                        GEMM_FULL, "s-deflate update"));
+      return PW_OK;
+    };
+    CU_TRY(cudaMemcpy2DAsync(Z, sizeof(double2) * npw, psi + (size_t)i * bs * ld, sizeof(double2) * ld,
+                             sizeof(double2) * npw, bs, cudaMemcpyDeviceToDevice, st), "block copy");
+    if (i > 0) PW_TRY(deflate(Z));
+    PW_TRY(apply_impl<double>(ctx, Z, npw, bs, HZ, SZ, npw));
+    PW_TRY(sortho3(ctx, Z, npw, HZ, npw, SZ, npw, bs, T, scal, "LOBPCG S-Ortho"));
+    double* ev = nullptr;
+    PW_TRY(rr_coeffs(ctx, Z, npw, HZ, npw, SZ, npw, bs, Cf, &ev, scal));
+    for (double2* A : {Z, HZ, SZ}) {
+      PW_TRY(cg<double>(ctx, 0, 0, npw, bs, bs, A, npw, Cf, bs, epi<double>(EPI_STORE, T, npw), 1, nullptr, st,
+                        GEMM_FULL, "LOBPCG rotation"));
+      CU_TRY(cudaMemcpyAsync(A, T, sizeof(double2) * cb, cudaMemcpyDeviceToDevice, st), "rotation copy");
+    }
+    CU_TRY(cudaMemcpyAsync(lam, ev, sizeof(double) * bs, cudaMemcpyDeviceToDevice, st), "Ritz values");
+    int done = 0;
+    for (int n = 0; n < nline; ++n) {
+      // W = K (H - Lambda S) Psi_i; the block's line loop ends once every residual is below tol
+      CU_TRY(la_lob_resid(HZ, SZ, Z, npw, npw, bs, lam, ctx->kin64, Z + cb, npw, rn, st), "LOBPCG residual");
+      CU_TRY(cudaMemcpyAsync(rn_h.data(), rn, sizeof(double) * bs, cudaMemcpyDeviceToHost, st), "residual copy");
+      CU_TRY(cudaStreamSynchronize(st), "residual sync");
+      if (*std::max_element(rn_h.begin(), rn_h.end()) < tol) break;
+      if (i > 0) PW_TRY(deflate(Z + cb));
+      PW_TRY(apply_impl<double>(ctx, Z + cb, npw, bs, HZ + cb, SZ + cb, npw));
+      const int kz = n == 0 ? 2 * bs : 3 * bs;
+      PW_TRY(sortho3(ctx, Z, npw, HZ, npw, SZ, npw, kz, T, scal, "LOBPCG S-Ortho"));
+      PW_TRY(rr_coeffs(ctx, Z, npw, HZ, npw, SZ, npw, kz, Cf, &ev, scal));
+      CU_TRY(la_lob_coef(Cf, kz, bs, B, st), "LOBPCG coefficients");
+      // [P_new | Psi_new] = Z B for Z, H Z, S Z; Psi_new = Psi part + P_new
+      for (double2* A : {Z, HZ, SZ}) {
+        PW_TRY(cg<double>(ctx, 0, 0, npw, 2 * bs, kz, A, npw, B, kz, epi<double>(EPI_STORE, T, npw), 1, nullptr, st,
+                          GEMM_FULL, "LOBPCG update"));
+        CU_TRY(cudaMemcpyAsync(A, T + cb, sizeof(double2) * cb, cudaMemcpyDeviceToDevice, st), "Psi update");
+        CU_TRY(cudaMemcpyAsync(A + 2 * cb, T, sizeof(double2) * cb, cudaMemcpyDeviceToDevice, st), "P update");
+      }
+      CU_TRY(cudaMemcpyAsync(lam, ev, sizeof(double) * bs, cudaMemcpyDeviceToDevice, st), "Ritz values");
+      done = n + 1;
+    }
+    if (its_h) its_h[i] = done;
+    CU_TRY(cudaMemcpy2DAsync(psi + (size_t)i * bs * ld, sizeof(double2) * ld, Z, sizeof(double2) * npw,
+                             sizeof(double2) * npw, bs, cudaMemcpyDeviceToDevice, st), "block store");
+    CU_TRY(cudaMemcpyAsync(HY + (size_t)i * cb, HZ, sizeof(double2) * cb, cudaMemcpyDeviceToDevice, st), "H block");
+    CU_TRY(cudaMemcpyAsync(SY + (size_t)i * cb, SZ, sizeof(double2) * cb, cudaMemcpyDeviceToDevice, st), "S block");
+  }
+  if (nblk > 1) {  // global S-Ortho + RR over all the bands
+    PW_TRY(sortho3(ctx, psi, ld, HY, npw, SY, npw, M, T, scal, "LOBPCG final S-Ortho"));
+    double* ev = nullptr;
+    PW_TRY(rr_coeffs(ctx, psi, ld, HY, npw, SY, npw, M, Cf, &ev, scal));
+    double2* blocks[3] = {psi, HY, SY};
+    const int64_t lds3[3] = {ld, npw, npw};
+    for (int b = 0; b < 3; ++b) {
+      PW_TRY(cg<double>(ctx, 0, 0, npw, M, M, blocks[b], lds3[b], Cf, M, epi<double>(EPI_STORE, T, npw), 1, nullptr,
+                        st, GEMM_FULL, "LOBPCG final rotation"));
+      CU_TRY(cudaMemcpy2DAsync(blocks[b], sizeof(double2) * lds3[b], T, sizeof(double2) * npw, sizeof(double2) * npw,
+                               M, cudaMemcpyDeviceToDevice, st), "final rotation copy");
+    }
+    CU_TRY(cudaMemcpyAsync(lam_all, ev, sizeof(double) * M, cudaMemcpyDeviceToDevice, st), "Ritz values");
+  }
+  CU_TRY(la_resid(HY, npw, SY, npw, npw, M, lam_all, res_all, st), "residuals");
+  CU_TRY(cudaMemcpyAsync(eig_h, lam_all, sizeof(double) * M, cudaMemcpyDeviceToHost, st), "eig copy");
+  if (resid_h) CU_TRY(cudaMemcpyAsync(resid_h, res_all, sizeof(double) * M, cudaMemcpyDeviceToHost, st), "resid copy");
+  CU_TRY(cudaStreamSynchronize(st), "LOBPCG sync");
+  return PW_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Spectrum slicing (the slice-wise solve the paper's closing section proposes)
+// ---------------------------------------------------------------------------
+// Jackson-damped Chebyshev coefficients of the indicator of [a, b] for a spectrum inside
+// [lo, hi] (mapped to [-1, 1]; the slice clipped to it): out[j] = g_j mu_j, j = 0..degree
+void window_coefficients(int degree, double a, double b, double lo, double hi, double* out) {
+  const double pi = 3.14159265358979323846264338327950288;
+  const double c = 0.5 * (hi + lo), e = 0.5 * (hi - lo);
+  const double ta = std::min(std::max((a - c) / e, -1.0), 1.0), tb = std::min(std::max((b - c) / e, -1.0), 1.0);
+  const double tha = std::acos(ta), thb = std::acos(tb);
+  const double al = pi / (degree + 2);
+  for (int j = 0; j <= degree; ++j) {
+    const double g = ((1.0 - (double)j / (degree + 2)) * std::sin(al) * std::cos(j * al) +
+                      std::cos(al) * std::sin(j * al) / (degree + 2)) / std::sin(al);
+    const double mu = j == 0 ? (tha - thb) / pi : 2.0 * (std::sin(j * tha) - std::sin(j * thb)) / (j * pi);
+    out[j] = g * mu;
+  }
+}
+
+int check_slices(int nslice, int nper, int degree, double lo, double hi, const double* cuts) {
+  if (nslice < 1 || nper < 1) return set_error(PW_EINVAL, "nslice and nper must be positive");
+  if (degree < 1) return set_error(PW_EINVAL, "degree must be positive");
+  if (!(hi > lo)) return set_error(PW_EINVAL, "spectrum bounds need hi > lo");
+  if (!cuts) return set_error(PW_EINVAL, "NULL cuts");
+  for (int s = 0; s < nslice; ++s)
+    if (!(cuts[s + 1] > cuts[s])) return set_error(PW_EINVAL, "cuts must be strictly ascending");
+  return PW_OK;
+}
+
+// every slice block of psi (nslice x nper bands) <- its window applied to it, one recurrence
+template <typename T>
+int slice_filter_impl(pw_ctx* ctx, cplx<T>* psi, int64_t ld, int nslice, int nper, int degree, double lo, double hi,
+                      const double* cuts) {
+  const int npw = ctx->npw, nband = nslice * nper;
+  const cudaStream_t st = ctx->stream;
+  std::vector<double> w(degree + 1), coef((size_t)(degree + 1) * nband);
+  for (int s = 0; s < nslice; ++s) {
+    window_coefficients(degree, cuts[s], cuts[s + 1], lo, hi, w.data());
+    for (int k = 0; k <= degree; ++k)
+      for (int j = 0; j < nper; ++j) coef[(size_t)k * nband + s * nper + j] = w[k];
+  }
+  WS(cd, double, WS_SLICEC, coef.size());
+  WS(acc, cplx<T>, WS_SLICEA, (size_t)npw * nband);
+  CU_TRY(cudaMemcpyAsync(cd, coef.data(), sizeof(double) * coef.size(), cudaMemcpyHostToDevice, st), "coefficients");
+  ChebSum<T> cs{acc, npw, cd};
+  PW_TRY(filter_impl<T>(ctx, psi, ld, nband, degree, lo, hi, nullptr, &cs));
+  CU_TRY(cudaMemcpy2DAsync(psi, sizeof(cplx<T>) * ld, acc, sizeof(cplx<T>) * npw, sizeof(cplx<T>) * npw, nband,
+                           cudaMemcpyDeviceToDevice, st), "slice copy-out");
+  CU_TRY(cudaStreamSynchronize(st), "slice sync");  // the host coefficients go out of scope
   return PW_OK;
 }
 
@@ -1505,6 +1735,53 @@ PW_API int pw_rayleigh_ritz(pw_ctx* ctx, void* psi, int64_t ldpsi, int nband, vo
   return rr_impl(ctx, (double2*)psi, ldpsi, nband, (double2*)hpsi, eig, resid);
 }
 
+PW_API int pw_slice_filter(pw_ctx* ctx, void* psi, int64_t ldpsi, int nslice, int nper, int degree, double lo,
+                           double hi, const double* cuts, int precision) {
+  PW_TRY(check_ctx(ctx));
+  PW_TRY(check_slices(nslice, nper, degree, lo, hi, cuts));
+  PW_TRY(check_block(ctx, psi, ldpsi, nslice * nper));
+  if (precision == PW_FP64)
+    return slice_filter_impl<double>(ctx, (double2*)psi, ldpsi, nslice, nper, degree, lo, hi, cuts);
+  if (precision == PW_MIXED)
+    return slice_filter_impl<float>(ctx, (float2*)psi, ldpsi, nslice, nper, degree, lo, hi, cuts);
+  return set_error(PW_EINVAL, "unknown precision");
+}
+
+PW_API int pw_spectrum_slice(pw_ctx* ctx, void* psi_v, int64_t ldpsi, int nslice, int nper, int degree, double lo,
+                             double hi, const double* cuts, int precision, double* eig, double* resid) {
+  PW_TRY(check_ctx(ctx));
+  PW_TRY(check_slices(nslice, nper, degree, lo, hi, cuts));
+  PW_TRY(check_block(ctx, psi_v, ldpsi, nslice * nper));
+  if (!eig) return set_error(PW_EINVAL, "eig is NULL");
+  if (precision != PW_FP64 && precision != PW_MIXED) return set_error(PW_EINVAL, "unknown precision");
+  double2* psi = (double2*)psi_v;
+  const int npw = ctx->npw, nband = nslice * nper;
+  if (precision == PW_FP64) {
+    PW_TRY(slice_filter_impl<double>(ctx, psi, ldpsi, nslice, nper, degree, lo, hi, cuts));
+  } else {
+    WS(y32, float2, WS_Y32, (size_t)npw * nband);
+    CU_TRY(la_to_c64(psi, ldpsi, y32, npw, npw, nband, ctx->stream), "to c64");
+    PW_TRY(slice_filter_impl<float>(ctx, y32, npw, nslice, nper, degree, lo, hi, cuts));
+    CU_TRY(la_to_c128(y32, npw, psi, ldpsi, npw, nband, ctx->stream), "to c128");
+  }
+  // independent small Rayleigh-Ritz steps, one per slice
+  for (int s = 0; s < nslice; ++s)
+    PW_TRY(rr_impl(ctx, psi + (size_t)s * nper * ldpsi, ldpsi, nper, nullptr, eig + (size_t)s * nper,
+                   resid ? resid + (size_t)s * nper : nullptr));
+  return PW_OK;
+}
+
+PW_API int pw_lobpcg_solve(pw_ctx* ctx, void* psi, int64_t ldpsi, int nband, int nblocks, int nline, double tol,
+                           double* eig, double* resid, int* iters) {
+  PW_TRY(check_ctx(ctx));
+  PW_TRY(check_block(ctx, psi, ldpsi, nband));
+  if (nband == 0) return PW_OK;
+  if (!eig) return set_error(PW_EINVAL, "eig is NULL");
+  if (nblocks < 1 || nband % nblocks) return set_error(PW_EINVAL, "nband (%d) must be a multiple of nblocks (%d)", nband, nblocks);
+  if (nline < 0) return set_error(PW_EINVAL, "nline must be non-negative");
+  return lobpcg_impl(ctx, (double2*)psi, ldpsi, nband, nblocks, nline, tol, eig, resid, iters);
+}
+
 PW_API int pw_chebfi_solve(pw_ctx* ctx, void* psi_v, int64_t ldpsi, int nband, int degree, int cycles,
                            int lanczos_steps, const void* v0, int precision, double* eig, double* resid,
                            double* bounds) {
@@ -1515,10 +1792,11 @@ PW_API int pw_chebfi_solve(pw_ctx* ctx, void* psi_v, int64_t ldpsi, int nband, i
   if (precision != PW_FP64 && precision != PW_MIXED) return set_error(PW_EINVAL, "unknown precision");
   double2* psi = (double2*)psi_v;
   double rqmin = 0, a = 0, upper = 0;
-  if (precision == PW_MIXED && !ctx->has_q) {
-    // the cut a is a filter parameter, not a result: the Rayleigh quotients of the starting
-    // block come from the complex64 H-apply (the FP64 apply of a block costs as much as a
-    // filter's worth of mixed steps); the Lanczos bound stays FP64
+  if (precision == PW_MIXED) {
+    // the cut a is a filter parameter, not a result: the numerators of the Rayleigh
+    // quotients of the starting block come from the complex64 H-apply (the FP64 apply of a
+    // block costs as much as a filter's worth of mixed steps), the denominators from the FP64
+    // S-apply (projector GEMMs only); the Lanczos bound stays FP64
     PW_TRY(bounds_impl(ctx, psi, ldpsi, 0, lanczos_steps, (const double2*)v0, nullptr, nullptr, &upper));
     const int npw = ctx->npw;
     const cudaStream_t st = ctx->stream;
@@ -1530,7 +1808,15 @@ PW_API int pw_chebfi_solve(pw_ctx* ctx, void* psi_v, int64_t ldpsi, int nband, i
     PW_TRY(apply_impl<float>(ctx, y32, npw, nband, h32, nullptr, npw));
     CU_TRY(la_to_c128(h32, npw, HY, npw, npw, nband, st), "to c128");
     CU_TRY(la_coldot(psi, ldpsi, HY, npw, npw, nband, rq, st), "rq num");
-    CU_TRY(la_coldot(psi, ldpsi, psi, ldpsi, npw, nband, rq + nband, st), "rq den");
+    const double2* SY = psi;
+    int64_t lds = ldpsi;
+    if (ctx->has_q) {
+      WS(SYb, double2, WS_SY, (size_t)npw * nband);
+      PW_TRY(apply_s64(ctx, psi, ldpsi, nband, SYb, npw));
+      SY = SYb;
+      lds = npw;
+    }
+    CU_TRY(la_coldot(psi, ldpsi, SY, lds, npw, nband, rq + nband, st), "rq den");
     double* mm = (double*)(rq + 2 * nband);
     double* rqv = (double*)(rq + 2 * nband + 1);
     CU_TRY(la_rq_minmax(rq, rq + nband, nband, rqv, mm, st), "rq minmax");
@@ -1641,12 +1927,12 @@ PW_API int pw_autotune(pw_ctx* ctx, int nband, int precision, double* best_ms) {
     return PW_OK;
   };
   // batch size with the current kernel forms, every kernel form at that size (complex64:
-  // x-line form (0-6) + 8 * plane form (0-3)), the batch size again with the forms kept
+  // x-line form + kFormStride * plane form), the batch size again with the forms kept
   for (size_t c : cand) PW_TRY(consider(c, best_v));
   const size_t c1 = best_c;
   if (precision == PW_MIXED) {
-    for (int pf = 0; pf < 4; ++pf)
-      for (int xf = 0; xf < 7; ++xf) PW_TRY(consider(c1, xf + 8 * pf));
+    for (int pf = 0; pf < kPlaneForms; ++pf)
+      for (int xf = 0; xf < kXlineForms; ++xf) PW_TRY(consider(c1, xf + kFormStride * pf));
   }
   const int v1 = best_v;
   for (size_t c : cand) PW_TRY(consider(c, v1));
@@ -1704,7 +1990,7 @@ PW_API int pw_fft_config(pw_ctx* ctx, int precision, int64_t set_batch_bytes, in
                          int* variant) {
   PW_TRY(check_ctx(ctx));
   if (precision != PW_FP64 && precision != PW_MIXED) return set_error(PW_EINVAL, "unknown precision");
-  if (set_variant > 30 || (set_variant >= 0 && set_variant % 8 > 6))
+  if (set_variant >= kFormStride * kPlaneForms || (set_variant >= 0 && set_variant % kFormStride >= kXlineForms))
     return set_error(PW_EINVAL, "unknown FFT kernel variant %d", set_variant);
   const int slot = precision == PW_MIXED ? 0 : 1;
   if (batch_bytes) *batch_bytes = (int64_t)ctx->fft_batch_bytes[slot];

@@ -62,6 +62,9 @@ template <typename C> __host__ __device__ __forceinline__ C czero() { C c; c.x =
 // potential grid is stored permuted instead.
 // ---------------------------------------------------------------------------
 constexpr int kMaxStages = 8;
+// FFT pass-kernel variant = x-line form (0-10) + kFormStride * plane form (0-3)
+constexpr int kFormStride = 16;
+constexpr int kXlineForms = 11, kPlaneForms = 4;
 struct FftDim {
   int n, nst;
   int radix[kMaxStages];
@@ -231,6 +234,16 @@ template <typename T>
 cudaError_t launch_dblock(int nproj, int nband, const T* D, const int* blk0, const int* blklen,
                           const cplx<T>* Cm, int64_t ldc, cplx<T>* Z, int64_t ldz, cudaStream_t st);
 
+// workspace slots of a context (pw_ctx::ws)
+enum WsSlot {
+  WS_HB = 0, WS_C, WS_Z, WS_SPLIT, WS_Y1, WS_Y2, WS_CW,      // H-apply and filter
+  WS_YSPLIT, WS_WSPLIT, WS_ZSPLIT, WS_TCPART, WS_TCERR,      // tensor-core mixed path
+  WS_HY, WS_SY, WS_ROT, WS_Y32,                              // Rayleigh-Ritz / solve
+  WS_GRAM, WS_GRAM2, WS_LINV, WS_TMP, WS_U, WS_JAC, WS_EIG,  // subspace matrices
+  WS_LZ, WS_RQ, WS_DEN, WS_SCAL, WS_VPOT, WS_PZ,
+  WS_OZA, WS_OZB, WS_OZPART, WS_OZAMAX, WS_OZEXP, WS_SCF,
+  WS_LOBZ, WS_LOBT, WS_LOBB, WS_LOBR, WS_LOBD, WS_SLICEC, WS_SLICEA, WS_NUM
+};
 }  // namespace pw
 
 // the context (opaque to C callers)
@@ -292,7 +305,7 @@ struct pw_ctx {
   int64_t prof_n[PW_PROF_NCLASS] = {};
   // grow-only workspaces
   struct Buf { void* p = nullptr; size_t bytes = 0; };
-  Buf ws[40];
+  Buf ws[pw::WS_NUM];
   bool poisoned = false;
   uint64_t ws_gen = 0;  // bumped whenever a workspace is (re)allocated (captured graphs check it)
   // tuning: bytes of half-box planes per FFT band batch (complex64, complex128); set by pw_autotune
@@ -324,14 +337,6 @@ struct pw_ctx {
 };
 
 namespace pw {
-enum WsSlot {
-  WS_HB = 0, WS_C, WS_Z, WS_SPLIT, WS_Y1, WS_Y2, WS_CW,      // H-apply and filter
-  WS_YSPLIT, WS_WSPLIT, WS_ZSPLIT, WS_TCPART, WS_TCERR,      // tensor-core mixed path
-  WS_HY, WS_SY, WS_ROT, WS_Y32,                              // Rayleigh-Ritz / solve
-  WS_GRAM, WS_GRAM2, WS_LINV, WS_TMP, WS_U, WS_JAC, WS_EIG,  // subspace matrices
-  WS_LZ, WS_RQ, WS_DEN, WS_SCAL, WS_VPOT, WS_PZ,
-  WS_OZA, WS_OZB, WS_OZPART, WS_OZAMAX, WS_OZEXP, WS_SCF, WS_NUM
-};
 void* ws_get(pw_ctx* c, int slot, size_t bytes, int* status);
 // process-wide count of kernel launches issued by this library (diagnostics)
 void count_launch();

@@ -31,7 +31,8 @@ EXPORTS = ("pw_ctx_create", "pw_ctx_destroy", "pw_ctx_set_stream", "pw_ctx_info"
            "pw_batch_destroy", "pw_batch_filter", "pw_batch_chebfi_solve", "pw_ctx_set_vloc", "pw_ctx_set_D",
            "pw_local_apply", "pw_diff_create", "pw_diff_destroy", "pw_diff_tape_bytes", "pw_diff_forward",
            "pw_diff_backward", "pw_fft_config", "pw_tc_config", "pw_fp64_config", "pw_ctx_sync",
-           "pw_ctx_test_wait_expiry", "pw_diag_fp64_fma_rate", "pw_scf_potential", "pw_scf_run", "pw_gamma_symmetrize",
+           "pw_ctx_test_wait_expiry", "pw_diag_fp64_fma_rate", "pw_scf_potential", "pw_scf_run", "pw_slice_filter", "pw_spectrum_slice",
+           "pw_lobpcg_solve", "pw_gamma_symmetrize",
            "pw_gamma_pack", "pw_gamma_unpack", "pw_strerror", "pw_last_error")
 
 PROF_CLASSES = ("plane_inv", "xline", "plane_fwd", "gemm_proj", "gemm_back", "small", "rr")
@@ -86,6 +87,9 @@ def load(path: Optional[str] = None):
     lib.pw_ctx_sync.argtypes = [vp]
     lib.pw_diag_fp64_fma_rate.argtypes = [vp, pd, pd]
     lib.pw_scf_potential.argtypes = [vp, vp, vp, vp, cd, vp, pd]
+    lib.pw_slice_filter.argtypes = [vp, vp, i64, ci, ci, ci, cd, cd, pd, ci]
+    lib.pw_spectrum_slice.argtypes = [vp, vp, i64, ci, ci, ci, cd, cd, pd, ci, pd, pd]
+    lib.pw_lobpcg_solve.argtypes = [vp, vp, i64, ci, ci, ci, cd, pd, pd, ctypes.POINTER(ctypes.c_int)]
     lib.pw_gamma_symmetrize.argtypes = [vp, vp, i64, ci, ci]
     lib.pw_gamma_pack.argtypes = [vp, vp, i64, ci, vp, i64, ci]
     lib.pw_gamma_unpack.argtypes = [vp, vp, i64, ci, vp, i64, ci]
@@ -404,6 +408,52 @@ class Context:
         _check(load().pw_density_grad(self._h, ctypes.c_void_p(a.data_ptr()), bp, ld, m, _dptr(w),
                                       ctypes.c_void_p(out.data_ptr()), 1 if accumulate else 0))
         return out
+
+    # -- spectrum slicing ------------------------------------------------------------------
+    def slice_filter(self, psi, nslice, degree, lo, hi, cuts, precision=PW_FP64):
+        """Each of the nslice band blocks of psi through its slice's window, in place."""
+        psi, m, ld = _block(psi, _dtype(precision), "psi")
+        if m % nslice:
+            raise ValueError("the band count must be a multiple of nslice")
+        c = np.ascontiguousarray(cuts, dtype=np.float64)
+        if c.size != nslice + 1:
+            raise ValueError("cuts needs nslice + 1 values")
+        self._sync_stream()
+        _check(load().pw_slice_filter(self._h, ctypes.c_void_p(psi.data_ptr()), ld, int(nslice), m // nslice,
+                                      int(degree), float(lo), float(hi), _dptr(c), precision))
+        return psi
+
+    def spectrum_slice(self, psi, nslice, degree, lo, hi, cuts, precision=PW_FP64):
+        """Window filter + per-slice FP64 Rayleigh-Ritz on psi (complex128, in place); returns
+        the Ritz values and residual norms as (nslice, nper) arrays."""
+        import torch
+        psi, m, ld = _block(psi, torch.complex128, "psi")
+        if m % nslice:
+            raise ValueError("the band count must be a multiple of nslice")
+        c = np.ascontiguousarray(cuts, dtype=np.float64)
+        if c.size != nslice + 1:
+            raise ValueError("cuts needs nslice + 1 values")
+        eig = np.zeros(m)
+        res = np.zeros(m)
+        self._sync_stream()
+        _check(load().pw_spectrum_slice(self._h, ctypes.c_void_p(psi.data_ptr()), ld, int(nslice), m // nslice,
+                                        int(degree), float(lo), float(hi), _dptr(c), precision, _dptr(eig),
+                                        _dptr(res)))
+        return eig.reshape(nslice, -1), res.reshape(nslice, -1)
+
+    # -- LOBPCG (Alg. 11) -----------------------------------------------------------------
+    def lobpcg_solve(self, psi, nblocks, nline, tol=0.0):
+        """FP64 LOBPCG in place on psi (complex128); returns (eig, resid, line minimisations
+        per block)."""
+        import torch
+        psi, m, ld = _block(psi, torch.complex128, "psi")
+        eig = np.zeros(m)
+        res = np.zeros(m)
+        its = (ctypes.c_int * max(int(nblocks), 1))()
+        self._sync_stream()
+        _check(load().pw_lobpcg_solve(self._h, ctypes.c_void_p(psi.data_ptr()), ld, m, int(nblocks), int(nline),
+                                      float(tol), _dptr(eig), _dptr(res), its))
+        return eig, res, list(its)[:int(nblocks)]
 
     # -- Gamma-point pairing -------------------------------------------------------------
     def gamma_symmetrize(self, psi, precision=PW_FP64):

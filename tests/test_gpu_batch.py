@@ -29,10 +29,10 @@ def contexts(prob, ecuts, variant=None):
     return ctxs
 
 
-# variant 19 on a 24^3 box: warp-group FFT kernels with the recurrence fused into pass 3
+# variant 35 on a 24^3 box: warp-group FFT kernels with the recurrence fused into pass 3
 @pytest.mark.parametrize("precision,variant,box", [(pwlib.PW_FP64, None, (24, 24, 30)),
                                                    (pwlib.PW_MIXED, None, (24, 24, 30)),
-                                                   (pwlib.PW_MIXED, 19, (24, 24, 24))])
+                                                   (pwlib.PW_MIXED, 35, (24, 24, 24))])
 def test_batch_filter_equals_per_k_filter(precision, variant, box):
     prob = problem(box)
     ecuts = W.ecut_jitter(prob.seed, len(KPTS), prob.ecut)
