@@ -15,7 +15,9 @@ when the timed region starts; L2 is flushed (256 MB write) between steps.  The b
 k-point form (32 k-points, one captured graph per filter) is measured after it in the same
 run and reported under "batched_kpoints" (skip with --no-batched), and the Gamma-point pairing
 of the same bands made real in r-space (M/2 packed complex bands per filter) under
-"gamma_paired" (skip with --no-gamma).
+"gamma_paired" (skip with --no-gamma); the paper's solver comparison (one ChebFi cycle
+against FP64 LOBPCG, 4 blocks x 4 line minimisations) and the spectrum-slicing form (8
+windows, degree 60) under "solvers" (skip with --no-solvers).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -59,6 +61,7 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-gamma", action="store_true")
+    ap.add_argument("--no-solvers", action="store_true", help="skip the LOBPCG and spectrum-slicing measurements")
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--tc-pieces", type=int, default=2,
                     help="bf16 pieces of the mixed GEMM operands: 2 (3 products) or 3 (6 products)")
@@ -430,6 +433,51 @@ def run_ours(args):
         e2e_val = weak_value(world, M * (m + 1), t_e2e)
     bytes_psi = psi0.nbytes
 
+    # the paper's comparison (Table 3 form): one ChebFi cycle (the e2e call above) against
+    # FP64 LOBPCG with 4 blocks and 4 line minimisations, on the same starting block; and the
+    # spectrum-slicing form (8 windows of M/8 bands, degree 60, complex64 window filter)
+    solvers = None
+    if world == 1 and not args.no_solvers and e2e_t:
+        Yl = torch.from_numpy(psi0).cuda()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        eig_l, res_l, its_l = ctx.lobpcg_solve(Yl, 4, 4)
+        torch.cuda.synchronize()
+        t_l = time.perf_counter() - t0
+        applies_l = M + M * sum(its_l)            # Rayleigh-quotient initialisation + one per line
+        del Yl
+        nsl, deg_s = 8, 60
+        # below the spectrum: the lowest Ritz value of the ChebFi cycle less 5% of the width
+        lo_s = float(eig_e[0]) - 0.05 * (b - float(eig_e[0]))
+        cuts = np.linspace(lo_s, float(eig_e[-1]), nsl + 1)
+        Ys = torch.from_numpy(psi0).cuda()
+        Y32s = Ys.to(torch.complex64)
+        ctx.slice_filter(Y32s.clone(), nsl, 4, lo_s, b, cuts, precision=pwlib.PW_MIXED)   # warm-up
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        ctx.slice_filter(Y32s, nsl, deg_s, lo_s, b, cuts, precision=pwlib.PW_MIXED)
+        e1.record(st)
+        torch.cuda.synchronize()
+        t_sf = e0.elapsed_time(e1) / 1e3
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        eig_s, res_s = ctx.spectrum_slice(Ys, nsl, deg_s, lo_s, b, cuts, precision=pwlib.PW_MIXED)
+        torch.cuda.synchronize()
+        t_ss = time.perf_counter() - t0
+        inside = sum(int(np.sum((eig_s[i] > cuts[i]) & (eig_s[i] < cuts[i + 1]))) for i in range(nsl))
+        del Ys, Y32s
+        solvers = {
+            "chebfi_cycle": {"seconds": float(t_e2e), "degree": m, "max_resid": float(np.max(res_e)),
+                             "precision": "mixed filter, FP64 Rayleigh-Ritz", "band_applies": M * (m + 1)},
+            "lobpcg": {"seconds": t_l, "blocks": 4, "nline": 4, "line_minimisations": its_l,
+                       "max_resid": float(np.max(res_l)), "precision": "FP64", "band_applies": applies_l,
+                       "band_applies_per_s": applies_l / t_l,
+                       "eig_max_diff_vs_chebfi": float(np.max(np.abs(eig_l - eig_e)))},
+            "spectrum_slicing": {"slices": nsl, "bands_per_slice": M // nsl, "degree": deg_s,
+                                 "window_filter_ms": 1e3 * t_sf, "value": M * deg_s / t_sf, "unit": UNIT,
+                                 "solve_seconds": t_ss, "ritz_values_inside_their_slice": inside,
+                                 "precision": "complex64 window filter, FP64 per-slice Rayleigh-Ritz"}}
+
     # roofline of the dominant kernel class of the filter, and of every class
     hbm, bf16, smmax, src = peaks()
     filt_classes = ("plane_inv", "xline", "plane_fwd", "gemm_proj", "gemm_back", "small")
@@ -527,7 +575,8 @@ def run_ours(args):
               "cpu_baseline": cpu, "clocks": clk, "gpu_launches": int(launches),
               "kernels_ms_per_step": {k: v[0] / args.steps for k, v in prof.items()},
               "kernel_launches_per_step": {k: v[1] / args.steps for k, v in prof.items()},
-              "fp64_fma_peak": fp64_peak, "gamma_paired": gamma, "batched_kpoints": batched})
+              "fp64_fma_peak": fp64_peak, "gamma_paired": gamma, "solvers": solvers,
+              "batched_kpoints": batched})
     if dist is not None:
         dist.barrier()
         dist.destroy_process_group()
