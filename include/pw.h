@@ -145,7 +145,9 @@ PW_API int pw_spectrum_bounds(pw_ctx* ctx, const void* psi, int64_t ld, int nban
  * c = (b+a)/2, e = (b-a)/2, Y_0 = psi, Y_1 = (A-c)Y_0/e,
  * Y_{k+1} = (2/e)(A-c)Y_k - Y_{k-1}, A = S^-1 H (Woodbury, Sec. 3.3) or H.
  * psi is overwritten with Y_m.  PW_FP64: complex128 block; PW_MIXED:
- * complex64 block, FP32 FFTs and BF16-split tensor-core projector GEMMs. */
+ * complex64 block, FP32 FFTs and BF16-split tensor-core projector GEMMs.  With Q a step
+ * projects only W = (T + V) Y_k onto the projectors; P^dagger Y_k follows the same
+ * recurrence in projector space through the stored P^dagger P. */
 PW_API int pw_chebyshev_filter(pw_ctx* ctx, void* psi, int64_t ldpsi, int nband,
                                int degree, double a, double b, int precision);
 
@@ -396,9 +398,8 @@ enum pw_prof_class {
  * the best time of one apply. */
 PW_API int pw_autotune(pw_ctx* ctx, int nband, int precision, double* best_ms);
 /* (pw_autotune, PW_MIXED, continued) It then times the K-split counts of the projection
- * GEMM C = P^dagger Y around the whole-waves rule for nband columns (and 2 nband with Q, where
- * the projections of Y and of (T + V) Y run as one GEMM) and keeps the fastest per column
- * count; other column counts use the rule. */
+ * GEMM C = P^dagger Y around the whole-waves rule for nband columns and keeps the fastest;
+ * other column counts use the rule. */
 /* Reads (*batch_bytes, *variant; either pointer may be NULL) and then, for arguments
  * >= 0, sets the FFT configuration of `precision`: bytes of half-box planes per band
  * batch (>= 1 band is always used) and the pass-kernel forms (as for

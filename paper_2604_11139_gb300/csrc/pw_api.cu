@@ -226,6 +226,7 @@ template <> struct Prec<double> {
   static const double2* tw(const pw_ctx* c) { return c->tw64; }
   static const double2* K(const pw_ctx* c) { return c->K64; }
   static const double2* E(const pw_ctx* c) { return c->E64; }
+  static const double2* B(const pw_ctx* c) { return c->B64; }
 };
 template <> struct Prec<float> {
   static const float2* P(const pw_ctx* c) { return c->P32; }
@@ -235,6 +236,7 @@ template <> struct Prec<float> {
   static const float2* tw(const pw_ctx* c) { return c->tw32; }
   static const float2* K(const pw_ctx* c) { return c->K32; }
   static const float2* E(const pw_ctx* c) { return c->E32; }
+  static const float2* B(const pw_ctx* c) { return c->B32; }
 };
 
 template <typename T>
@@ -576,13 +578,18 @@ int filter_impl(pw_ctx* ctx, cplx<T>* psi, int64_t ldpsi, int nband, int degree,
   const int bb = band_batch(ctx, nband, sizeof(C));
   const int64_t hb_bs = (int64_t)ctx->sp.nplane * ctx->n[1] * ctx->n[2];
   WS(hb, C, WS_HB, hb_bs * bb);
-  constexpr bool kMixedQ = std::is_same<T, float>::value;
-  // complex64 with Q: C_proj = P^dagger Y_k and C_w = P^dagger W side by side (one GEMM)
-  const bool joint = kMixedQ && ctx->has_q;
-  WS(Cm, C, WS_C, (size_t)np * nband * (joint ? 2 : 1));
-  WS(Z, C, WS_Z, (size_t)np * nband);
-  WS(Cwb, C, WS_CW, (size_t)np * nband);
-  C* Cw = joint ? Cm + (size_t)np * nband : Cwb;
+  // With Q the step needs C_k = P^dagger Y_k and C_w = P^dagger W, W = (T + V) Y_k.  Only C_w
+  // is a projection of the block: C_k follows the filter's recurrence in projector space,
+  // P^dagger Y_{k+1} = alpha (C_w + (P^dagger P) Z - c C_k) - beta C_{k-1} (Z the step's
+  // projector-space coefficients, Y_{k+1} = alpha (W + P Z - c Y_k) - beta Y_{k-1}), from the
+  // stored P^dagger P: one N x N_p projection per step instead of two, the other an N_p x N_p
+  // product.  C_0 is projected once.  Without Q, C_k itself is the one projection per step.
+  const bool shadow = ctx->has_q && np > 0;
+  const size_t pcol = (size_t)np * nband;
+  WS(Cm, C, WS_C, pcol * (shadow ? 4 : 1));  // with Q: C_{k-1}, C_k, C_{k+1} rotating, then C_w
+  WS(Z, C, WS_Z, pcol);
+  C* Cw = shadow ? Cm + 3 * pcol : nullptr;
+  auto Crot = [&](int j) { return Cm + (size_t)(((j % 3) + 3) % 3) * pcol; };
   const int ns = nsplit_for(np, nband, npw);
   WS(spl, C, WS_SPLIT, (size_t)ns * np * nband);
   WS(Y1, C, WS_Y1, (size_t)npw * nband);
@@ -592,19 +599,40 @@ int filter_impl(pw_ctx* ctx, cplx<T>* psi, int64_t ldpsi, int nband, int degree,
   const double cc = 0.5 * (b + a), e = 0.5 * (b - a);
   constexpr bool kMixed = std::is_same<T, float>::value;
   __nv_bfloat16* ys = nullptr;
-  // with Q the projections of Y_k and of W = (T + V) Y_k run as one GEMM over 2 nband
-  // columns: the bf16 pieces hold Y_k in rows [0, nband) and W in rows [nband, 2 nband), so P's
-  // pieces are streamed once per step
-  const int ycols = (kMixed && ctx->has_q) ? 2 * nband : nband;
   int64_t ys_ps = 0;  // piece stride of the bf16 pieces; kp1 is known once the operands of P exist
   if (kMixed && np > 0) {
     PW_TRY(ensure_tc(ctx));
-    ys_ps = (int64_t)ycols * ctx->kp1;
+    ys_ps = (int64_t)nband * ctx->kp1;
     ProfScope ps(ctx, PW_PROF_GEMM_PROJ);
     WS(ysb, __nv_bfloat16, WS_YSPLIT, (size_t)ctx->tc_pieces * ys_ps);
     ys = ysb;
     PW_TRY(tc_split_into(ctx, (const float2*)psi, ldpsi, npw, nband, ctx->kp1, ys_ps, ys));
+    if (shadow) PW_TRY(tc_project(ctx, ys, nband, (float2*)Crot(0)));  // C_0 = P^dagger Y_0
+  } else if (shadow) {
+    ProfScope ps(ctx, PW_PROF_GEMM_PROJ);
+    PW_TRY(cg<T>(ctx, 1, 0, np, nband, npw, Prec<T>::P(ctx), npw, psi, ldpsi, epi<T>(EPI_STORE, Crot(0), np), ns, spl,
+                 st, GEMM_FULL, "filter projection of Y_0"));
   }
+  // C_{k+1} = alpha (C_w + (P^dagger P) Z - c C_k) - beta C_{k-1}, the recurrence of the step
+  // in projector space (with Q; not needed after the last step)
+  auto shadow_step = [&](int k) -> int {
+    if (!shadow || k + 1 >= degree) return PW_OK;
+    ProfScope ps(ctx, PW_PROF_SMALL);
+    C* next = Crot(k + 1);
+    CU_TRY(cudaMemcpyAsync(next, Cw, sizeof(C) * pcol, cudaMemcpyDeviceToDevice, st), "C_w copy");
+    Epi<T> ce = epi<T>(EPI_CHEB, next, np, (T)(k == 0 ? 1.0 / e : 2.0 / e));
+    ce.beta = (T)1;
+    ce.shift = (T)cc;
+    ce.yk = Crot(k);
+    ce.ldy = np;
+    ce.ykm1 = (k == 0) ? nullptr : Crot(k - 1);
+    ce.ldy2 = np;
+    ce.dev_ce = dev_ce;
+    ce.first = (k == 0);
+    PW_TRY(cg<T>(ctx, 0, 0, np, nband, np, Prec<T>::B(ctx), np, Z, np, ce, 1, spl, st, GEMM_FULL,
+                 "projector-space recurrence"));
+    return PW_OK;
+  };
   // complex64 with S = I and the warp-group plane kernels: the nonlocal term first
   // (projection, D, back-projection into PZ), then the FFT passes with the recurrence and
   // the bf16 split of Y_{k+1} fused into pass 3 (fewer block reads than the recurrence in
@@ -673,10 +701,9 @@ int filter_impl(pw_ctx* ctx, cplx<T>* psi, int64_t ldpsi, int nband, int degree,
     if (kMixed && np > 0) {
       {
         ProfScope ps(ctx, PW_PROF_GEMM_PROJ);
-        if (ctx->has_q) {
-          PW_TRY(tc_split_into(ctx, (const float2*)dst, ldd, npw, nband, ctx->kp1, ys_ps,
-                               ys + (int64_t)nband * ctx->kp1));
-          PW_TRY(tc_project(ctx, ys, 2 * nband, (float2*)Cm));  // [P^dagger Y_k, P^dagger W]
+        if (shadow) {
+          PW_TRY(tc_split_into(ctx, (const float2*)dst, ldd, npw, nband, ctx->kp1, ys_ps, ys));
+          PW_TRY(tc_project(ctx, ys, nband, (float2*)Cw));  // P^dagger W; C_k from the recurrence
         } else {
           PW_TRY(tc_project(ctx, ys, nband, (float2*)Cm));
         }
@@ -687,11 +714,12 @@ int filter_impl(pw_ctx* ctx, cplx<T>* psi, int64_t ldpsi, int nband, int degree,
         if (!ctx->has_q) {
           CU_TRY(launch_dblock<T>(np, nband, Prec<T>::D(ctx), ctx->blk0, ctx->blklen, Cm, np, Z, np, st), "filter D");
         } else {
-          PW_TRY(cg<T>(ctx, 0, 0, np, nband, np, Prec<T>::E(ctx), np, Cm, np, epi<T>(EPI_STORE, Z, np), 1, spl, st, GEMM_FULL, "filter E C"));
+          PW_TRY(cg<T>(ctx, 0, 0, np, nband, np, Prec<T>::E(ctx), np, Crot(k), np, epi<T>(EPI_STORE, Z, np), 1, spl, st, GEMM_FULL, "filter E C"));
           PW_TRY(cg<T>(ctx, 0, 0, np, nband, np, Prec<T>::K(ctx), np, Cw, np, epi<T>(EPI_ACCUM, Z, np, (T)-1), 1, spl, st, GEMM_FULL, "filter K Cw"));
         }
         PW_TRY(tc_split(ctx, (const float2*)Z, np, np, nband, ctx->kp2, WS_ZSPLIT, &zs));
       }
+      PW_TRY(shadow_step(k));
       ProfScope ps(ctx, PW_PROF_GEMM_BACK);
       tc::TcEpi te{};
       te.mode = tc::TC_EPI_CHEB;
@@ -709,7 +737,8 @@ int filter_impl(pw_ctx* ctx, cplx<T>* psi, int64_t ldpsi, int nband, int degree,
       te.split = ys;
       te.split_ld = ctx->kp1;
       te.split_piece_stride = ys_ps;
-      te.out_pieces = (k + 1 < degree) ? ctx->tc_pieces : 0;
+      // the next projection needs the pieces of Y_{k+1} only without Q (with Q it projects W)
+      te.out_pieces = (!shadow && k + 1 < degree) ? ctx->tc_pieces : 0;
       PW_TRY(tc_backproject(ctx, zs, nband, te));
       PW_TRY(add_term(dst, ldd, k + 1));
       continue;
@@ -726,9 +755,10 @@ int filter_impl(pw_ctx* ctx, cplx<T>* psi, int64_t ldpsi, int nband, int degree,
     if (np > 0) {
       {
         ProfScope ps(ctx, PW_PROF_GEMM_PROJ);
-        // C = P^dagger Y_k
-        PW_TRY(cg<T>(ctx, 1, 0, np, nband, npw, Prec<T>::P(ctx), npw, cur, ldc, epi<T>(EPI_STORE, Cm, np), ns, spl, st, GEMM_FULL, "filter projection"));
-        if (ctx->has_q)
+        // C = P^dagger Y_k (without Q), C_w = P^dagger W (with Q; C_k from the recurrence)
+        if (!shadow)
+          PW_TRY(cg<T>(ctx, 1, 0, np, nband, npw, Prec<T>::P(ctx), npw, cur, ldc, epi<T>(EPI_STORE, Cm, np), ns, spl, st, GEMM_FULL, "filter projection"));
+        else
           PW_TRY(cg<T>(ctx, 1, 0, np, nband, npw, Prec<T>::P(ctx), npw, dst, ldd, epi<T>(EPI_STORE, Cw, np), ns, spl, st, GEMM_FULL, "filter projection of W"));
       }
       {
@@ -737,10 +767,11 @@ int filter_impl(pw_ctx* ctx, cplx<T>* psi, int64_t ldpsi, int nband, int degree,
           CU_TRY(launch_dblock<T>(np, nband, Prec<T>::D(ctx), ctx->blk0, ctx->blklen, Cm, np, Z, np, st), "filter D");
         } else {
           // S^-1 H Y = W + P [E C - K P^dagger W],  E = (I - K P^dagger P) D  (Woodbury, Sec. 3.3)
-          PW_TRY(cg<T>(ctx, 0, 0, np, nband, np, Prec<T>::E(ctx), np, Cm, np, epi<T>(EPI_STORE, Z, np), 1, spl, st, GEMM_FULL, "filter E C"));
+          PW_TRY(cg<T>(ctx, 0, 0, np, nband, np, Prec<T>::E(ctx), np, Crot(k), np, epi<T>(EPI_STORE, Z, np), 1, spl, st, GEMM_FULL, "filter E C"));
           PW_TRY(cg<T>(ctx, 0, 0, np, nband, np, Prec<T>::K(ctx), np, Cw, np, epi<T>(EPI_ACCUM, Z, np, (T)-1), 1, spl, st, GEMM_FULL, "filter K Cw"));
         }
       }
+      PW_TRY(shadow_step(k));
       ProfScope ps(ctx, PW_PROF_GEMM_BACK);
       PW_TRY(cg<T>(ctx, 0, 0, npw, nband, np, Prec<T>::P(ctx), npw, Z, np, ce, 1, spl, st, GEMM_FULL, "filter recurrence"));
     } else {
@@ -1456,6 +1487,10 @@ int create_impl(const pw_problem_desc* d, void* stream, pw_ctx** out) {
                                 1, nullptr, st), "E");
     CU_TRY(cast_z2c(ctx->K64, ctx->K32, (int64_t)nn, st), "K cast");
     CU_TRY(cast_z2c(ctx->E64, ctx->E32, (int64_t)nn, st), "E cast");
+    // P^dagger P stays: the filter's projector-space recurrence uses it
+    ctx->B64 = Bm;
+    PW_TRY(upload(ctx, &ctx->B32, (const float2*)nullptr, nn));
+    CU_TRY(cast_z2c(ctx->B64, ctx->B32, (int64_t)nn, st), "P^dagger P cast");
     PW_TRY(check_flag(ctx, flag, "Woodbury set-up (Q or Q^-1 + P^dagger P)"));
   }
   CU_TRY(cudaStreamSynchronize(st), "context set-up");
@@ -1940,10 +1975,10 @@ PW_API int pw_autotune(pw_ctx* ctx, int nband, int precision, double* best_ms) {
   ctx->fft_variant[slot] = best_v;
   if (best_ms) *best_ms = best;
   // mixed projection GEMM: time the K splits around the whole-waves rule for the column
-  // counts the filter uses (nband, and 2 nband for the joint projection with Q)
+  // count the filter uses (nband: P^dagger Y_k without Q, P^dagger W with Q)
   if (precision == PW_MIXED && ctx->nproj > 0) {
     PW_TRY(ensure_tc(ctx));
-    const int ncols[2] = {nband, ctx->has_q ? 2 * nband : 0};
+    const int ncols[2] = {nband, 0};
     for (int cols : ncols) {
       if (cols <= 0) continue;
       __nv_bfloat16* ysp;

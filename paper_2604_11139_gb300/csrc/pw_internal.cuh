@@ -286,6 +286,8 @@ struct pw_ctx {
   double2* E64 = nullptr;   // E = (I - K P^dagger P) D
   float2* K32 = nullptr;
   float2* E32 = nullptr;
+  double2* B64 = nullptr;   // P^dagger P (with Q: the filter's projector-space recurrence)
+  float2* B32 = nullptr;
   // tensor-core operands of the mixed path: bf16 pieces of the real-ified P (built on first use)
   int tc_pieces = 3;         // bf16 pieces per operand (2: 3 products, 3: 6 products)
   int tc_built_pieces = 0;   // pieces the operands below were built with (0 = not built)
