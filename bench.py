@@ -493,17 +493,17 @@ def run_ours(args):
     # pass 3 carries the recurrence (reads P Z and Y_{k-1}, writes the bf16 pieces of Y_{k+1})
     # when the warp-group plane kernels run without Q
     fused = (fft_cfg[1] // 16 in (2, 3)) and prob.Q is None
-    # GEMM launches per filter step: the projection of Y_k (and, with Q, of W = (T + V) Y_k for
-    # the Woodbury correction), one back-projection; the class times also hold the bf16 splits
-    # of the operands and the split-K sums of the projection
-    nproj_gemms = 2 if prob.Q is not None else 1
+    # projector GEMMs of M columns per filter: without Q the projection of Y_k at every step;
+    # with Q the projection of W = (T + V) Y_k at every step plus that of Y_0 (P^dagger Y_k
+    # follows the recurrence in projector space); one back-projection per step.  The class
+    # times also hold the bf16 splits of the operands and the split-K sums of the projection
     alg = {"plane_inv": ("hbm", nb_avg * (npw + half) * c8),
            "xline": ("hbm", nb_avg * 2 * half * c8 + box[0] * box[1] * box[2] * 4),
            "plane_fwd": ("hbm", nb_avg * ((half + (4 if fused else 2) * npw) * c8 + (4 * pieces * npw if fused else 0))),
            # bf16 products of one projector GEMM call over all bands: 2 (2 Np)(2 N) M per product
            "gemm_proj": ("tensor", 2.0 * (2 * nproj) * (2 * npw) * M * (3 if pieces == 2 else 6)),
            "gemm_back": ("tensor", 2.0 * (2 * nproj) * (2 * npw) * M * (3 if pieces == 2 else 6))}
-    gemm_launches = {"gemm_proj": args.steps * m * nproj_gemms, "gemm_back": args.steps * m}
+    gemm_launches = {"gemm_proj": args.steps * (m + (1 if prob.Q is not None else 0)), "gemm_back": args.steps * m}
     per_class = {}
     for cname, (bnd, units) in alg.items():
         ms_c, n_c = prof[cname]

@@ -393,6 +393,7 @@ enum pw_prof_class {
  * b is transformed).  Plane forms: 0 line groups, 1 one thread per line, 2 groups of warps per 32
  * lines with table twiddles over the whole plane in shared memory, 3 the same over the
  * plane's sphere rows and 32-column slices (less shared memory per CTA on large boxes).
+ * PW_FP64 tunes the plane form only (0 or 3, variant 0 or 48; its x-line form is fixed).
  * Forms other than 0 cover box lengths with two-stage radix plans.  Keeps the fastest for
  * `precision` in the context.  Synchronises the stream; *best_ms (may be NULL) receives
  * the best time of one apply. */

@@ -2596,9 +2596,12 @@ static cudaError_t plane_rs_pair(int which, const cplx<T>* psi, int64_t ldpsi, c
                                  const SphereDev& sp, const FftPlan& plan, const cplx<T>* tw, const T* kin,
                                  cplx<T>* out, int64_t ldout, int nb, cudaStream_t st, const Pass3Rec* rec) {
   using PR = PlaneR<N2, N3, TW>;
-  if constexpr (!PR::ok || !std::is_same<T, float>::value) {
+  constexpr bool kF32 = std::is_same<T, float>::value;
+  if constexpr (!PR::ok) {
     return cudaErrorNotSupported;
   } else {
+    // complex128 planes take twice the shared memory (174 KB on 120^3) and no fused recurrence
+    if (!kF32 && rec) return cudaErrorNotSupported;
     const size_t sm = plane_rs_smem<T, N2, N3, TW>(sp);
     if (sm > 227 * 1024) return cudaErrorNotSupported;
     cudaError_t e;
@@ -2609,11 +2612,13 @@ static cudaError_t plane_rs_pair(int which, const cplx<T>* psi, int64_t ldpsi, c
         return e;
       k_plane_inv_rs<T, N2, N3, TW><<<grid, PR::THREADS, sm, st>>>(psi, ldpsi, hb, hb_bs, sp, plan, tw); count_launch();
     } else if (rec) {
-      if ((e = cudaFuncSetAttribute(k_plane_fwd_rs<T, N2, N3, TW, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)sm)))
-        return e;
-      k_plane_fwd_rs<T, N2, N3, TW, true><<<grid, PR::THREADS, sm, st>>>(hb, hb_bs, sp, plan, tw, kin, psi, ldpsi,
-                                                                        out, ldout, *rec); count_launch();
+      if constexpr (kF32) {
+        if ((e = cudaFuncSetAttribute(k_plane_fwd_rs<T, N2, N3, TW, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)sm)))
+          return e;
+        k_plane_fwd_rs<T, N2, N3, TW, true><<<grid, PR::THREADS, sm, st>>>(hb, hb_bs, sp, plan, tw, kin, psi, ldpsi,
+                                                                          out, ldout, *rec); count_launch();
+      }
     } else {
       if ((e = cudaFuncSetAttribute(k_plane_fwd_rs<T, N2, N3, TW, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     (int)sm)))
@@ -2773,8 +2778,10 @@ cudaError_t launch_local_apply(const FftPlan& plan, const cplx<T>* tw, const Sph
   // multi-band forms double-buffered), plane form = variant / 16 (0 line groups, 1 one thread
   // per line, 2 warp groups over the whole plane, 3 warp groups over sphere rows and 32-column
   // slices)
-  const int fv = (std::is_same<T, float>::value && prof) ? prof->fft_variant[0] : 0;
-  int xf = fv % kFormStride;
+  // complex128: only the plane form is selectable (0 line groups, 3 sphere rows + column
+  // slices); the x-line pass keeps the line-group form
+  const int fv = prof ? prof->fft_variant[std::is_same<T, float>::value ? 0 : 1] : 0;
+  int xf = std::is_same<T, float>::value ? fv % kFormStride : 0;
   const int pf = fv / kFormStride;
   // the swapped-radix x-line forms need V permuted for that order: the context's potential
   // has such a copy, an arbitrary potential (pw_local_apply) takes the unswapped form; the
@@ -2794,8 +2801,8 @@ cudaError_t launch_local_apply(const FftPlan& plan, const cplx<T>* tw, const Sph
     if constexpr (std::is_same<T, float>::value) {
       if (tpl) e = plane_tpl<T>(0, psi + b0 * ldpsi, ldpsi, hb, hb_bs, sp, plan, kin, nullptr, 0, nb, st);
       if (pwg) e = plane_wg<T>(0, psi + b0 * ldpsi, ldpsi, hb, hb_bs, sp, plan, tw, kin, nullptr, 0, nb, st);
-      if (prs) e = plane_rs<T>(0, psi + b0 * ldpsi, ldpsi, hb, hb_bs, sp, plan, tw, kin, nullptr, 0, nb, st);
     }
+    if (prs) e = plane_rs<T>(0, psi + b0 * ldpsi, ldpsi, hb, hb_bs, sp, plan, tw, kin, nullptr, 0, nb, st);
     if (e == cudaErrorNotSupported) {
       (void)cudaGetLastError();
       e = plane_lg<T>(0, psi + b0 * ldpsi, ldpsi, hb, hb_bs, sp, plan, tw, kin, nullptr, 0, nb, st);
@@ -2836,9 +2843,9 @@ cudaError_t launch_local_apply(const FftPlan& plan, const cplx<T>* tw, const Sph
       if (tpl) e = plane_tpl<T>(1, psi + b0 * ldpsi, ldpsi, hb, hb_bs, sp, plan, kin, out + b0 * ldout, ldout, nb, st);
       if (pwg)
         e = plane_wg<T>(1, psi + b0 * ldpsi, ldpsi, hb, hb_bs, sp, plan, tw, kin, out + b0 * ldout, ldout, nb, st);
-      if (prs)
-        e = plane_rs<T>(1, psi + b0 * ldpsi, ldpsi, hb, hb_bs, sp, plan, tw, kin, out + b0 * ldout, ldout, nb, st);
     }
+    if (prs)
+      e = plane_rs<T>(1, psi + b0 * ldpsi, ldpsi, hb, hb_bs, sp, plan, tw, kin, out + b0 * ldout, ldout, nb, st);
     if (e == cudaErrorNotSupported) {
       (void)cudaGetLastError();
       e = plane_lg<T>(1, psi + b0 * ldpsi, ldpsi, hb, hb_bs, sp, plan, tw, kin, out + b0 * ldout, ldout, nb, st);

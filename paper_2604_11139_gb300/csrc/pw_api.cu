@@ -1968,6 +1968,10 @@ PW_API int pw_autotune(pw_ctx* ctx, int nband, int precision, double* best_ms) {
   if (precision == PW_MIXED) {
     for (int pf = 0; pf < kPlaneForms; ++pf)
       for (int xf = 0; xf < kXlineForms; ++xf) PW_TRY(consider(c1, xf + kFormStride * pf));
+  } else {
+    // complex128: line-group planes or sphere rows + column slices (x-line form fixed)
+    PW_TRY(consider(c1, 0));
+    PW_TRY(consider(c1, 3 * kFormStride));
   }
   const int v1 = best_v;
   for (size_t c : cand) PW_TRY(consider(c, v1));
@@ -2025,9 +2029,11 @@ PW_API int pw_fft_config(pw_ctx* ctx, int precision, int64_t set_batch_bytes, in
                          int* variant) {
   PW_TRY(check_ctx(ctx));
   if (precision != PW_FP64 && precision != PW_MIXED) return set_error(PW_EINVAL, "unknown precision");
-  if (set_variant >= kFormStride * kPlaneForms || (set_variant >= 0 && set_variant % kFormStride >= kXlineForms))
-    return set_error(PW_EINVAL, "unknown FFT kernel variant %d", set_variant);
   const int slot = precision == PW_MIXED ? 0 : 1;
+  // complex128 has plane forms 0 and 3 only
+  if (set_variant >= kFormStride * kPlaneForms || (set_variant >= 0 && set_variant % kFormStride >= kXlineForms) ||
+      (slot == 1 && set_variant > 0 && set_variant != 3 * kFormStride))
+    return set_error(PW_EINVAL, "unknown FFT kernel variant %d", set_variant);
   if (batch_bytes) *batch_bytes = (int64_t)ctx->fft_batch_bytes[slot];
   if (variant) *variant = ctx->fft_variant[slot];
   if (set_batch_bytes >= 0) ctx->fft_batch_bytes[slot] = (size_t)set_batch_bytes;

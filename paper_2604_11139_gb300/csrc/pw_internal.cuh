@@ -319,7 +319,10 @@ struct pw_ctx {
   // 4 as 3 with several bands per CTA (V kept in registers); plane forms: 0 line groups,
   // 1 one thread per line, 2 groups of warps per 32 lines with table twiddles.  Forms other
   // than 0 cover two-stage plans in complex64 only (otherwise form 0 runs); set by pw_autotune
-  int fft_variant[2] = {0, 0};
+  // FFT pass-kernel forms (complex64, complex128): complex128 defaults to the sphere-row +
+  // column-slice plane kernels (plane form 3), which fall back to line groups where they do
+  // not apply (1.2x the line-group form on the 120^3 box)
+  int fft_variant[2] = {0, 3 * pw::kFormStride};
   int last_sweeps = 0;  // Jacobi sweeps of the last Rayleigh-Ritz step
   // K splits of the mixed projection GEMM per column count, chosen by pw_autotune (columns ->
   // splits); other column counts use the whole-waves rule

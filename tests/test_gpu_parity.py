@@ -276,6 +276,12 @@ def test_full_size_fp64_at_scale_sampled_bands():
         torch.cuda.synchronize()
         ref = ham.apply_h(psi)
         assert rel(h.cpu().numpy()[:, :ctx.npw], ref).max() < 1e-11
+        ctx.fft_config(pwlib.PW_FP64, variant=48)   # complex128 row-slice plane kernels
+        h.zero_()
+        ctx.hamiltonian_apply(t, h)
+        torch.cuda.synchronize()
+        assert rel(h.cpu().numpy()[:, :ctx.npw], ref).max() < 1e-11
+        ctx.fft_config(pwlib.PW_FP64, variant=0)
         for variant in (0, 1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 16, 19, 32, 35, 36, 38, 39, 40, 41, 42, 48, 51, 52, 54, 55, 58):
             ctx.fft_config(pwlib.PW_MIXED, variant=variant)
             t32 = to_dev(psi, torch.complex64)
@@ -317,6 +323,12 @@ def test_full_size_other_boxes_sampled_bands(key):
         err = rel(h.cpu().numpy()[:, :ctx.npw], ref).max()
         print(f"{key}: H psi FP64 rel err {err:.2e}")
         assert err < 1e-11
+        ctx.fft_config(pwlib.PW_FP64, variant=48)   # complex128 row-slice plane kernels
+        h48 = torch.zeros_like(t)
+        ctx.hamiltonian_apply(t, h48)
+        torch.cuda.synchronize()
+        assert rel(h48.cpu().numpy()[:, :ctx.npw], ref).max() < 1e-11
+        ctx.fft_config(pwlib.PW_FP64, variant=0)
         if sp is not None:
             assert rel(sp.cpu().numpy()[:, :ctx.npw], ham.apply_s(psi)).max() < 1e-12
         for variant in (0, 1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 16, 19, 32, 35, 36, 38, 39, 40, 41, 42, 48, 51, 52, 54, 55, 58):
