@@ -392,7 +392,8 @@ enum pw_prof_class {
  * copies (the several-band forms 8 and 10 double-buffered: band b + 1 in flight while band
  * b is transformed).  Plane forms: 0 line groups, 1 one thread per line, 2 groups of warps per 32
  * lines with table twiddles over the whole plane in shared memory, 3 the same over the
- * plane's sphere rows and 32-column slices (less shared memory per CTA on large boxes).
+ * plane's sphere rows and 32-column slices (less shared memory per CTA on large boxes),
+ * 4 form 3 for the inverse pass and form 2 for the forward pass.
  * PW_FP64 tunes the plane form only (0 or 3, variant 0 or 48; its x-line form is fixed).
  * Forms other than 0 cover box lengths with two-stage radix plans.  Keeps the fastest for
  * `precision` in the context.  Synchronises the stream; *best_ms (may be NULL) receives

@@ -2008,6 +2008,11 @@ template <int N2, int N3, int TW> struct PlaneW {
   static constexpr int THREADS = 32 * TW * NG;
   static constexpr bool ok = (P2.nst == 2 && P3.nst == 2);
 };
+// byte offset of pass 3's prefetched blocks: after the plane and the row map, 16-aligned
+template <typename C, int N2, int N3, int TW>
+__host__ __device__ constexpr size_t plane_wg_stage_off() {
+  return ((sizeof(C) * (size_t)N2 * PlaneW<N2, N3, TW>::FP + sizeof(int) * N2) + 15) / 16 * 16;
+}
 
 template <typename T, int N2, int N3, int TW>
 __global__ void __launch_bounds__(PlaneW<N2, N3, TW>::THREADS) k_plane_inv_wg(const cplx<T>* __restrict__ psi,
@@ -2032,7 +2037,8 @@ __global__ void __launch_bounds__(PlaneW<N2, N3, TW>::THREADS) k_plane_inv_wg(co
   __syncthreads();
   for (int i = threadIdx.x; i < nr; i += blockDim.x) ymap[pmod(sp.row_k[r0 + i], N2)] = i;
   // z-lines, chunks of 32 * NG rows (the chunk count is the same for every thread); the
-  // first stage reads the row's run of coefficients straight from the block
+  // first stage reads the row's run of coefficients straight from the block (staging the
+  // plane's block first measured slower: with one CTA per SM nothing overlaps the wait)
   for (int c0 = 0; c0 < nr; c0 += 32 * NG) {
     const int row = c0 + g * 32 + lane;
     const bool live = row < nr;
@@ -2130,6 +2136,20 @@ __global__ void __launch_bounds__(PlaneW<N2, N3, TW>::THREADS) k_plane_fwd_wg(co
   const C* srcp = hb + (int64_t)b * hb_bs + (int64_t)p * N2 * N3;
   const C* twy = tw + plan.d[1].tw_off[0];
   const C* twz = tw + plan.d[2].tw_off[0];
+  // the plane's block of Y_k and of the kinetic diagonal (contiguous in the sphere order),
+  // prefetched by asynchronous copies while the y- and z-lines are transformed
+  C* Sy = reinterpret_cast<C*>(smem_raw + plane_wg_stage_off<C, N2, N3, TW>());
+  T* Sk = reinterpret_cast<T*>(Sy + sp.max_plane_g);
+  const int pg0 = nr > 0 ? sp.row_g0[r0] : 0;
+  const int pcnt = nr > 0 ? sp.row_g0[r0 + nr - 1] + sp.row_cnt[r0 + nr - 1] - pg0 : 0;
+  {
+    const C* yb = psi + (int64_t)b * ldpsi + pg0;
+    for (int i = threadIdx.x; i < pcnt; i += blockDim.x) {
+      cp_async_el<sizeof(C)>(Sy + i, yb + i);
+      cp_async_el<sizeof(T)>(Sk + i, kin + pg0 + i);
+    }
+    cp_async_commit();
+  }
   for (int i = threadIdx.x; i < N2; i += blockDim.x) ymap[i] = -1;
   __syncthreads();
   for (int i = threadIdx.x; i < nr; i += blockDim.x) ymap[pmod(sp.row_k[r0 + i], N2)] = i;
@@ -2169,7 +2189,6 @@ __global__ void __launch_bounds__(PlaneW<N2, N3, TW>::THREADS) k_plane_fwd_wg(co
   __syncthreads();
   // z-lines of the rows holding coefficients, chunks of 32 * NG rows: gather with the
   // kinetic term
-  const C* yv = psi + (int64_t)b * ldpsi;
   C* o = out + (int64_t)b * ldout;
   T ra = 0, rs = 0;  // recurrence alpha and shift
   if constexpr (REC) {
@@ -2214,15 +2233,17 @@ __global__ void __launch_bounds__(PlaneW<N2, N3, TW>::THREADS) k_plane_fwd_wg(co
     __syncthreads();
   }
   // gather the plane's coefficients, one warp per row (coalesced reads and writes), with the
-  // kinetic term (and the recurrence)
+  // kinetic term (and the recurrence); Y_k and t_G from the prefetched blocks
+  cp_async_wait<0>();
+  __syncthreads();
   for (int row = w; row < nr; row += blockDim.x >> 5) {
     const int g0 = sp.row_g0[r0 + row], cnt = sp.row_cnt[r0 + row], l0 = sp.row_l0[r0 + row];
     const C* line = F + pmod(sp.row_k[r0 + row], N2) * FP;
     for (int idx = lane; idx < cnt; idx += 32) {
       const C v = line[pmod(l0 + idx, N3)];
       const int gg = g0 + idx;
-      const C yy = yv[gg];
-      const T k = kin[gg];
+      const C yy = Sy[gg - pg0];
+      const T k = Sk[gg - pg0];
       if constexpr (!REC) {
         o[gg] = mk<C>(k * yy.x + v.x, k * yy.y + v.y);
       } else {
@@ -2253,8 +2274,10 @@ __global__ void __launch_bounds__(PlaneW<N2, N3, TW>::THREADS) k_plane_fwd_wg(co
 }
 
 template <typename T, int N2, int N3, int TW>
-static size_t plane_wg_smem() {
-  return sizeof(cplx<T>) * (size_t)N2 * PlaneW<N2, N3, TW>::FP + sizeof(int) * N2;
+static size_t plane_wg_smem(const SphereDev& sp, int which) {
+  // plane, row map; pass 3 also the prefetched blocks of Y_k and t_G of its plane
+  return which ? plane_wg_stage_off<cplx<T>, N2, N3, TW>() + (sizeof(cplx<T>) + sizeof(T)) * (size_t)sp.max_plane_g
+               : sizeof(cplx<T>) * (size_t)N2 * PlaneW<N2, N3, TW>::FP + sizeof(int) * N2;
 }
 
 template <typename T, int N2, int N3, int TW>
@@ -2265,7 +2288,7 @@ static cudaError_t plane_wg_pair(int which, const cplx<T>* psi, int64_t ldpsi, c
   if constexpr (!PW::ok) {
     return cudaErrorNotSupported;
   } else {
-    const size_t sm = plane_wg_smem<T, N2, N3, TW>();
+    const size_t sm = plane_wg_smem<T, N2, N3, TW>(sp, which);
     if (sm > 227 * 1024) return cudaErrorNotSupported;
     cudaError_t e;
     if (which == 0) {
@@ -2777,7 +2800,7 @@ cudaError_t launch_local_apply(const FftPlan& plan, const cplx<T>* tw, const Sph
   // plan in the other order, 7-10 as 3-6 with the planes staged by asynchronous copies, the
   // multi-band forms double-buffered), plane form = variant / 16 (0 line groups, 1 one thread
   // per line, 2 warp groups over the whole plane, 3 warp groups over sphere rows and 32-column
-  // slices)
+  // slices, 4 = 3 for pass 1 and 2 for pass 3)
   // complex128: only the plane form is selectable (0 line groups, 3 sphere rows + column
   // slices); the x-line pass keeps the line-group form
   const int fv = prof ? prof->fft_variant[std::is_same<T, float>::value ? 0 : 1] : 0;
@@ -2792,7 +2815,8 @@ cudaError_t launch_local_apply(const FftPlan& plan, const cplx<T>* tw, const Sph
       vperm_x = (const T*)prof->vperm32_sw;
     else xf -= 2;
   }
-  const bool tpl = pf == 1, pwg = pf == 2, prs = pf == 3;
+  // plane form 4: pass 1 over sphere rows + column slices, pass 3 over the whole plane
+  const bool tpl = pf == 1, pwg = pf == 2, prs = pf == 3, pmix = pf == 4;
   const bool xtw = xf == 2, xtwr = xf_twr(xf);
   for (int b0 = 0; b0 < nband; b0 += band_batch) {
     const int nb = min(band_batch, nband - b0);
@@ -2802,7 +2826,7 @@ cudaError_t launch_local_apply(const FftPlan& plan, const cplx<T>* tw, const Sph
       if (tpl) e = plane_tpl<T>(0, psi + b0 * ldpsi, ldpsi, hb, hb_bs, sp, plan, kin, nullptr, 0, nb, st);
       if (pwg) e = plane_wg<T>(0, psi + b0 * ldpsi, ldpsi, hb, hb_bs, sp, plan, tw, kin, nullptr, 0, nb, st);
     }
-    if (prs) e = plane_rs<T>(0, psi + b0 * ldpsi, ldpsi, hb, hb_bs, sp, plan, tw, kin, nullptr, 0, nb, st);
+    if (prs || pmix) e = plane_rs<T>(0, psi + b0 * ldpsi, ldpsi, hb, hb_bs, sp, plan, tw, kin, nullptr, 0, nb, st);
     if (e == cudaErrorNotSupported) {
       (void)cudaGetLastError();
       e = plane_lg<T>(0, psi + b0 * ldpsi, ldpsi, hb, hb_bs, sp, plan, tw, kin, nullptr, 0, nb, st);
@@ -2841,7 +2865,7 @@ cudaError_t launch_local_apply(const FftPlan& plan, const cplx<T>* tw, const Sph
     e = cudaErrorNotSupported;
     if constexpr (std::is_same<T, float>::value) {
       if (tpl) e = plane_tpl<T>(1, psi + b0 * ldpsi, ldpsi, hb, hb_bs, sp, plan, kin, out + b0 * ldout, ldout, nb, st);
-      if (pwg)
+      if (pwg || pmix)
         e = plane_wg<T>(1, psi + b0 * ldpsi, ldpsi, hb, hb_bs, sp, plan, tw, kin, out + b0 * ldout, ldout, nb, st);
     }
     if (prs)
@@ -2870,7 +2894,8 @@ static bool plane_rs_covers(const FftPlan& plan) {
 bool local_apply_rec_supported(const FftPlan& plan, const ::pw_ctx* prof) {
   if (!prof) return false;
   const int pf = prof->fft_variant[0] / kFormStride;
-  return (pf == 2 && plane_wg_covers(plan)) || (pf == 3 && plane_rs_covers(plan));
+  return (pf == 2 && plane_wg_covers(plan)) || (pf == 3 && plane_rs_covers(plan)) ||
+         (pf == 4 && plane_wg_covers(plan) && plane_rs_covers(plan));
 }
 
 cudaError_t launch_local_apply_rec(const FftPlan& plan, const float2* tw, const SphereDev& sp, const float* vperm,
@@ -2886,7 +2911,8 @@ cudaError_t launch_local_apply_rec(const FftPlan& plan, const float2* tw, const 
     if (prof->vperm32_sw && vperm == prof->vperm32) vperm_x = prof->vperm32_sw;
     else xf -= 2;
   }
-  const bool prs = prof->fft_variant[0] / kFormStride == 3;
+  const int pfr = prof->fft_variant[0] / kFormStride;
+  const bool prs = pfr == 3, inv_rs = pfr == 3 || pfr == 4;
   const int64_t hb_bs = (int64_t)sp.nplane * plan.n[1] * plan.n[2];
   const int nyz = plan.n[1] * plan.n[2];
   const int lyz = 32;
@@ -2895,7 +2921,7 @@ cudaError_t launch_local_apply_rec(const FftPlan& plan, const float2* tw, const 
   for (int b0 = 0; b0 < nband; b0 += band_batch) {
     const int nb = min(band_batch, nband - b0);
     prof_begin(prof, PW_PROF_PLANE_INV);
-    if ((e = (prs ? plane_rs<T> : plane_wg<T>)(0, psi + b0 * ldpsi, ldpsi, hb, hb_bs, sp, plan, tw, kin, nullptr, 0,
+    if ((e = (inv_rs ? plane_rs<T> : plane_wg<T>)(0, psi + b0 * ldpsi, ldpsi, hb, hb_bs, sp, plan, tw, kin, nullptr, 0,
                                                 nb, st, nullptr)))
       return e;
     prof_end(prof, PW_PROF_PLANE_INV);

@@ -1342,6 +1342,11 @@ int create_impl(const pw_problem_desc* d, void* stream, pw_ctx** out) {
   ctx->sp.nrow = (int)rk.size();
   ctx->sp.max_rows = 0;
   for (int p = 0; p < ctx->sp.nplane; ++p) ctx->sp.max_rows = std::max(ctx->sp.max_rows, pl_row0[p + 1] - pl_row0[p]);
+  ctx->sp.max_plane_g = 0;
+  for (int p = 0; p < ctx->sp.nplane; ++p)  // a plane's coefficients are one contiguous block of the sphere
+    ctx->sp.max_plane_g = std::max(ctx->sp.max_plane_g,
+                                   (pl_row0[p + 1] < (int)rg0.size() ? rg0[pl_row0[p + 1]] : ctx->npw) -
+                                       rg0[pl_row0[p]]);
   int* dv;
   PW_TRY(upload(ctx, &dv, pl_h.data(), pl_h.size())); ctx->sp.plane_h = dv;
   PW_TRY(upload(ctx, &dv, pl_row0.data(), pl_row0.size())); ctx->sp.plane_row0 = dv;
@@ -1937,12 +1942,13 @@ PW_API int pw_autotune(pw_ctx* ctx, int nband, int precision, double* best_ms) {
   double best = 1e30;
   size_t best_c = ctx->fft_batch_bytes[slot];
   int best_v = ctx->fft_variant[slot];
-  auto consider = [&](size_t c, int v) -> int {
+  std::vector<std::pair<float, int>> form_times;  // (time, variant) of the form sweep
+  auto consider = [&](size_t c, int v, int reps = 5) -> int {
     const int bb = (int)std::max<size_t>(1, std::min<size_t>(c / std::max<size_t>(per, 1), nband));
     if (c != cand[0] && bb * per > c && bb == 1) return PW_OK;
     ctx->fft_variant[slot] = v;
-    float tot = 1e30f;  // the fastest of 4 timed runs (after a warm-up) resists noise best
-    for (int rep = 0; rep < 5; ++rep) {
+    float tot = 1e30f;  // the fastest of the timed runs (after a warm-up) resists noise best
+    for (int rep = 0; rep < reps; ++rep) {
       CU_TRY(cudaEventRecord(g.e0, st), "autotune event");
       cudaError_t e;
       if (precision == PW_MIXED)
@@ -1959,6 +1965,7 @@ PW_API int pw_autotune(pw_ctx* ctx, int nband, int precision, double* best_ms) {
       if (rep > 0) tot = std::min(tot, ms);  // first repetition warms up
     }
     if (tot < best) { best = tot; best_c = c; best_v = v; }
+    form_times.push_back({tot, v});
     return PW_OK;
   };
   // batch size with the current kernel forms, every kernel form at that size (complex64:
@@ -1966,8 +1973,17 @@ PW_API int pw_autotune(pw_ctx* ctx, int nband, int precision, double* best_ms) {
   for (size_t c : cand) PW_TRY(consider(c, best_v));
   const size_t c1 = best_c;
   if (precision == PW_MIXED) {
+    form_times.clear();
     for (int pf = 0; pf < kPlaneForms; ++pf)
       for (int xf = 0; xf < kXlineForms; ++xf) PW_TRY(consider(c1, xf + kFormStride * pf));
+    // the forms within a few per cent of each other: the best four timed again, round robin,
+    // and the fastest of all their runs kept
+    std::vector<std::pair<float, int>> top = form_times;
+    std::sort(top.begin(), top.end());
+    if (top.size() > 4) top.resize(4);
+    best = 1e30;
+    for (int round = 0; round < 3; ++round)
+      for (const auto& f : top) PW_TRY(consider(c1, f.second, 3));
   } else {
     // complex128: line-group planes or sphere rows + column slices (x-line form fixed)
     PW_TRY(consider(c1, 0));

@@ -62,9 +62,9 @@ template <typename C> __host__ __device__ __forceinline__ C czero() { C c; c.x =
 // potential grid is stored permuted instead.
 // ---------------------------------------------------------------------------
 constexpr int kMaxStages = 8;
-// FFT pass-kernel variant = x-line form (0-10) + kFormStride * plane form (0-3)
+// FFT pass-kernel variant = x-line form (0-10) + kFormStride * plane form (0-4)
 constexpr int kFormStride = 16;
-constexpr int kXlineForms = 11, kPlaneForms = 4;
+constexpr int kXlineForms = 11, kPlaneForms = 5;
 struct FftDim {
   int n, nst;
   int radix[kMaxStages];
@@ -141,6 +141,7 @@ __host__ __device__ constexpr CPlan make_cplan(int n) {
 // plane-wave sphere decomposition: planes (fixed h) -> rows (fixed h,k) -> runs of l
 struct SphereDev {
   int npw, nplane, nrow, max_rows;
+  int max_plane_g;        // largest coefficient count of one x-plane (its contiguous block)
   const int* plane_h;     // [nplane] Miller h
   const int* plane_row0;  // [nplane+1]
   const int* row_k;       // [nrow]
