@@ -18,6 +18,10 @@ cudaError_t la_trinv_lower(const double2* L, int64_t lda, int n, double2* X, int
 // ws: 3 n*n + n + 2 complex; norms_dev: 2 doubles.  Synchronises the stream once per sweep.
 int la_jacobi_eigh(double2* A, int n, double2* U, double* eig, double2* ws, double* norms_dev,
                    cudaStream_t st, int max_sweeps, double tol, int* sweeps_out);
+// FP32 Jacobi pre-rotation: V (n x n) <- the rotation that brings A (complex64, destroyed) to
+// off-diagonal norm below tol relative (or to the FP32 floor); ws: 2 n*n + n + 2 complex64
+int la_jacobi_rotate32(float2* A, int n, float2* V, float2* ws, double* norms_dev, cudaStream_t st, int max_sweeps,
+                       double tol, int* sweeps_out);
 cudaError_t la_coldot(const double2* A, int64_t lda, const double2* B, int64_t ldb, int npw, int m,
                       double2* out, cudaStream_t st);
 cudaError_t la_resid(const double2* HY, int64_t ldh, const double2* SY, int64_t lds, int npw, int m,

@@ -207,7 +207,13 @@ cudaError_t la_trinv_lower(const double2* L, int64_t lda, int n, double2* X, int
 }
 
 // ---- parallel cyclic Jacobi for Hermitian A (n x n, lda = n) ---------------------------
-struct Rot { double c, s; double2 ph; };  // J = [[c, s], [-s ph, c ph]]
+// Templated on the complex type: FP64 for the eigensolve itself, FP32 for the pre-rotation of
+// the mixed solver (la_jacobi_eigh32 below).
+template <typename C> struct RotT {
+  using R = decltype(C{}.x);
+  R c, s;
+  C ph;
+};  // J = [[c, s], [-s ph, c ph]]
 
 __device__ __forceinline__ void rr_pair(int t, int i, int np, int& p, int& q) {
   auto pos = [&](int s) { return s == 0 ? 0 : ((s - 1 + t) % (np - 1)) + 1; };
@@ -215,25 +221,33 @@ __device__ __forceinline__ void rr_pair(int t, int i, int np, int& p, int& q) {
   q = pos(np - 1 - i);
 }
 
-__device__ __forceinline__ Rot jac_rot(const double2* A, int n, int p, int q) {
-  Rot r{1.0, 0.0, make_double2(1.0, 0.0)};
+template <typename C>
+__device__ __forceinline__ RotT<C> jac_rot(const C* A, int n, int p, int q) {
+  using R = typename RotT<C>::R;
+  RotT<C> r;
+  r.c = (R)1;
+  r.s = (R)0;
+  r.ph.x = (R)1;
+  r.ph.y = (R)0;
   if (p >= n || q >= n) return r;
-  const double a = A[p + (int64_t)p * n].x, d = A[q + (int64_t)q * n].x;
-  const double2 b = A[p + (int64_t)q * n];
-  const double ab = hypot(b.x, b.y);
-  if (!(ab > 1e-300)) return r;
-  const double tau = (d - a) / (2.0 * ab);
-  const double t = (tau >= 0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
-  r.c = 1.0 / sqrt(1.0 + t * t);
+  const R a = A[p + (int64_t)p * n].x, d = A[q + (int64_t)q * n].x;
+  const C b = A[p + (int64_t)q * n];
+  const R ab = hypot(b.x, b.y);
+  if (!(ab > (R)(sizeof(R) == 8 ? 1e-300 : 1e-37))) return r;
+  const R tau = (d - a) / ((R)2 * ab);
+  const R t = (tau >= 0 ? (R)1 : (R)-1) / (fabs(tau) + sqrt((R)1 + tau * tau));
+  r.c = (R)1 / sqrt((R)1 + t * t);
   r.s = t * r.c;
-  r.ph = make_double2(b.x / ab, -b.y / ab);
+  r.ph.x = b.x / ab;
+  r.ph.y = -b.y / ab;
   return r;
 }
 
 // the rotation of every pair of round t, computed once (FP64 square roots and divisions
 // are the expensive part of a round).  One pair per CTA of one warp: FP64 issues at a small
 // fraction of the FP32 rate, so the pairs are spread over the SMs rather than queued on one.
-__global__ void k_jacobi_rot(const double2* __restrict__ A, int n, int np, int t, Rot* __restrict__ rot) {
+template <typename C>
+__global__ void k_jacobi_rot(const C* __restrict__ A, int n, int np, int t, RotT<C>* __restrict__ rot) {
   const int i = blockIdx.x;
   if (i >= np / 2 || threadIdx.x != 0) return;
   int p, q;
@@ -241,36 +255,38 @@ __global__ void k_jacobi_rot(const double2* __restrict__ A, int n, int np, int t
   rot[i] = jac_rot(A, n, p, q);
 }
 
-__global__ void k_jacobi_round(const double2* __restrict__ Ao, double2* __restrict__ An,
-                               const double2* __restrict__ Vo, double2* __restrict__ Vn, int n, int np, int t,
-                               const Rot* __restrict__ rot) {
+template <typename C>
+__global__ void k_jacobi_round(const C* __restrict__ Ao, C* __restrict__ An, const C* __restrict__ Vo,
+                               C* __restrict__ Vn, int n, int np, int t, const RotT<C>* __restrict__ rot) {
   const int npair = np / 2;
   const int64_t nblk = (int64_t)npair * npair;
   const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  C z;
+  z.x = 0;
+  z.y = 0;
   if (idx < nblk) {
     const int I = (int)(idx % npair), Jx = (int)(idx / npair);
     int pI, qI, pJ, qJ;
     rr_pair(t, I, np, pI, qI);
     rr_pair(t, Jx, np, pJ, qJ);
-    const Rot ri = rot[I], rj = rot[Jx];
+    const RotT<C> ri = rot[I], rj = rot[Jx];
     const bool vpI = pI < n, vqI = qI < n, vpJ = pJ < n, vqJ = qJ < n;
-    const double2 z = make_double2(0, 0);
-    const double2 b00 = (vpI && vpJ) ? Ao[pI + (int64_t)pJ * n] : z;
-    const double2 b01 = (vpI && vqJ) ? Ao[pI + (int64_t)qJ * n] : z;
-    const double2 b10 = (vqI && vpJ) ? Ao[qI + (int64_t)pJ * n] : z;
-    const double2 b11 = (vqI && vqJ) ? Ao[qI + (int64_t)qJ * n] : z;
+    const C b00 = (vpI && vpJ) ? Ao[pI + (int64_t)pJ * n] : z;
+    const C b01 = (vpI && vqJ) ? Ao[pI + (int64_t)qJ * n] : z;
+    const C b10 = (vqI && vpJ) ? Ao[qI + (int64_t)pJ * n] : z;
+    const C b11 = (vqI && vqJ) ? Ao[qI + (int64_t)qJ * n] : z;
     // T = blk * J_J ;  J_J = [[c, s], [-s ph, c ph]]
-    const double2 mJ10 = cscale(rj.ph, -rj.s), mJ11 = cscale(rj.ph, rj.c);
-    const double2 t00 = cadd(cscale(b00, rj.c), cmul(b01, mJ10));
-    const double2 t01 = cadd(cscale(b00, rj.s), cmul(b01, mJ11));
-    const double2 t10 = cadd(cscale(b10, rj.c), cmul(b11, mJ10));
-    const double2 t11 = cadd(cscale(b10, rj.s), cmul(b11, mJ11));
+    const C mJ10 = cscale(rj.ph, -rj.s), mJ11 = cscale(rj.ph, rj.c);
+    const C t00 = cadd(cscale(b00, rj.c), cmul(b01, mJ10));
+    const C t01 = cadd(cscale(b00, rj.s), cmul(b01, mJ11));
+    const C t10 = cadd(cscale(b10, rj.c), cmul(b11, mJ10));
+    const C t11 = cadd(cscale(b10, rj.s), cmul(b11, mJ11));
     // N = J_I^H T ; J_I^H = [[c, -s conj(ph)], [s, c conj(ph)]]
-    const double2 h01 = cscale(cconj(ri.ph), -ri.s), h11 = cscale(cconj(ri.ph), ri.c);
-    const double2 n00 = cadd(cscale(t00, ri.c), cmul(h01, t10));
-    const double2 n01 = cadd(cscale(t01, ri.c), cmul(h01, t11));
-    const double2 n10 = cadd(cscale(t00, ri.s), cmul(h11, t10));
-    const double2 n11 = cadd(cscale(t01, ri.s), cmul(h11, t11));
+    const C h01 = cscale(cconj(ri.ph), -ri.s), h11 = cscale(cconj(ri.ph), ri.c);
+    const C n00 = cadd(cscale(t00, ri.c), cmul(h01, t10));
+    const C n01 = cadd(cscale(t01, ri.c), cmul(h01, t11));
+    const C n10 = cadd(cscale(t00, ri.s), cmul(h11, t10));
+    const C n11 = cadd(cscale(t01, ri.s), cmul(h11, t11));
     if (vpI && vpJ) An[pI + (int64_t)pJ * n] = n00;
     if (vpI && vqJ) An[pI + (int64_t)qJ * n] = n01;
     if (vqI && vpJ) An[qI + (int64_t)pJ * n] = n10;
@@ -280,33 +296,115 @@ __global__ void k_jacobi_round(const double2* __restrict__ Ao, double2* __restri
     const int r = (int)(k % n), Jx = (int)(k / n);
     int pJ, qJ;
     rr_pair(t, Jx, np, pJ, qJ);
-    const Rot rj = rot[Jx];
+    const RotT<C> rj = rot[Jx];
     const bool vp = pJ < n, vq = qJ < n;
-    const double2 z = make_double2(0, 0);
-    const double2 vpv = vp ? Vo[r + (int64_t)pJ * n] : z;
-    const double2 vqv = vq ? Vo[r + (int64_t)qJ * n] : z;
-    const double2 mJ10 = cscale(rj.ph, -rj.s), mJ11 = cscale(rj.ph, rj.c);
+    const C vpv = vp ? Vo[r + (int64_t)pJ * n] : z;
+    const C vqv = vq ? Vo[r + (int64_t)qJ * n] : z;
+    const C mJ10 = cscale(rj.ph, -rj.s), mJ11 = cscale(rj.ph, rj.c);
     if (vp) Vn[r + (int64_t)pJ * n] = cadd(cscale(vpv, rj.c), cmul(vqv, mJ10));
     if (vq) Vn[r + (int64_t)qJ * n] = cadd(cscale(vpv, rj.s), cmul(vqv, mJ11));
   }
 }
 
-__global__ void k_eye(double2* V, int n) {
+// One pairing round with the rotations computed inside the kernel (used in FP32, where a
+// rotation costs a few instructions against a launch): a CTA updates a 16 x 16 tile of 2 x 2
+// blocks of A (pairs I, J) or a 16-row x 16-pair tile of V after its first threads have
+// computed the rotations the tile needs from the round's input matrix.
+constexpr int kJT = 16;
+template <typename C>
+__global__ void __launch_bounds__(256) k_jacobi_round_fused(const C* __restrict__ Ao, C* __restrict__ An,
+                                                           const C* __restrict__ Vo, C* __restrict__ Vn, int n,
+                                                           int np, int t, int ta) {
+  __shared__ RotT<C> ri_s[kJT], rj_s[kJT];
+  const int npair = np / 2;
+  const int tx = threadIdx.x % kJT, ty = threadIdx.x / kJT;
+  const bool is_a = (int)blockIdx.x < ta;
+  int I0 = 0, J0, r0 = 0;
+  if (is_a) {
+    const int tpr = (npair + kJT - 1) / kJT;
+    I0 = (blockIdx.x % tpr) * kJT;
+    J0 = (blockIdx.x / tpr) * kJT;
+  } else {
+    const int b = blockIdx.x - ta;
+    const int tpr = (n + kJT - 1) / kJT;
+    r0 = (b % tpr) * kJT;
+    J0 = (b / tpr) * kJT;
+  }
+  if (threadIdx.x < kJT) {
+    const int J = J0 + threadIdx.x;
+    if (J < npair) {
+      int p, q;
+      rr_pair(t, J, np, p, q);
+      rj_s[threadIdx.x] = jac_rot(Ao, n, p, q);
+    }
+  } else if (is_a && threadIdx.x < 2 * kJT) {
+    const int I = I0 + threadIdx.x - kJT;
+    if (I < npair) {
+      int p, q;
+      rr_pair(t, I, np, p, q);
+      ri_s[threadIdx.x - kJT] = jac_rot(Ao, n, p, q);
+    }
+  }
+  __syncthreads();
+  C z;
+  z.x = 0;
+  z.y = 0;
+  if (is_a) {
+    const int I = I0 + tx, Jx = J0 + ty;
+    if (I >= npair || Jx >= npair) return;
+    int pI, qI, pJ, qJ;
+    rr_pair(t, I, np, pI, qI);
+    rr_pair(t, Jx, np, pJ, qJ);
+    const RotT<C> ri = ri_s[tx], rj = rj_s[ty];
+    const bool vpI = pI < n, vqI = qI < n, vpJ = pJ < n, vqJ = qJ < n;
+    const C b00 = (vpI && vpJ) ? Ao[pI + (int64_t)pJ * n] : z;
+    const C b01 = (vpI && vqJ) ? Ao[pI + (int64_t)qJ * n] : z;
+    const C b10 = (vqI && vpJ) ? Ao[qI + (int64_t)pJ * n] : z;
+    const C b11 = (vqI && vqJ) ? Ao[qI + (int64_t)qJ * n] : z;
+    const C mJ10 = cscale(rj.ph, -rj.s), mJ11 = cscale(rj.ph, rj.c);
+    const C t00 = cadd(cscale(b00, rj.c), cmul(b01, mJ10));
+    const C t01 = cadd(cscale(b00, rj.s), cmul(b01, mJ11));
+    const C t10 = cadd(cscale(b10, rj.c), cmul(b11, mJ10));
+    const C t11 = cadd(cscale(b10, rj.s), cmul(b11, mJ11));
+    const C h01 = cscale(cconj(ri.ph), -ri.s), h11 = cscale(cconj(ri.ph), ri.c);
+    if (vpI && vpJ) An[pI + (int64_t)pJ * n] = cadd(cscale(t00, ri.c), cmul(h01, t10));
+    if (vpI && vqJ) An[pI + (int64_t)qJ * n] = cadd(cscale(t01, ri.c), cmul(h01, t11));
+    if (vqI && vpJ) An[qI + (int64_t)pJ * n] = cadd(cscale(t00, ri.s), cmul(h11, t10));
+    if (vqI && vqJ) An[qI + (int64_t)qJ * n] = cadd(cscale(t01, ri.s), cmul(h11, t11));
+  } else {
+    const int r = r0 + tx, Jx = J0 + ty;
+    if (r >= n || Jx >= npair) return;
+    int pJ, qJ;
+    rr_pair(t, Jx, np, pJ, qJ);
+    const RotT<C> rj = rj_s[ty];
+    const bool vp = pJ < n, vq = qJ < n;
+    const C vpv = vp ? Vo[r + (int64_t)pJ * n] : z;
+    const C vqv = vq ? Vo[r + (int64_t)qJ * n] : z;
+    const C mJ10 = cscale(rj.ph, -rj.s), mJ11 = cscale(rj.ph, rj.c);
+    if (vp) Vn[r + (int64_t)pJ * n] = cadd(cscale(vpv, rj.c), cmul(vqv, mJ10));
+    if (vq) Vn[r + (int64_t)qJ * n] = cadd(cscale(vpv, rj.s), cmul(vqv, mJ11));
+  }
+}
+
+template <typename C>
+__global__ void k_eye(C* V, int n) {
   const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (idx >= (int64_t)n * n) return;
   const int i = (int)(idx % n), j = (int)(idx / n);
-  V[idx] = make_double2(i == j ? 1.0 : 0.0, 0.0);
+  V[idx].x = (i == j) ? 1 : 0;
+  V[idx].y = 0;
 }
 
-// out[0] = sum_{i != j} |A_ij|^2, out[1] = sum_i A_ii^2
-__global__ void k_offnorm(const double2* A, int n, double* out) {
+// out[0] = sum_{i != j} |A_ij|^2, out[1] = sum_i A_ii^2 (accumulated in FP64)
+template <typename C>
+__global__ void k_offnorm(const C* A, int n, double* out) {
   __shared__ double so[256], sd[256];
   double o = 0, d = 0;
   for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < (int64_t)n * n;
        idx += (int64_t)gridDim.x * blockDim.x) {
     const int i = (int)(idx % n), j = (int)(idx / n);
-    const double2 a = A[idx];
-    if (i == j) d += a.x * a.x; else o += a.x * a.x + a.y * a.y;
+    const double ax = A[idx].x, ay = A[idx].y;
+    if (i == j) d += ax * ax; else o += ax * ax + ay * ay;
   }
   so[threadIdx.x] = o; sd[threadIdx.x] = d;
   __syncthreads();
@@ -315,6 +413,59 @@ __global__ void k_offnorm(const double2* A, int n, double* out) {
     __syncthreads();
   }
   if (threadIdx.x == 0) { atomicAdd(out, so[0]); atomicAdd(out + 1, sd[0]); }
+}
+
+// cyclic Jacobi sweeps on A (n x n, lda n, destroyed; the rotated matrix ends in A) with the
+// accumulated rotations in V; ws: 2 n*n + n + 2 complex of type C.  Returns the sweeps done.
+template <typename C>
+int jacobi_sweeps(C* A, int n, C* V, C* ws, double* norms_dev, cudaStream_t st, int max_sweeps, double tol,
+                  bool* converged, C** A_out, C** V_out) {
+  C* A2 = ws;
+  C* V2 = ws + (int64_t)n * n;
+  RotT<C>* rot = reinterpret_cast<RotT<C>*>(ws + 2 * (int64_t)n * n);
+  const int64_t nn = (int64_t)n * n;
+  k_eye<C><<<(unsigned)((nn + 255) / 256), 256, 0, st>>>(V, n); count_launch();
+  const int np = (n % 2) ? n + 1 : n;
+  const int npair = np / 2;
+  const int64_t work = (int64_t)npair * npair + (int64_t)n * npair;
+  const unsigned nblk = (unsigned)((work + 255) / 256);
+  C *Acur = A, *Anext = A2, *Vcur = V, *Vnext = V2;
+  int sweep = 0;
+  bool conv = (n <= 1);
+  double h[2];
+  double prev_off = INFINITY;
+  // FP32: one launch per round, the rotations recomputed per CTA; FP64: the rotations once per
+  // round in their own launch (recomputing them per CTA costs more FP64 time than the launch)
+  constexpr bool kFused = sizeof(C) == 8;
+  const int tpa = (npair + kJT - 1) / kJT, ta = tpa * tpa, tv = ((n + kJT - 1) / kJT) * tpa;
+  while (!conv && sweep < max_sweeps) {
+    for (int t = 0; t < np - 1; ++t) {
+      if (kFused) {
+        k_jacobi_round_fused<C><<<ta + tv, 256, 0, st>>>(Acur, Anext, Vcur, Vnext, n, np, t, ta); count_launch();
+      } else {
+        k_jacobi_rot<C><<<npair, 32, 0, st>>>(Acur, n, np, t, rot); count_launch();
+        k_jacobi_round<C><<<nblk, 256, 0, st>>>(Acur, Anext, Vcur, Vnext, n, np, t, rot); count_launch();
+      }
+      C* x = Acur; Acur = Anext; Anext = x;
+      x = Vcur; Vcur = Vnext; Vnext = x;
+    }
+    ++sweep;
+    cudaMemsetAsync(norms_dev, 0, 2 * sizeof(double), st);
+    k_offnorm<C><<<64, 256, 0, st>>>(Acur, n, norms_dev); count_launch();
+    cudaError_t e = cudaMemcpyAsync(h, norms_dev, 2 * sizeof(double), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return -1;
+    // converged below tol * ||A||_F, or stalled at the rounding floor (no halving in a sweep)
+    const double off = sqrt(h[0]), nrm = sqrt(h[0] + h[1]);
+    const double floor_rel = sizeof(C) == 16 ? 1e-10 : 1e-4;
+    if (off <= tol * nrm) conv = true;
+    else if (off <= floor_rel * nrm && off > 0.5 * prev_off) conv = true;
+    prev_off = off;
+  }
+  *converged = conv;
+  *A_out = Acur;
+  *V_out = Vcur;
+  return sweep;
 }
 
 // ascending sort of the diagonal with its eigenvectors (rank by counting; ties by index)
@@ -339,48 +490,35 @@ __global__ void k_sort_eig(const double2* A, const double2* V, int n, double* ei
 
 int la_jacobi_eigh(double2* A, int n, double2* U, double* eig, double2* ws, double* norms_dev,
                    cudaStream_t st, int max_sweeps, double tol, int* sweeps_out) {
-  // ws: 3 n*n + n + 2 complex (A copy, V, V copy, the rotations of a round)
-  double2* A2 = ws;
-  double2* V = ws + (int64_t)n * n;
-  double2* V2 = ws + 2 * (int64_t)n * n;
-  Rot* rot = reinterpret_cast<Rot*>(ws + 3 * (int64_t)n * n);
-  const int64_t nn = (int64_t)n * n;
-  k_eye<<<(unsigned)((nn + 255) / 256), 256, 0, st>>>(V, n); count_launch();
-  cudaMemcpyAsync(A2, A, sizeof(double2) * nn, cudaMemcpyDeviceToDevice, st);
-  cudaMemcpyAsync(V2, V, sizeof(double2) * nn, cudaMemcpyDeviceToDevice, st);
-  const int np = (n % 2) ? n + 1 : n;
-  const int npair = np / 2;
-  const int64_t work = (int64_t)npair * npair + (int64_t)n * npair;
-  const unsigned nblk = (unsigned)((work + 255) / 256);
-  double2 *Acur = A, *Anext = A2, *Vcur = V, *Vnext = V2;
-  int sweep = 0;
-  bool conv = (n <= 1);
-  double h[2];
-  double prev_off = INFINITY;
-  while (!conv && sweep < max_sweeps) {
-    for (int t = 0; t < np - 1; ++t) {
-      k_jacobi_rot<<<npair, 32, 0, st>>>(Acur, n, np, t, rot); count_launch();
-      k_jacobi_round<<<nblk, 256, 0, st>>>(Acur, Anext, Vcur, Vnext, n, np, t, rot); count_launch();
-      double2* x = Acur; Acur = Anext; Anext = x;
-      x = Vcur; Vcur = Vnext; Vnext = x;
-    }
-    ++sweep;
-    cudaMemsetAsync(norms_dev, 0, 2 * sizeof(double), st);
-    k_offnorm<<<64, 256, 0, st>>>(Acur, n, norms_dev); count_launch();
-    cudaError_t e = cudaMemcpyAsync(h, norms_dev, 2 * sizeof(double), cudaMemcpyDeviceToHost, st);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-    if (e != cudaSuccess) return cuda_status(e, "jacobi");
-    // converged below tol * ||A||_F, or stalled at the rounding floor (no halving in a sweep)
-    const double off = sqrt(h[0]), nrm = sqrt(h[0] + h[1]);
-    if (off <= tol * nrm) conv = true;
-    else if (off <= 1e-10 * nrm && off > 0.5 * prev_off) conv = true;
-    prev_off = off;
-  }
+  // ws: 3 n*n + n + 2 complex (V, then the A copy, V copy and rotations of a round)
+  double2* V = ws;
+  bool conv = false;
+  double2 *Af = nullptr, *Vf = nullptr;
+  const int sweep = jacobi_sweeps<double2>(A, n, V, ws + (int64_t)n * n, norms_dev, st, max_sweeps, tol, &conv, &Af,
+                                           &Vf);
+  if (sweep < 0) return cuda_status(cudaGetLastError(), "jacobi");
   if (sweeps_out) *sweeps_out = sweep;
-  k_sort_eig<<<n, 128, 0, st>>>(Acur, Vcur, n, eig, U); count_launch();
+  k_sort_eig<<<n, 128, 0, st>>>(Af, Vf, n, eig, U); count_launch();
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_status(e, "jacobi sort");
   return conv ? PW_OK : set_error(PW_ENOTCONV, "Jacobi eigensolver: %d sweeps without convergence", sweep);
+}
+
+// FP32 Jacobi pre-rotation of the mixed solver: A (complex64 n x n, destroyed) is rotated
+// until its off-diagonal part is below tol (relative) or stops decreasing; V (complex64 n x n)
+// receives the accumulated rotation.  ws: 2 n*n + n + 2 complex64.
+int la_jacobi_rotate32(float2* A, int n, float2* V, float2* ws, double* norms_dev, cudaStream_t st, int max_sweeps,
+                       double tol, int* sweeps_out) {
+  bool conv = false;
+  float2 *Af = nullptr, *Vf = nullptr;
+  const int sweep = jacobi_sweeps<float2>(A, n, V, ws, norms_dev, st, max_sweeps, tol, &conv, &Af, &Vf);
+  if (sweep < 0) return cuda_status(cudaGetLastError(), "jacobi (FP32)");
+  if (Vf != V) {
+    cudaError_t e = cudaMemcpyAsync(V, Vf, sizeof(float2) * (size_t)n * n, cudaMemcpyDeviceToDevice, st);
+    if (e != cudaSuccess) return cuda_status(e, "jacobi (FP32) copy");
+  }
+  if (sweeps_out) *sweeps_out = sweep;
+  return PW_OK;
 }
 
 // ---- column reductions ------------------------------------------------------------

@@ -900,6 +900,55 @@ int check_flag(pw_ctx* ctx, int* flag_dev, const char* what) {
   return PW_OK;
 }
 
+// Hermitian eigensolve of a reduced matrix A (n x n, lda n, destroyed): U (n x n) and eig
+// (device, ascending); jac: 3 n*n + n + 2 complex128, norms: 2 doubles (device).  From n = 128 an
+// FP32 Jacobi pre-rotation first: V32 brings A near diagonal at the FP32 rate; V = V32 made
+// unitary in FP64 (Cholesky-QR), A' = V^dagger A V by FP64-accurate GEMMs is then a similarity
+// transform of A to rounding and nearly diagonal, so the FP64 Jacobi on A' needs only a few
+// sweeps; U = V U'.
+constexpr int kMixedEigMin = 128;
+int eigh_impl(pw_ctx* ctx, double2* A, int n, double2* U, double* eig, double2* jac, double* norms, int* sweeps) {
+  const cudaStream_t st = ctx->stream;
+  if (n < kMixedEigMin) return la_jacobi_eigh(A, n, U, eig, jac, norms, st, 40, 1e-13, sweeps);
+  const size_t nn = (size_t)n * n;
+  const size_t bytes = sizeof(double2) * 5 * nn + sizeof(float2) * (4 * nn + n + 2) + 64;
+  WS(mixb, unsigned char, WS_EIGMIX, bytes);
+  double2* V = (double2*)mixb;
+  double2* Vo = V + nn;
+  double2* T = Vo + nn;
+  double2* Gv = T + nn;
+  double2* Lv = Gv + nn;
+  float2* A32 = (float2*)(Lv + nn);
+  float2* V32 = A32 + nn;
+  float2* w32 = V32 + nn;
+  int* flag = (int*)(w32 + 2 * nn + n + 2);
+  CU_TRY(cudaMemsetAsync(flag, 0, sizeof(int), st), "flag reset");
+  CU_TRY(la_to_c64(A, n, A32, n, n, n, st), "eig: to c64");
+  int sw32 = 0, sw64 = 0;
+  PW_TRY(la_jacobi_rotate32(A32, n, V32, w32, norms, st, 30, 1e-6, &sw32));
+  CU_TRY(la_to_c128(V32, n, V, n, n, n, st), "eig: to c128");
+  // Vo = V L^{-dagger}, L L^dagger = V^dagger V
+  PW_TRY(cg<double>(ctx, 1, 0, n, n, n, V, n, V, n, epi<double>(EPI_STORE, Gv, n), 1, nullptr, st, GEMM_FULL,
+                    "eig basis Gram"));
+  CU_TRY(la_herm_sym(Gv, n, n, st), "eig basis Gram sym");
+  CU_TRY(la_cholesky(Gv, n, n, flag, st), "eig basis Cholesky");
+  CU_TRY(la_trinv_lower(Gv, n, n, Lv, n, T, st), "eig basis triangular inverse");
+  PW_TRY(cg<double>(ctx, 0, 1, n, n, n, V, n, Lv, n, epi<double>(EPI_STORE, Vo, n), 1, nullptr, st, GEMM_B_UPPER,
+                    "eig basis orthonormalisation"));
+  PW_TRY(check_flag(ctx, flag, "eigensolver basis Cholesky"));
+  // A' = Vo^dagger A Vo (into A), FP64 Jacobi on it, U = Vo U'
+  PW_TRY(cg<double>(ctx, 0, 0, n, n, n, A, n, Vo, n, epi<double>(EPI_STORE, T, n), 1, nullptr, st, GEMM_FULL,
+                    "eig rotate 1"));
+  PW_TRY(cg<double>(ctx, 1, 0, n, n, n, Vo, n, T, n, epi<double>(EPI_STORE, A, n), 1, nullptr, st, GEMM_FULL,
+                    "eig rotate 2"));
+  CU_TRY(la_herm_sym(A, n, n, st), "eig rotated sym");
+  PW_TRY(la_jacobi_eigh(A, n, T, eig, jac, norms, st, 40, 1e-13, &sw64));
+  PW_TRY(cg<double>(ctx, 0, 0, n, n, n, Vo, n, T, n, epi<double>(EPI_STORE, U, n), 1, nullptr, st, GEMM_FULL,
+                    "eig back-rotation"));
+  if (sweeps) *sweeps = sw64;
+  return PW_OK;
+}
+
 // q_out (ld npw): the S-orthonormal block Q before the rotation; x_out (m x m): the rotation X
 // (Psi = Q X); eig_dev_out (device, m): the Ritz values.  Each may be NULL.
 //
@@ -956,7 +1005,7 @@ int rr_impl(pw_ctx* ctx, double2* Y, int64_t ldy, int m, double2* hpsi_out, doub
   CU_TRY(la_herm_sym(G, m, m, st), "reduced sym");
   PW_TRY(check_flag(ctx, scal, "Rayleigh-Ritz Cholesky"));
   int sweeps = 0;
-  PW_TRY(la_jacobi_eigh(G, m, U, eig, jac, norms, st, 40, 1e-13, &sweeps));
+  PW_TRY(eigh_impl(ctx, G, m, U, eig, jac, norms, &sweeps));
   ctx->last_sweeps = sweeps;
   // X = Linv^dagger U  -> tmp
   CU_TRY(launch_cgemm<double>(1, 0, m, m, m, Linv, m, U, m, epi<double>(EPI_STORE, tmp, m), 1, nullptr, st), "back-transform");
@@ -1036,7 +1085,7 @@ int rr_coeffs(pw_ctx* ctx, const double2* Z, int64_t ldz, const double2* HZ, int
   CU_TRY(la_herm_sym(G, k, k, st), "reduced sym");
   PW_TRY(check_flag(ctx, flag, "LOBPCG Rayleigh-Ritz Cholesky"));
   int sweeps = 0;
-  PW_TRY(la_jacobi_eigh(G, k, U, ev, jac, ev + 2 * k, st, 40, 1e-13, &sweeps));
+  PW_TRY(eigh_impl(ctx, G, k, U, ev, jac, ev + 2 * k, &sweeps));
   CU_TRY(launch_cgemm<double>(1, 0, k, k, k, Linv, k, U, k, epi<double>(EPI_STORE, C, k), 1, nullptr, st), "back-transform");
   *eig_dev = ev;
   return PW_OK;
@@ -1977,13 +2026,32 @@ PW_API int pw_autotune(pw_ctx* ctx, int nband, int precision, double* best_ms) {
     for (int pf = 0; pf < kPlaneForms; ++pf)
       for (int xf = 0; xf < kXlineForms; ++xf) PW_TRY(consider(c1, xf + kFormStride * pf));
     // the forms within a few per cent of each other: the best four timed again, round robin,
-    // and the fastest of all their runs kept
+    // inside two steps of the filter itself (its projector GEMMs between the passes change
+    // what the passes find in L2), and the fastest of all their runs kept
     std::vector<std::pair<float, int>> top = form_times;
     std::sort(top.begin(), top.end());
     if (top.size() > 4) top.resize(4);
-    best = 1e30;
-    for (int round = 0; round < 3; ++round)
-      for (const auto& f : top) PW_TRY(consider(c1, f.second, 3));
+    WS(yf, float2, WS_Y32, (size_t)ctx->npw * nband);
+    CU_TRY(cudaMemsetAsync(yf, 0, sizeof(float2) * (size_t)ctx->npw * nband, st), "autotune block");
+    ctx->fft_batch_bytes[slot] = c1;
+    float fbest = 1e30f;
+    int fv = best_v;
+    for (int round = 0; round < 3; ++round) {
+      for (const auto& f : top) {
+        ctx->fft_variant[slot] = f.second;
+        if (round == 0) PW_TRY(filter_impl<float>(ctx, yf, ctx->npw, nband, 2, 0.0, 1.0));  // warm-up
+        CU_TRY(cudaEventRecord(g.e0, st), "autotune event");
+        PW_TRY(filter_impl<float>(ctx, yf, ctx->npw, nband, 2, 0.0, 1.0));
+        CU_TRY(cudaEventRecord(g.e1, st), "autotune event");
+        CU_TRY(cudaEventSynchronize(g.e1), "autotune sync");
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, g.e0, g.e1);
+        if (ms < fbest) { fbest = ms; fv = f.second; }
+      }
+    }
+    best_v = fv;
+    best_c = c1;
+    ctx->fft_variant[slot] = fv;
   } else {
     // complex128: line-group planes or sphere rows + column slices (x-line form fixed)
     PW_TRY(consider(c1, 0));

@@ -243,7 +243,7 @@ enum WsSlot {
   WS_GRAM, WS_GRAM2, WS_LINV, WS_TMP, WS_U, WS_JAC, WS_EIG,  // subspace matrices
   WS_LZ, WS_RQ, WS_DEN, WS_SCAL, WS_VPOT, WS_PZ,
   WS_OZA, WS_OZB, WS_OZPART, WS_OZAMAX, WS_OZEXP, WS_SCF,
-  WS_LOBZ, WS_LOBT, WS_LOBB, WS_LOBR, WS_LOBD, WS_SLICEC, WS_SLICEA, WS_NUM
+  WS_LOBZ, WS_LOBT, WS_LOBB, WS_LOBR, WS_LOBD, WS_SLICEC, WS_SLICEA, WS_EIGMIX, WS_NUM
 };
 }  // namespace pw
 
