@@ -418,3 +418,20 @@ def test_fp64_digit_gemms_agree_with_dfma(key):
         assert rel(out[1][0], out[0][0]).max() < 1e-13
         assert rel(out[1][1], out[0][1]).max() < 1e-13
         assert np.abs(out[1][3] - out[0][3]).max() < 1e-12
+
+
+def test_fft_config_accepts_the_documented_forms_only():
+    """complex64: x-line forms 0-10, plane forms 0-4 (variant = x + 16 p); complex128: plane
+    forms 0 and 3 only (variants 0 and 48); everything else PW_EINVAL."""
+    prob = W.make_problem("tiny_gamma_fp64", box=(16, 16, 16), ecut=3.0, nband=4)
+    with pwlib.Context.from_problem(prob) as ctx:
+        for v in (0, 10, 16, 48, 64, 74):
+            assert ctx.fft_config(pwlib.PW_MIXED, variant=v)[1] == v
+        for v in (11, 15, 80, 100):
+            with pytest.raises(pwlib.PWError):
+                ctx.fft_config(pwlib.PW_MIXED, variant=v)
+        for v in (0, 48):
+            assert ctx.fft_config(pwlib.PW_FP64, variant=v)[1] == v
+        for v in (3, 32, 64):
+            with pytest.raises(pwlib.PWError):
+                ctx.fft_config(pwlib.PW_FP64, variant=v)
