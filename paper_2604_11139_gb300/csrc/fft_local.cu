@@ -2039,9 +2039,13 @@ __global__ void __launch_bounds__(PlaneW<N2, N3, TW>::THREADS) k_plane_inv_wg(co
   // z-lines, chunks of 32 * NG rows (the chunk count is the same for every thread); the
   // first stage reads the row's run of coefficients straight from the block (staging the
   // plane's block first measured slower: with one CTA per SM nothing overlaps the wait)
-  for (int c0 = 0; c0 < nr; c0 += 32 * NG) {
-    const int row = c0 + g * 32 + lane;
-    const bool live = row < nr;
+  // the rows are spread over every warp of the CTA: ngz groups of 32 rows (as many as the
+  // plane needs), each group's butterflies over nwz = TW NG / ngz warps
+  const int ngz = max(1, min(NG, (nr + 31) / 32)), nwz = (TW * NG) / ngz;
+  const int gz = w / nwz, tz = w % nwz;
+  for (int c0 = 0; c0 < nr; c0 += 32 * ngz) {
+    const int row = c0 + gz * 32 + lane;
+    const bool live = gz < ngz && row < nr;
     int g0 = 0, cnt = 0, l0 = 0;
     C* line = F;
     if (live) {
@@ -2050,7 +2054,7 @@ __global__ void __launch_bounds__(PlaneW<N2, N3, TW>::THREADS) k_plane_inv_wg(co
     }
     if (live) {
 #pragma unroll 1
-      for (int J = t; J < Z2; J += TW) {
+      for (int J = tz; J < Z2; J += nwz) {
         C x[Z1];
 #pragma unroll
         for (int a = 0; a < Z1; ++a) {
@@ -2069,7 +2073,7 @@ __global__ void __launch_bounds__(PlaneW<N2, N3, TW>::THREADS) k_plane_inv_wg(co
     __syncthreads();
     if (live) {
 #pragma unroll 1
-      for (int blk = t; blk < Z1; blk += TW) {
+      for (int blk = tz; blk < Z1; blk += nwz) {
         C y[Z2];
 #pragma unroll
         for (int m = 0; m < Z2; ++m) y[m] = line[blk * Z2 + m];
@@ -2199,6 +2203,7 @@ __global__ void __launch_bounds__(PlaneW<N2, N3, TW>::THREADS) k_plane_fwd_wg(co
       ra = (T)((rec.first ? 1.0 : 2.0) / rec.dev_ce[1]);
     }
   }
+  // (spreading these rows over all the CTA's warps, as pass 1 does, measured slower here)
   for (int c0 = 0; c0 < nr; c0 += 32 * NG) {
     const int row = c0 + g * 32 + lane;
     const bool live = row < nr;
