@@ -492,7 +492,7 @@ def run_ours(args):
     pieces = ctx.tc_config()
     # pass 3 carries the recurrence (reads P Z and Y_{k-1}, writes the bf16 pieces of Y_{k+1})
     # when the warp-group plane kernels run without Q
-    fused = (fft_cfg[1] // 16 in (2, 3, 4)) and prob.Q is None
+    fused = (fft_cfg[1] // 16 in (2, 3, 4, 5, 6)) and prob.Q is None
     # projector GEMMs of M columns per filter: without Q the projection of Y_k at every step;
     # with Q the projection of W = (T + V) Y_k at every step plus that of Y_0 (P^dagger Y_k
     # follows the recurrence in projector space); one back-projection per step.  The class
@@ -565,7 +565,10 @@ def run_ours(args):
                                               "?", "?", "?", "?", "?"][fft_cfg[1] % 16],
                              "plane_kernels": ["line groups", "one thread per line", "warp groups, whole plane",
                                                "warp groups, sphere rows + 32-column slices",
-                                               "pass 1: sphere rows + 32-column slices; pass 3: whole plane"]
+                                               "pass 1: sphere rows + 32-column slices; pass 3: whole plane",
+                                               "pass 1: sphere rows + 32-column slices; pass 3: whole plane, "
+                                               "persistent with the next plane prefetched",
+                                               "whole plane, persistent, next plane prefetched (both passes)"]
                              [fft_cfg[1] // 16],
                              "variant": fft_cfg[1]},
               "fp64": fp64, "eig_err_vs_fp64": eig_err,

@@ -382,7 +382,7 @@ enum pw_prof_class {
 };
 /* Autotuner: times the local-potential FFT passes on nband bands for several band
  * batch sizes (the batch's half-box planes from 16 MB to 2 GB) and, for PW_MIXED, the
- * forms of the pass kernels, variant = x-line form + 16 * plane form.  x-line forms:
+ * forms of the pass kernels, variant = x-line form + 16 * plane form (0-6).  x-line forms:
  * 0 line groups of 1-8 threads with shared-memory twiddles, 1 one thread per line with
  * compile-time twiddles, 2 groups of warps per 32 lines with compile-time twiddles,
  * 3 the same with run-time butterfly indices and table twiddles, 4 as 3 with several bands
@@ -393,7 +393,10 @@ enum pw_prof_class {
  * b is transformed).  Plane forms: 0 line groups, 1 one thread per line, 2 groups of warps per 32
  * lines with table twiddles over the whole plane in shared memory, 3 the same over the
  * plane's sphere rows and 32-column slices (less shared memory per CTA on large boxes),
- * 4 form 3 for the inverse pass and form 2 for the forward pass.
+ * 4 form 3 for the inverse pass and form 2 for the forward pass, 5 as 4 with a persistent
+ * forward pass (one CTA per SM walking the planes; the next plane is prefetched into L2 and its
+ * blocks of Y_k and t_G into shared memory while the current one is gathered), 6 both passes
+ * whole-plane and persistent (pass 1 prefetching the next plane's sphere block into L2).
  * PW_FP64 tunes the plane form only (0 or 3, variant 0 or 48; its x-line form is fixed).
  * Forms other than 0 cover box lengths with two-stage radix plans.  Keeps the fastest for
  * `precision` in the context.  Synchronises the stream; *best_ms (may be NULL) receives

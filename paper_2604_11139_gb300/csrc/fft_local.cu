@@ -2014,11 +2014,12 @@ __host__ __device__ constexpr size_t plane_wg_stage_off() {
   return ((sizeof(C) * (size_t)N2 * PlaneW<N2, N3, TW>::FP + sizeof(int) * N2) + 15) / 16 * 16;
 }
 
-template <typename T, int N2, int N3, int TW>
-__global__ void __launch_bounds__(PlaneW<N2, N3, TW>::THREADS) k_plane_inv_wg(const cplx<T>* __restrict__ psi,
-                                                                               int64_t ldpsi, cplx<T>* __restrict__ hb,
-                                                                               int64_t hb_bs, SphereDev sp, FftPlan plan,
-                                                                               const cplx<T>* __restrict__ tw) {
+// One (plane p, band b) item of pass 1 with the whole plane in shared memory; `before_y`
+// runs between the z-lines and the y-lines (the persistent form prefetches there).
+template <typename T, int N2, int N3, int TW, typename G>
+__device__ __forceinline__ void plane_inv_wg_item(int p, int b, const cplx<T>* __restrict__ psi, int64_t ldpsi,
+                                                  cplx<T>* __restrict__ hb, int64_t hb_bs, const SphereDev& sp,
+                                                  const FftPlan& plan, const cplx<T>* __restrict__ tw, G&& before_y) {
   using C = cplx<T>;
   using PW = PlaneW<N2, N3, TW>;
   constexpr int FP = PW::FP, NG = PW::NG;
@@ -2028,7 +2029,6 @@ __global__ void __launch_bounds__(PlaneW<N2, N3, TW>::THREADS) k_plane_inv_wg(co
   C* F = reinterpret_cast<C*>(smem_raw);
   int* ymap = reinterpret_cast<int*>(F + N2 * FP);
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, g = w / TW, t = w % TW;
-  const int p = blockIdx.x, b = blockIdx.y;
   const int r0 = sp.plane_row0[p], nr = sp.plane_row0[p + 1] - r0;
   const C* src = psi + (int64_t)b * ldpsi;
   const C* twy = tw + plan.d[1].tw_off[0];
@@ -2084,6 +2084,7 @@ __global__ void __launch_bounds__(PlaneW<N2, N3, TW>::THREADS) k_plane_inv_wg(co
     }
   }
   __syncthreads();
+  before_y();
   // y-lines: column c = 32 g + lane; rows without coefficients read as zero
   const int c = g * 32 + lane;
   const bool livec = c < N3;
@@ -2118,14 +2119,54 @@ __global__ void __launch_bounds__(PlaneW<N2, N3, TW>::THREADS) k_plane_inv_wg(co
   }
 }
 
-template <typename T, int N2, int N3, int TW, bool REC>
-__global__ void __launch_bounds__(PlaneW<N2, N3, TW>::THREADS) k_plane_fwd_wg(const cplx<T>* __restrict__ hb,
+template <typename T, int N2, int N3, int TW>
+__global__ void __launch_bounds__(PlaneW<N2, N3, TW>::THREADS) k_plane_inv_wg(const cplx<T>* __restrict__ psi,
+                                                                               int64_t ldpsi, cplx<T>* __restrict__ hb,
                                                                                int64_t hb_bs, SphereDev sp, FftPlan plan,
-                                                                               const cplx<T>* __restrict__ tw,
-                                                                               const T* __restrict__ kin,
-                                                                               const cplx<T>* __restrict__ psi,
-                                                                               int64_t ldpsi, cplx<T>* __restrict__ out,
-                                                                               int64_t ldout, Pass3Rec rec) {
+                                                                               const cplx<T>* __restrict__ tw) {
+  plane_inv_wg_item<T, N2, N3, TW>(blockIdx.x, blockIdx.y, psi, ldpsi, hb, hb_bs, sp, plan, tw, [] {});
+}
+
+// Persistent form: one CTA per resident slot walks the (plane, band) items; during an item's
+// y-lines the next item's block of sphere coefficients is prefetched into L2 (one bulk
+// prefetch, its start rounded down and its end rounded down to 16 bytes).
+template <typename T, int N2, int N3, int TW>
+__global__ void __launch_bounds__(PlaneW<N2, N3, TW>::THREADS) k_plane_inv_wgp(const cplx<T>* __restrict__ psi,
+                                                                                int64_t ldpsi, cplx<T>* __restrict__ hb,
+                                                                                int64_t hb_bs, SphereDev sp,
+                                                                                FftPlan plan,
+                                                                                const cplx<T>* __restrict__ tw, int nb) {
+  using C = cplx<T>;
+  const int nitems = sp.nplane * nb;
+  for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+    const int nxt = it + gridDim.x;
+    plane_inv_wg_item<T, N2, N3, TW>(it % sp.nplane, it / sp.nplane, psi, ldpsi, hb, hb_bs, sp, plan, tw, [&] {
+      if (nxt < nitems && threadIdx.x == 0) {
+        const int pn = nxt % sp.nplane, bn = nxt / sp.nplane;
+        const int r0 = sp.plane_row0[pn], nr = sp.plane_row0[pn + 1] - r0;
+        if (nr > 0) {
+          const int g0 = sp.row_g0[r0], g1 = sp.row_g0[r0 + nr - 1] + sp.row_cnt[r0 + nr - 1];
+          const uintptr_t a0 = (uintptr_t)(psi + (int64_t)bn * ldpsi + g0) & ~(uintptr_t)15;
+          const uintptr_t a1 = (uintptr_t)(psi + (int64_t)bn * ldpsi + g1) & ~(uintptr_t)15;
+          if (a1 > a0)
+            asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(a0), "r"((unsigned)(a1 - a0)) : "memory");
+        }
+      }
+    });
+    __syncthreads();  // the plane and the row map are reused by the next item
+  }
+}
+
+// One (plane p, band b) item of pass 3 with the whole plane in shared memory.  Sy and Sk
+// receive the plane's blocks of Y_k and t_G by asynchronous copies that the caller issued
+// (committed as the group before any it issues in `before_gather`); `before_gather` runs
+// after the z-lines and waits for them.
+template <typename T, int N2, int N3, int TW, bool REC, typename G>
+__device__ __forceinline__ void plane_fwd_wg_item(int p, int b, const cplx<T>* __restrict__ hb, int64_t hb_bs,
+                                                  const SphereDev& sp, const FftPlan& plan,
+                                                  const cplx<T>* __restrict__ tw, const cplx<T>* __restrict__ psi,
+                                                  int64_t ldpsi, cplx<T>* __restrict__ out, int64_t ldout,
+                                                  const Pass3Rec& rec, cplx<T>* Sy, T* Sk, G&& before_gather) {
   using C = cplx<T>;
   using PW = PlaneW<N2, N3, TW>;
   constexpr int FP = PW::FP, NG = PW::NG;
@@ -2135,25 +2176,11 @@ __global__ void __launch_bounds__(PlaneW<N2, N3, TW>::THREADS) k_plane_fwd_wg(co
   C* F = reinterpret_cast<C*>(smem_raw);
   int* ymap = reinterpret_cast<int*>(F + N2 * FP);
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, g = w / TW, t = w % TW;
-  const int p = blockIdx.x, b = blockIdx.y;
   const int r0 = sp.plane_row0[p], nr = sp.plane_row0[p + 1] - r0;
   const C* srcp = hb + (int64_t)b * hb_bs + (int64_t)p * N2 * N3;
   const C* twy = tw + plan.d[1].tw_off[0];
   const C* twz = tw + plan.d[2].tw_off[0];
-  // the plane's block of Y_k and of the kinetic diagonal (contiguous in the sphere order),
-  // prefetched by asynchronous copies while the y- and z-lines are transformed
-  C* Sy = reinterpret_cast<C*>(smem_raw + plane_wg_stage_off<C, N2, N3, TW>());
-  T* Sk = reinterpret_cast<T*>(Sy + sp.max_plane_g);
   const int pg0 = nr > 0 ? sp.row_g0[r0] : 0;
-  const int pcnt = nr > 0 ? sp.row_g0[r0 + nr - 1] + sp.row_cnt[r0 + nr - 1] - pg0 : 0;
-  {
-    const C* yb = psi + (int64_t)b * ldpsi + pg0;
-    for (int i = threadIdx.x; i < pcnt; i += blockDim.x) {
-      cp_async_el<sizeof(C)>(Sy + i, yb + i);
-      cp_async_el<sizeof(T)>(Sk + i, kin + pg0 + i);
-    }
-    cp_async_commit();
-  }
   for (int i = threadIdx.x; i < N2; i += blockDim.x) ymap[i] = -1;
   __syncthreads();
   for (int i = threadIdx.x; i < nr; i += blockDim.x) ymap[pmod(sp.row_k[r0 + i], N2)] = i;
@@ -2239,7 +2266,7 @@ __global__ void __launch_bounds__(PlaneW<N2, N3, TW>::THREADS) k_plane_fwd_wg(co
   }
   // gather the plane's coefficients, one warp per row (coalesced reads and writes), with the
   // kinetic term (and the recurrence); Y_k and t_G from the prefetched blocks
-  cp_async_wait<0>();
+  before_gather();
   __syncthreads();
   for (int row = w; row < nr; row += blockDim.x >> 5) {
     const int g0 = sp.row_g0[r0 + row], cnt = sp.row_cnt[r0 + row], l0 = sp.row_l0[r0 + row];
@@ -2278,24 +2305,153 @@ __global__ void __launch_bounds__(PlaneW<N2, N3, TW>::THREADS) k_plane_fwd_wg(co
   }
 }
 
+// copies of a plane's blocks of Y_k (band b) and of t_G into Sy, Sk (one committed group)
+template <typename C, typename T>
+__device__ __forceinline__ void plane_fwd_stage(const SphereDev& sp, int p, int b, const C* psi, int64_t ldpsi,
+                                                const T* kin, C* Sy, T* Sk) {
+  const int r0 = sp.plane_row0[p], nr = sp.plane_row0[p + 1] - r0;
+  const int pg0 = nr > 0 ? sp.row_g0[r0] : 0;
+  const int pcnt = nr > 0 ? sp.row_g0[r0 + nr - 1] + sp.row_cnt[r0 + nr - 1] - pg0 : 0;
+  const C* yb = psi + (int64_t)b * ldpsi + pg0;
+  for (int i = threadIdx.x; i < pcnt; i += blockDim.x) {
+    cp_async_el<sizeof(C)>(Sy + i, yb + i);
+    cp_async_el<sizeof(T)>(Sk + i, kin + pg0 + i);
+  }
+  cp_async_commit();
+}
+
+// one CTA per (plane, band): the plane's blocks of Y_k and t_G are copied while the y- and
+// z-lines are transformed
+template <typename T, int N2, int N3, int TW, bool REC>
+__global__ void __launch_bounds__(PlaneW<N2, N3, TW>::THREADS) k_plane_fwd_wg(const cplx<T>* __restrict__ hb,
+                                                                               int64_t hb_bs, SphereDev sp, FftPlan plan,
+                                                                               const cplx<T>* __restrict__ tw,
+                                                                               const T* __restrict__ kin,
+                                                                               const cplx<T>* __restrict__ psi,
+                                                                               int64_t ldpsi, cplx<T>* __restrict__ out,
+                                                                               int64_t ldout, Pass3Rec rec) {
+  using C = cplx<T>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* Sy = reinterpret_cast<C*>(smem_raw + plane_wg_stage_off<C, N2, N3, TW>());
+  T* Sk = reinterpret_cast<T*>(Sy + sp.max_plane_g);
+  const int p = blockIdx.x, b = blockIdx.y;
+  plane_fwd_stage<C, T>(sp, p, b, psi, ldpsi, kin, Sy, Sk);
+  plane_fwd_wg_item<T, N2, N3, TW, REC>(p, b, hb, hb_bs, sp, plan, tw, psi, ldpsi, out, ldout, rec, Sy, Sk,
+                                        [] { cp_async_wait<0>(); });
+}
+
+// Persistent form: one CTA per SM walks the (plane, band) items; while an item's coefficients
+// are gathered, the next item's half-box plane is prefetched into L2 (one bulk prefetch of the
+// contiguous plane) and its blocks of Y_k and t_G are copied into the other of two buffers.
+template <typename T, int N2, int N3, int TW, bool REC>
+__global__ void __launch_bounds__(PlaneW<N2, N3, TW>::THREADS) k_plane_fwd_wgp(const cplx<T>* __restrict__ hb,
+                                                                                int64_t hb_bs, SphereDev sp,
+                                                                                FftPlan plan,
+                                                                                const cplx<T>* __restrict__ tw,
+                                                                                const T* __restrict__ kin,
+                                                                                const cplx<T>* __restrict__ psi,
+                                                                                int64_t ldpsi, cplx<T>* __restrict__ out,
+                                                                                int64_t ldout, Pass3Rec rec, int nb) {
+  using C = cplx<T>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* Sy0 = reinterpret_cast<C*>(smem_raw + plane_wg_stage_off<C, N2, N3, TW>());
+  T* Sk0 = reinterpret_cast<T*>(Sy0 + 2 * (size_t)sp.max_plane_g);
+  const int nitems = sp.nplane * nb;
+  int buf = 0;
+  if ((int)blockIdx.x < nitems)
+    plane_fwd_stage<C, T>(sp, blockIdx.x % sp.nplane, blockIdx.x / sp.nplane, psi, ldpsi, kin, Sy0, Sk0);
+  for (int it = blockIdx.x; it < nitems; it += gridDim.x, buf ^= 1) {
+    const int p = it % sp.nplane, b = it / sp.nplane;
+    const int nxt = it + gridDim.x;
+    C* Sy = Sy0 + (size_t)buf * sp.max_plane_g;
+    T* Sk = Sk0 + (size_t)buf * sp.max_plane_g;
+    plane_fwd_wg_item<T, N2, N3, TW, REC>(p, b, hb, hb_bs, sp, plan, tw, psi, ldpsi, out, ldout, rec, Sy, Sk, [&] {
+      if (nxt < nitems) {
+        const int pn = nxt % sp.nplane, bn = nxt / sp.nplane;
+        if (threadIdx.x == 0) {
+          const C* plane = hb + (int64_t)bn * hb_bs + (int64_t)pn * N2 * N3;
+          asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(plane), "r"((unsigned)(sizeof(C) * N2 * N3))
+                       : "memory");
+        }
+        // the other buffer was released by the barrier that ended the previous item
+        plane_fwd_stage<C, T>(sp, pn, bn, psi, ldpsi, kin, Sy0 + (size_t)(buf ^ 1) * sp.max_plane_g,
+                              Sk0 + (size_t)(buf ^ 1) * sp.max_plane_g);
+        cp_async_wait<1>();
+      } else {
+        cp_async_wait<0>();
+      }
+    });
+    __syncthreads();  // the plane, the row map and this buffer are reused two items later
+  }
+}
+
 template <typename T, int N2, int N3, int TW>
-static size_t plane_wg_smem(const SphereDev& sp, int which) {
-  // plane, row map; pass 3 also the prefetched blocks of Y_k and t_G of its plane
-  return which ? plane_wg_stage_off<cplx<T>, N2, N3, TW>() + (sizeof(cplx<T>) + sizeof(T)) * (size_t)sp.max_plane_g
+static size_t plane_wg_smem(const SphereDev& sp, int which, bool persist = false) {
+  // plane, row map; pass 3 also the prefetched blocks of Y_k and t_G of its plane (two of each
+  // in the persistent form)
+  return which ? plane_wg_stage_off<cplx<T>, N2, N3, TW>() +
+                     (persist ? 2 : 1) * (sizeof(cplx<T>) + sizeof(T)) * (size_t)sp.max_plane_g
                : sizeof(cplx<T>) * (size_t)N2 * PlaneW<N2, N3, TW>::FP + sizeof(int) * N2;
 }
 
 template <typename T, int N2, int N3, int TW>
 static cudaError_t plane_wg_pair(int which, const cplx<T>* psi, int64_t ldpsi, cplx<T>* hb, int64_t hb_bs,
                                  const SphereDev& sp, const FftPlan& plan, const cplx<T>* tw, const T* kin,
-                                 cplx<T>* out, int64_t ldout, int nb, cudaStream_t st, const Pass3Rec* rec) {
+                                 cplx<T>* out, int64_t ldout, int nb, cudaStream_t st, const Pass3Rec* rec,
+                                 bool persist) {
   using PW = PlaneW<N2, N3, TW>;
   if constexpr (!PW::ok) {
     return cudaErrorNotSupported;
   } else {
-    const size_t sm = plane_wg_smem<T, N2, N3, TW>(sp, which);
+    const size_t sm = plane_wg_smem<T, N2, N3, TW>(sp, which, persist && which == 1);
     if (sm > 227 * 1024) return cudaErrorNotSupported;
     cudaError_t e;
+    if (which == 1 && persist) {
+      int nsm = 152, dev = 0;
+      if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+      // as many resident CTAs as the SMs hold (one on 120 x 120 planes, more on smaller ones)
+      auto grid_of = [&](const void* fn) {
+        int per = 1;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, PW::THREADS, sm) != cudaSuccess || per < 1) per = 1;
+        return std::max(1, std::min(sp.nplane * nb, nsm * per));
+      };
+      if (rec) {
+        if constexpr (std::is_same<T, float>::value) {
+          if ((e = cudaFuncSetAttribute(k_plane_fwd_wgp<T, N2, N3, TW, true>,
+                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm)))
+            return e;
+          const int grid = grid_of((const void*)k_plane_fwd_wgp<T, N2, N3, TW, true>);
+          k_plane_fwd_wgp<T, N2, N3, TW, true><<<grid, PW::THREADS, sm, st>>>(hb, hb_bs, sp, plan, tw, kin, psi,
+                                                                             ldpsi, out, ldout, *rec, nb);
+          count_launch();
+        } else {
+          return cudaErrorNotSupported;
+        }
+      } else {
+        if ((e = cudaFuncSetAttribute(k_plane_fwd_wgp<T, N2, N3, TW, false>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm)))
+          return e;
+        const int grid = grid_of((const void*)k_plane_fwd_wgp<T, N2, N3, TW, false>);
+        k_plane_fwd_wgp<T, N2, N3, TW, false><<<grid, PW::THREADS, sm, st>>>(hb, hb_bs, sp, plan, tw, kin, psi,
+                                                                            ldpsi, out, ldout, Pass3Rec{}, nb);
+        count_launch();
+      }
+      return cudaGetLastError();
+    }
+    if (which == 0 && persist) {
+      int nsm = 152, dev = 0, per = 1;
+      if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+      if ((e = cudaFuncSetAttribute(k_plane_inv_wgp<T, N2, N3, TW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)sm)))
+        return e;
+      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_plane_inv_wgp<T, N2, N3, TW>, PW::THREADS, sm) !=
+              cudaSuccess || per < 1)
+        per = 1;
+      const int grid = std::max(1, std::min(sp.nplane * nb, nsm * per));
+      k_plane_inv_wgp<T, N2, N3, TW><<<grid, PW::THREADS, sm, st>>>(psi, ldpsi, hb, hb_bs, sp, plan, tw, nb);
+      count_launch();
+      return cudaGetLastError();
+    }
     if (which == 0) {
       if ((e = cudaFuncSetAttribute(k_plane_inv_wg<T, N2, N3, TW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     (int)sm)))
@@ -2337,11 +2493,13 @@ static cudaError_t plane_wg_pair(int which, const cplx<T>* psi, int64_t ldpsi, c
 template <typename T>
 static cudaError_t plane_wg(int which, const cplx<T>* psi, int64_t ldpsi, cplx<T>* hb, int64_t hb_bs,
                             const SphereDev& sp, const FftPlan& plan, const cplx<T>* tw, const T* kin, cplx<T>* out,
-                            int64_t ldout, int nb, cudaStream_t st, const Pass3Rec* rec = nullptr) {
+                            int64_t ldout, int nb, cudaStream_t st, const Pass3Rec* rec = nullptr,
+                            bool persist = false) {
   const int n2 = plan.n[1], n3 = plan.n[2];
 #define PW_WG_CASE(A, B, TWN)                                                                                  \
   if (n2 == A && n3 == B)                                                                                      \
-    return plane_wg_pair<T, A, B, TWN>(which, psi, ldpsi, hb, hb_bs, sp, plan, tw, kin, out, ldout, nb, st, rec);
+    return plane_wg_pair<T, A, B, TWN>(which, psi, ldpsi, hb, hb_bs, sp, plan, tw, kin, out, ldout, nb, st, rec, \
+                                       persist);
   PW_WG_CASE(24, 24, 4)
   PW_WG_CASE(64, 64, 4)
   PW_WG_CASE(72, 90, 4)
@@ -2820,8 +2978,11 @@ cudaError_t launch_local_apply(const FftPlan& plan, const cplx<T>* tw, const Sph
       vperm_x = (const T*)prof->vperm32_sw;
     else xf -= 2;
   }
-  // plane form 4: pass 1 over sphere rows + column slices, pass 3 over the whole plane
-  const bool tpl = pf == 1, pwg = pf == 2, prs = pf == 3, pmix = pf == 4;
+  // plane form 4: pass 1 over sphere rows + column slices, pass 3 over the whole plane; 5 the
+  // same with the persistent pass 3 (next plane prefetched); 6 both passes whole-plane and
+  // persistent
+  const bool tpl = pf == 1, pwg = pf == 2 || pf == 6, prs = pf == 3, pmix = pf == 4 || pf == 5;
+  const bool ppers = pf == 5 || pf == 6, ipers = pf == 6;
   const bool xtw = xf == 2, xtwr = xf_twr(xf);
   for (int b0 = 0; b0 < nband; b0 += band_batch) {
     const int nb = min(band_batch, nband - b0);
@@ -2829,7 +2990,8 @@ cudaError_t launch_local_apply(const FftPlan& plan, const cplx<T>* tw, const Sph
     e = cudaErrorNotSupported;
     if constexpr (std::is_same<T, float>::value) {
       if (tpl) e = plane_tpl<T>(0, psi + b0 * ldpsi, ldpsi, hb, hb_bs, sp, plan, kin, nullptr, 0, nb, st);
-      if (pwg) e = plane_wg<T>(0, psi + b0 * ldpsi, ldpsi, hb, hb_bs, sp, plan, tw, kin, nullptr, 0, nb, st);
+      if (pwg) e = plane_wg<T>(0, psi + b0 * ldpsi, ldpsi, hb, hb_bs, sp, plan, tw, kin, nullptr, 0, nb, st, nullptr,
+                               ipers);
     }
     if (prs || pmix) e = plane_rs<T>(0, psi + b0 * ldpsi, ldpsi, hb, hb_bs, sp, plan, tw, kin, nullptr, 0, nb, st);
     if (e == cudaErrorNotSupported) {
@@ -2871,7 +3033,8 @@ cudaError_t launch_local_apply(const FftPlan& plan, const cplx<T>* tw, const Sph
     if constexpr (std::is_same<T, float>::value) {
       if (tpl) e = plane_tpl<T>(1, psi + b0 * ldpsi, ldpsi, hb, hb_bs, sp, plan, kin, out + b0 * ldout, ldout, nb, st);
       if (pwg || pmix)
-        e = plane_wg<T>(1, psi + b0 * ldpsi, ldpsi, hb, hb_bs, sp, plan, tw, kin, out + b0 * ldout, ldout, nb, st);
+        e = plane_wg<T>(1, psi + b0 * ldpsi, ldpsi, hb, hb_bs, sp, plan, tw, kin, out + b0 * ldout, ldout, nb, st,
+                        nullptr, ppers);
     }
     if (prs)
       e = plane_rs<T>(1, psi + b0 * ldpsi, ldpsi, hb, hb_bs, sp, plan, tw, kin, out + b0 * ldout, ldout, nb, st);
@@ -2899,8 +3062,8 @@ static bool plane_rs_covers(const FftPlan& plan) {
 bool local_apply_rec_supported(const FftPlan& plan, const ::pw_ctx* prof) {
   if (!prof) return false;
   const int pf = prof->fft_variant[0] / kFormStride;
-  return (pf == 2 && plane_wg_covers(plan)) || (pf == 3 && plane_rs_covers(plan)) ||
-         (pf == 4 && plane_wg_covers(plan) && plane_rs_covers(plan));
+  return ((pf == 2 || pf == 6) && plane_wg_covers(plan)) || (pf == 3 && plane_rs_covers(plan)) ||
+         ((pf == 4 || pf == 5) && plane_wg_covers(plan) && plane_rs_covers(plan));
 }
 
 cudaError_t launch_local_apply_rec(const FftPlan& plan, const float2* tw, const SphereDev& sp, const float* vperm,
@@ -2917,7 +3080,8 @@ cudaError_t launch_local_apply_rec(const FftPlan& plan, const float2* tw, const 
     else xf -= 2;
   }
   const int pfr = prof->fft_variant[0] / kFormStride;
-  const bool prs = pfr == 3, inv_rs = pfr == 3 || pfr == 4;
+  const bool prs = pfr == 3, inv_rs = pfr == 3 || pfr == 4 || pfr == 5, fwd_pers = pfr == 5 || pfr == 6;
+  const bool inv_pers = pfr == 6;
   const int64_t hb_bs = (int64_t)sp.nplane * plan.n[1] * plan.n[2];
   const int nyz = plan.n[1] * plan.n[2];
   const int lyz = 32;
@@ -2926,9 +3090,10 @@ cudaError_t launch_local_apply_rec(const FftPlan& plan, const float2* tw, const 
   for (int b0 = 0; b0 < nband; b0 += band_batch) {
     const int nb = min(band_batch, nband - b0);
     prof_begin(prof, PW_PROF_PLANE_INV);
-    if ((e = (inv_rs ? plane_rs<T> : plane_wg<T>)(0, psi + b0 * ldpsi, ldpsi, hb, hb_bs, sp, plan, tw, kin, nullptr, 0,
-                                                nb, st, nullptr)))
-      return e;
+    e = inv_rs ? plane_rs<T>(0, psi + b0 * ldpsi, ldpsi, hb, hb_bs, sp, plan, tw, kin, nullptr, 0, nb, st, nullptr)
+               : plane_wg<T>(0, psi + b0 * ldpsi, ldpsi, hb, hb_bs, sp, plan, tw, kin, nullptr, 0, nb, st, nullptr,
+                             inv_pers);
+    if (e) return e;
     prof_end(prof, PW_PROF_PLANE_INV);
     prof_begin(prof, PW_PROF_XLINE);
     e = cudaErrorNotSupported;
@@ -2954,9 +3119,11 @@ cudaError_t launch_local_apply_rec(const FftPlan& plan, const float2* tw, const 
     r.pz = rec.pz + b0 * rec.ldpz;
     if (rec.ykm1) r.ykm1 = rec.ykm1 + b0 * rec.ldykm1;
     if (rec.split) r.split = (__nv_bfloat16*)rec.split + b0 * rec.split_ld;
-    if ((e = (prs ? plane_rs<T> : plane_wg<T>)(1, psi + b0 * ldpsi, ldpsi, hb, hb_bs, sp, plan, tw, kin,
-                                                out + b0 * ldout, ldout, nb, st, &r)))
-      return e;
+    e = prs ? plane_rs<T>(1, psi + b0 * ldpsi, ldpsi, hb, hb_bs, sp, plan, tw, kin, out + b0 * ldout, ldout, nb, st,
+                          &r)
+            : plane_wg<T>(1, psi + b0 * ldpsi, ldpsi, hb, hb_bs, sp, plan, tw, kin, out + b0 * ldout, ldout, nb, st,
+                          &r, fwd_pers);
+    if (e) return e;
     prof_end(prof, PW_PROF_PLANE_FWD);
   }
   return cudaGetLastError();

@@ -2025,15 +2025,23 @@ PW_API int pw_autotune(pw_ctx* ctx, int nband, int precision, double* best_ms) {
     form_times.clear();
     for (int pf = 0; pf < kPlaneForms; ++pf)
       for (int xf = 0; xf < kXlineForms; ++xf) PW_TRY(consider(c1, xf + kFormStride * pf));
-    // the forms within a few per cent of each other: the best four timed again, round robin,
-    // inside two steps of the filter itself (its projector GEMMs between the passes change
-    // what the passes find in L2), and the fastest of all their runs kept
-    std::vector<std::pair<float, int>> top = form_times;
-    std::sort(top.begin(), top.end());
-    if (top.size() > 4) top.resize(4);
+    // the plane forms compared again inside two steps of the filter itself, round robin (its
+    // projector GEMMs between the passes change what the passes find in L2; the persistent
+    // plane forms gain there and not in bare applies), each with the x-line form of the best
+    // bare time; the fastest of all their runs kept
+    const int xbest = best_v % kFormStride;
+    std::vector<std::pair<float, int>> top;
+    for (int pf = 0; pf < kPlaneForms; ++pf) top.push_back({0.f, xbest + kFormStride * pf});
+    // at the batch size that suits the forms found (the first batch sweep ran with the
+    // initial forms, which may prefer other sizes)
+    {
+      const int vb = best_v;
+      for (size_t c : cand) PW_TRY(consider(c, vb));
+    }
+    const size_t c2 = best_c;
     WS(yf, float2, WS_Y32, (size_t)ctx->npw * nband);
     CU_TRY(cudaMemsetAsync(yf, 0, sizeof(float2) * (size_t)ctx->npw * nband, st), "autotune block");
-    ctx->fft_batch_bytes[slot] = c1;
+    ctx->fft_batch_bytes[slot] = c2;
     float fbest = 1e30f;
     int fv = best_v;
     for (int round = 0; round < 3; ++round) {
@@ -2050,7 +2058,7 @@ PW_API int pw_autotune(pw_ctx* ctx, int nband, int precision, double* best_ms) {
       }
     }
     best_v = fv;
-    best_c = c1;
+    best_c = c2;
     ctx->fft_variant[slot] = fv;
   } else {
     // complex128: line-group planes or sphere rows + column slices (x-line form fixed)

@@ -62,9 +62,9 @@ template <typename C> __host__ __device__ __forceinline__ C czero() { C c; c.x =
 // potential grid is stored permuted instead.
 // ---------------------------------------------------------------------------
 constexpr int kMaxStages = 8;
-// FFT pass-kernel variant = x-line form (0-10) + kFormStride * plane form (0-4)
+// FFT pass-kernel variant = x-line form (0-10) + kFormStride * plane form (0-6)
 constexpr int kFormStride = 16;
-constexpr int kXlineForms = 11, kPlaneForms = 5;
+constexpr int kXlineForms = 11, kPlaneForms = 7;
 struct FftDim {
   int n, nst;
   int radix[kMaxStages];

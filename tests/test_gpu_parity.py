@@ -91,7 +91,7 @@ def test_hamiltonian_apply_fp64(key):
         assert torch.count_nonzero(h[:, ctx.npw:]) == 0
 
 
-@pytest.mark.parametrize("variant", [0, 1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 16, 19, 32, 35, 36, 38, 39, 40, 41, 42, 48, 51, 52, 54, 55, 58, 67, 71])
+@pytest.mark.parametrize("variant", [0, 1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 16, 19, 32, 35, 36, 38, 39, 40, 41, 42, 48, 51, 52, 54, 55, 58, 67, 71, 83, 87, 99, 103])
 @pytest.mark.parametrize("key", ["cubic16_q", "ortho_k_ragged", "tiny_24_aliasing", "box_64_tl8"])
 def test_hamiltonian_apply_mixed(key, variant):
     """The complex64 FFT pass kernel forms (variant = x-line form + 16 * plane form: line
@@ -125,7 +125,7 @@ def test_filter_fp64(key):
             assert rel(t.cpu().numpy()[:, :ctx.npw], ref).max() < 1e-10, degree
 
 
-@pytest.mark.parametrize("variant", [0, 1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 16, 19, 32, 35, 36, 38, 39, 40, 41, 42, 48, 51, 52, 54, 55, 58, 67, 71])
+@pytest.mark.parametrize("variant", [0, 1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 16, 19, 32, 35, 36, 38, 39, 40, 41, 42, 48, 51, 52, 54, 55, 58, 67, 71, 83, 87, 99, 103])
 @pytest.mark.parametrize("key", ["cubic16_q", "tiny_24_aliasing", "box_64_tl8"])
 def test_filter_mixed(key, variant):
     prob, ham, ctx = setup(key)
@@ -282,7 +282,7 @@ def test_full_size_fp64_at_scale_sampled_bands():
         torch.cuda.synchronize()
         assert rel(h.cpu().numpy()[:, :ctx.npw], ref).max() < 1e-11
         ctx.fft_config(pwlib.PW_FP64, variant=0)
-        for variant in (0, 1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 16, 19, 32, 35, 36, 38, 39, 40, 41, 42, 48, 51, 52, 54, 55, 58, 67, 71):
+        for variant in (0, 1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 16, 19, 32, 35, 36, 38, 39, 40, 41, 42, 48, 51, 52, 54, 55, 58, 67, 71, 83, 87, 99, 103):
             ctx.fft_config(pwlib.PW_MIXED, variant=variant)
             t32 = to_dev(psi, torch.complex64)
             h32 = torch.zeros_like(t32)
@@ -331,7 +331,7 @@ def test_full_size_other_boxes_sampled_bands(key):
         ctx.fft_config(pwlib.PW_FP64, variant=0)
         if sp is not None:
             assert rel(sp.cpu().numpy()[:, :ctx.npw], ham.apply_s(psi)).max() < 1e-12
-        for variant in (0, 1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 16, 19, 32, 35, 36, 38, 39, 40, 41, 42, 48, 51, 52, 54, 55, 58, 67, 71):
+        for variant in (0, 1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 16, 19, 32, 35, 36, 38, 39, 40, 41, 42, 48, 51, 52, 54, 55, 58, 67, 71, 83, 87, 99, 103):
             ctx.fft_config(pwlib.PW_MIXED, variant=variant)
             t32 = to_dev(psi, torch.complex64)
             h32 = torch.zeros_like(t32)
@@ -421,13 +421,13 @@ def test_fp64_digit_gemms_agree_with_dfma(key):
 
 
 def test_fft_config_accepts_the_documented_forms_only():
-    """complex64: x-line forms 0-10, plane forms 0-4 (variant = x + 16 p); complex128: plane
+    """complex64: x-line forms 0-10, plane forms 0-6 (variant = x + 16 p); complex128: plane
     forms 0 and 3 only (variants 0 and 48); everything else PW_EINVAL."""
     prob = W.make_problem("tiny_gamma_fp64", box=(16, 16, 16), ecut=3.0, nband=4)
     with pwlib.Context.from_problem(prob) as ctx:
-        for v in (0, 10, 16, 48, 64, 74):
+        for v in (0, 10, 16, 48, 64, 74, 80, 90, 96, 106):
             assert ctx.fft_config(pwlib.PW_MIXED, variant=v)[1] == v
-        for v in (11, 15, 80, 100):
+        for v in (11, 15, 107, 112):
             with pytest.raises(pwlib.PWError):
                 ctx.fft_config(pwlib.PW_MIXED, variant=v)
         for v in (0, 48):
