@@ -37,9 +37,13 @@ constexpr bool xf_swap(int xf) { return xf == 5 || xf == 6 || xf == 9 || xf == 1
 constexpr bool xf_staged(int xf) { return xf >= 7 && xf <= 10; }
 
 // ---- butterfly arithmetic ---------------------------------------------------------
-// complex64 butterflies use the paired FP32 instructions of sm_100-class SMs (one add,
-// multiply or fused multiply-add for both halves of a float2, each half rounded to nearest
-// as the scalar instruction would); complex128 keeps the scalar forms.
+// complex64 sums, differences and real scalings use the paired FP32 instructions of
+// sm_100-class SMs (one add, multiply or fused multiply-add for both halves of a float2,
+// each half rounded to nearest as the scalar instruction would); complex128 keeps the
+// scalar forms.  The products by +-i swap the halves of an operand, which a paired
+// instruction cannot do in place, so they stay two scalar instructions (measured on the
+// 120^3 plane passes: 6% faster than paired with the swap; all-scalar butterflies are
+// slower still).  Every form rounds each result identically.
 __device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
 __device__ __forceinline__ double2 bf_add(double2 a, double2 b) { return cadd(a, b); }
 __device__ __forceinline__ float2 bf_add(float2 a, float2 b) { return __fadd2_rn(a, b); }
@@ -57,13 +61,13 @@ template <int S> __device__ __forceinline__ double2 bf_add_muli(double2 a, doubl
   return make_double2(fma(-S * s, b.y, a.x), fma(S * s, b.x, a.y));
 }
 template <int S> __device__ __forceinline__ float2 bf_add_muli(float2 a, float2 b, float s = 1.f) {
-  return __ffma2_rn(f2(b.y, b.x), f2(-S * s, S * s), a);
+  return f2(__fmaf_rn(-S * s, b.y, a.x), __fmaf_rn(S * s, b.x, a.y));
 }
 template <int S> __device__ __forceinline__ double2 bf_sub_muli(double2 a, double2 b, double s = 1.0) {
   return make_double2(fma(S * s, b.y, a.x), fma(-S * s, b.x, a.y));
 }
 template <int S> __device__ __forceinline__ float2 bf_sub_muli(float2 a, float2 b, float s = 1.f) {
-  return __ffma2_rn(f2(b.y, b.x), f2(S * s, -S * s), a);
+  return f2(__fmaf_rn(S * s, b.y, a.x), __fmaf_rn(-S * s, b.x, a.y));
 }
 
 // ---- small DFTs: y_m = sum_k x_k exp(S 2 pi i k m / R) -------------------------
@@ -1430,12 +1434,18 @@ template <int N> __device__ __forceinline__ void cp_async_wait() {
 // Copies one band's np planes of the CTA's 32 lines into the line buffer Lb (element p of
 // lane l at Lb[p * 32 + l], which is where the first stage reads and writes it); lanes past
 // the end of the yz range are not copied (their results are never stored).
+// (blockDim.x a multiple of 32: warp w copies the planes p with p mod (warp count) = w, lane l
+// its line l, by pointer increments)
 template <typename C>
 __device__ __forceinline__ void xw_stage_planes(C* Lb, const C* hbb, int yz0, int nyz, int np) {
   const int nl = min(32, nyz - yz0);
-  for (int q = threadIdx.x; q < np * 32; q += blockDim.x) {
-    const int p = q >> 5, l = q & 31;
-    if (l < nl) cp_async_el<sizeof(C)>(Lb + q, hbb + (int64_t)p * nyz + yz0 + l);
+  const int l = threadIdx.x & 31, nw = blockDim.x >> 5;
+  if (l < nl) {
+    int p = threadIdx.x >> 5;
+    const C* src = hbb + (int64_t)p * nyz + yz0 + l;
+    C* dst = Lb + p * 32 + l;
+    const int64_t ss = (int64_t)nw * nyz;
+    for (; p < np; p += nw, src += ss, dst += nw * 32) cp_async_el<sizeof(C)>(dst, src);
   }
   cp_async_commit();
 }
