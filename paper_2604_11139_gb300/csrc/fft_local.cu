@@ -337,6 +337,9 @@ __device__ void fft_lines(C* buf, int nlines, int ls, int es, const FftDim& d, c
 }
 
 __device__ __forceinline__ int pmod(int a, int n) { int r = a % n; return r < 0 ? r + n : r; }
+// (s + d) mod N for 0 <= s, d < N: one conditional subtraction (the gathers step l0 + idx
+// by 32 as wrap_n<N3>(l, 32 % N3) instead of a division each)
+template <int N> __device__ __forceinline__ int wrap_n(int s, int d) { const int v = s + d; return v >= N ? v - N : v; }
 
 // ---- line-group engine: each line is transformed by a group of TL threads of one warp
 // (TL a power of two dividing the butterfly count of every stage), butterflies of a
@@ -1408,10 +1411,13 @@ __device__ __forceinline__ void xw_bf_fwd(const C* L, C* hbl, const C* __restric
     for (int m = 1; m < R1; ++m) x[m] = cmul(x[m], __ldg(&tw1[J * TA + m * TB - 1]));
   }
   dftR<C, -1, R1>(x);
+  // plane p = J + R2 a at hbl + p nyz, stepped by a running pointer
+  C* o = hbl + (int64_t)J * nyz;
+  const int64_t so = (int64_t)R2 * nyz;
+  const int na = live ? (np - J + R2 - 1) / R2 : 0;  // planes J + R2 a < np
 #pragma unroll
-  for (int a = 0; a < R1; ++a) {
-    const int p = J + R2 * a;
-    if (live && p < np) hbl[(int64_t)p * nyz] = x[a];
+  for (int a = 0; a < R1; ++a, o += so) {
+    if (a < na) *o = x[a];
   }
 }
 
@@ -2281,8 +2287,9 @@ __device__ __forceinline__ void plane_fwd_wg_item(int p, int b, const cplx<T>* _
   for (int row = w; row < nr; row += blockDim.x >> 5) {
     const int g0 = sp.row_g0[r0 + row], cnt = sp.row_cnt[r0 + row], l0 = sp.row_l0[r0 + row];
     const C* line = F + pmod(sp.row_k[r0 + row], N2) * FP;
-    for (int idx = lane; idx < cnt; idx += 32) {
-      const C v = line[pmod(l0 + idx, N3)];
+    int lz = pmod(l0 + lane, N3);
+    for (int idx = lane; idx < cnt; idx += 32, lz = wrap_n<N3>(lz, 32 % N3)) {
+      const C v = line[lz];
       const int gg = g0 + idx;
       const C yy = Sy[gg - pg0];
       const T k = Sk[gg - pg0];
@@ -2747,8 +2754,9 @@ __global__ void __launch_bounds__(PlaneR<N2, N3, TW>::THREADS) k_plane_fwd_rs(co
   for (int row = t; row < nr; row += TW) {
     const int g0 = sp.row_g0[r0 + row], cnt = sp.row_cnt[r0 + row], l0 = sp.row_l0[r0 + row];
     const C* line = R + (size_t)row * FR;
-    for (int idx = lane; idx < cnt; idx += 32) {
-      const C v = line[pmod(l0 + idx, N3)];
+    int lz = pmod(l0 + lane, N3);
+    for (int idx = lane; idx < cnt; idx += 32, lz = wrap_n<N3>(lz, 32 % N3)) {
+      const C v = line[lz];
       const int gg = g0 + idx;
       const C yy = yv[gg];
       const T k = kin[gg];
