@@ -2028,10 +2028,21 @@ PW_API int pw_autotune(pw_ctx* ctx, int nband, int precision, double* best_ms) {
     // the plane forms compared again inside two steps of the filter itself, round robin (its
     // projector GEMMs between the passes change what the passes find in L2; the persistent
     // plane forms gain there and not in bare applies), each with the x-line form of the best
-    // bare time; the fastest of all their runs kept
+    // bare time, and the runner-up x-line form (by its best bare time over the plane forms)
+    // with the best plane form, since bare applies rank close x-line forms within their
+    // noise; the fastest of all their runs kept
     const int xbest = best_v % kFormStride;
     std::vector<std::pair<float, int>> top;
     for (int pf = 0; pf < kPlaneForms; ++pf) top.push_back({0.f, xbest + kFormStride * pf});
+    {
+      float t2 = 1e30f;
+      int x2 = -1;
+      for (const auto& f : form_times) {
+        const int xf = f.second % kFormStride;
+        if (xf != xbest && f.first < t2) { t2 = f.first; x2 = xf; }
+      }
+      if (x2 >= 0) top.push_back({0.f, x2 + kFormStride * (best_v / kFormStride)});
+    }
     // at the batch size that suits the forms found (the first batch sweep ran with the
     // initial forms, which may prefer other sizes)
     {
