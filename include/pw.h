@@ -397,6 +397,9 @@ enum pw_prof_class {
  * forward pass (one CTA per SM walking the planes; the next plane is prefetched into L2 and its
  * blocks of Y_k and t_G into shared memory while the current one is gathered), 6 both passes
  * whole-plane and persistent (pass 1 prefetching the next plane's sphere block into L2).
+ * For PW_MIXED the bare-apply ranking is then checked inside two steps of the filter itself:
+ * every plane form with the best x-line form, and the runner-up x-line form with the best
+ * plane form; the fastest there is kept.
  * PW_FP64 tunes the plane form only (0 or 3, variant 0 or 48; its x-line form is fixed).
  * Forms other than 0 cover box lengths with two-stage radix plans.  Keeps the fastest for
  * `precision` in the context.  Synchronises the stream; *best_ms (may be NULL) receives
