@@ -76,3 +76,29 @@ def test_explicit_projector_descriptor_checked_on_the_host():
     d.nproj = 2
     assert lib.pw_ctx_create(ctypes.byref(d), None, ctypes.byref(h)) == -1
     assert b"need D" in lib.pw_last_error()
+
+
+def _zero(t):
+    if t in (ctypes.c_int, ctypes.c_int64, ctypes.c_uint64):
+        return 0
+    if t is ctypes.c_double:
+        return 0.0
+    return None  # pointers and handles
+
+
+def test_every_entry_point_rejects_a_null_handle_without_a_gpu():
+    # every call whose first argument is a context, batch or differentiation handle (or the
+    # descriptor / context array that makes one) returns PW_EINVAL for NULL and touches no
+    # device; destroy(NULL) is a no-op; the FMA-rate diagnostic takes a stream, not a handle
+    lib = pwlib.load()
+    skip = {"pw_strerror", "pw_last_error", "pw_kernel_launches", "pw_diag_fp64_fma_rate"}
+    destroy = {"pw_ctx_destroy", "pw_batch_destroy", "pw_diff_destroy"}
+    for name in sorted(set(pwlib.EXPORTS) - skip):
+        fn = getattr(lib, name)
+        args = [_zero(t) for t in fn.argtypes]
+        st = fn(*args)
+        if name in destroy:
+            assert st == 0, name
+        else:
+            assert st == -1, (name, st, lib.pw_last_error())
+            assert lib.pw_last_error(), name
