@@ -116,7 +116,7 @@ def test_explicit_projectors_mixed(case):
 
 def test_explicit_projectors_rayleigh_ritz():
     """Rayleigh-Ritz with the random P and Q: eigenvalues against the oracle's pencil
-    reduction (one S-Ortho pass on the GPU, two in the oracle; reading r11) to 1e-10 Ha."""
+    reduction (one S-Ortho pass on the GPU, two in the oracle, the same span) to 1e-10 Ha."""
     _, prob, P, D, Q = CASES[3]
     ham = oracle_for(prob, P, D, Q)
     with context_for(prob, P, D, Q) as ctx:

@@ -240,7 +240,7 @@ def test_s_ortho():
 
 @pytest.mark.parametrize("with_q", [False, True])
 def test_one_s_ortho_pass_before_rr_gives_the_same_ritz_pairs(with_q):
-    """Reading r11 of the GPU path: one Cholesky-QR pass, then Alg. 5 (whose Cholesky of
+    """How the GPU path orthonormalises before Rayleigh-Ritz: one Cholesky-QR pass, then Alg. 5 (whose Cholesky of
     S_Psi is the second pass), against the oracle's two passes then Alg. 5, on a filtered
     (ill-conditioned) block; and Ritz values do not depend on the basis of the span."""
     p = small_problem(with_q=with_q, nband=8)
